@@ -1,0 +1,109 @@
+"""Problem geometry and medium model (Sec. II, Eq. 1-3).  FP64 oracle; test
+infrastructure only.
+
+Conventions (readings of points the paper leaves open):
+
+* Time dependence e^{-i omega t}: every complex quantity is the complex
+  conjugate of the paper's e^{+j omega t} form; attenuation therefore
+  enters the compressibility as +i kappa''.  Speed of sound is unaffected.
+* Arrays are stored depth-major: shape (Nz, Nx) in 2D, (Nz, Ny, Nx) in 3D,
+  x fastest.  Pixel n has centre x = (ix + 1/2 - Nx/2) h,
+  y = (iy + 1/2 - Ny/2) h, z = iz h (depth increases downward).
+* The linear array sits one pixel above the first row of centres, at
+  z = -h, centred laterally: element e at x = (e - (N_E - 1)/2) pitch,
+  y = 0.  This places the sensing elements on the edge of V (Eq. 4) while
+  keeping every source-pixel distance >= h.
+"""
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+@dataclass
+class Problem:
+    """One reconstruction problem.
+
+    shape  : grid shape in array order, (Nz, Nx) or (Nz, Ny, Nx)
+    h      : pixel / voxel edge [m]
+    c0     : background speed of sound [m/s] (lossless background)
+    elem   : element positions [N_E, d] in (x, z) or (x, y, z) order [m]
+    freqs  : frequencies [N_F] in Hz
+    Transmitters and receivers are the same N_E elements (each element
+    transmits in turn, all receive), so N_T = N_R = N_E.
+    """
+    shape: tuple
+    h: float
+    c0: float
+    elem: np.ndarray
+    freqs: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dim(self):
+        return len(self.shape)
+
+    @property
+    def n(self):
+        return int(np.prod(self.shape))
+
+    @property
+    def n_elem(self):
+        return int(self.elem.shape[0])
+
+    @property
+    def n_freq(self):
+        return int(len(self.freqs))
+
+    @property
+    def cell_volume(self):
+        return self.h ** self.dim
+
+
+def linear_array(n_elem, pitch, h, dim):
+    """Element positions of a top-edge linear array (reading above)."""
+    xe = (np.arange(n_elem, dtype=np.float64) - (n_elem - 1) / 2.0) * pitch
+    if dim == 2:
+        return np.stack([xe, np.full(n_elem, -h)], axis=1)
+    return np.stack([xe, np.zeros(n_elem), np.full(n_elem, -h)], axis=1)
+
+
+def pixel_centres(shape, h):
+    """Centres of all pixels, [N, d] in (x, [y], z) order, row-major over
+    ``shape`` (x fastest)."""
+    if len(shape) == 2:
+        nz, nx = shape
+        z, x = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+        return np.stack([((x + 0.5 - nx / 2.0) * h).ravel(),
+                         (z * h).ravel().astype(np.float64)], axis=1)
+    nz, ny, nx = shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx),
+                          indexing="ij")
+    return np.stack([((x + 0.5 - nx / 2.0) * h).ravel(),
+                     ((y + 0.5 - ny / 2.0) * h).ravel(),
+                     (z * h).ravel().astype(np.float64)], axis=1)
+
+
+def wavenumbers(prob):
+    """k_l = omega_l / c0 (real: lossless background; k^2 = omega^2 kappa0
+    rho0 with kappa0 = 1/(c0^2 rho0), Sec. II)."""
+    return 2.0 * np.pi * np.asarray(prob.freqs, dtype=np.float64) / prob.c0
+
+
+def contrast_from_sos(c, c0, alpha=None):
+    """Contrast m = kappa/kappa0 - 1 (Eq. 3).
+
+    kappa' = 1/(c^2 rho0) (the alpha^2 term dropped, as the approximation of
+    Eq. 2 does), kappa'' = alpha/(pi c rho0) with alpha in Np/m/Hz, and under
+    e^{-i omega t} kappa = kappa' + i kappa''.  rho0 cancels in the ratio.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    m = (c0 * c0) / (c * c) - 1.0
+    if alpha is None:
+        return m.astype(np.complex128)
+    return m + 1j * np.asarray(alpha, dtype=np.float64) * c0 * c0 / (np.pi * c)
+
+
+def sos_from_contrast(m, c0):
+    """Speed of sound from the real part of the contrast, the inverse of
+    Eq. 2-3 for a lossless point: c = c0 / sqrt(1 + Re m)."""
+    return c0 / np.sqrt(1.0 + np.real(np.asarray(m)))
