@@ -1,0 +1,212 @@
+/*
+ * libfwi -- C ABI of the data-parallel hot path of TV-regularised
+ * frequency-domain full-waveform inversion for single-sided linear arrays
+ * (Guo, Auerbach, Eldar, "TV-Regularized Frequency-Domain Full-Waveform
+ * Inversion for Single-Sided Linear Ultrasound Array Data").
+ *
+ * One process, one GPU (sm_103a).  Every computational step runs in the
+ * library's own CUDA kernels; there is no CPU fallback.
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Time dependence e^{-i omega t} (the paper writes e^{+j omega t}; all
+ *    complex quantities here are the complex conjugates of the paper's).
+ *  - Grid n[0] x n[1] x n[2] = Nx x Ny x Nz (Ny = 1 in 2D), pixel edge h.
+ *    Arrays over the grid are depth-major, x fastest: index
+ *    (iz * Ny + iy) * Nx + ix.  Pixel centres x = (ix + 1/2 - Nx/2) h,
+ *    y = (iy + 1/2 - Ny/2) h, z = iz h.  N = Nx * Ny * Nz.
+ *  - Complex numbers are interleaved (re, im): "c128" = 2 doubles,
+ *    "c64" = 2 floats.  "cF" denotes the field type of the context:
+ *    c64 for FWI_MIXED, c128 for FWI_FP64.
+ *  - Transmitters and receivers are the same n_elem elements; data are
+ *    stored [n_freq][n_elem (transmit)][n_elem (receive)].
+ *  - Fields are stored [n_freq][n_elem][N].
+ *  - "dev" pointers are device memory of the context's device, owned by the
+ *    caller, and must not alias one another unless a call says so.  "host"
+ *    pointers are host memory owned by the caller.  The library owns only
+ *    the context and its workspace (allocated in fwi_create, freed in
+ *    fwi_destroy); no call allocates device memory after fwi_create.
+ *  - All device work is enqueued on the context's stream.  Calls that fill
+ *    a host result (fwi_solve_info, misfit) synchronise that stream before
+ *    returning; the others only enqueue.
+ *  - Errors: every call returns an fwi_status; on failure the context keeps
+ *    a message readable with fwi_last_error.  No exception crosses the ABI.
+ *    Device-side loops are bounded (krylov_max_it) and report a per-RHS
+ *    status; no kernel traps.
+ */
+#ifndef LIBFWI_H
+#define LIBFWI_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define FWI_API __attribute__((visibility("default")))
+#else
+#define FWI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fwi_status {
+  FWI_OK = 0,
+  FWI_ERR_INVALID_ARG = 1,   /* bad descriptor, size, pointer or index */
+  FWI_ERR_NOMEM = 2,         /* workspace allocation failed in fwi_create */
+  FWI_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  FWI_ERR_NOT_CONVERGED = 4, /* some RHS hit krylov_max_it (results written) */
+  FWI_ERR_BREAKDOWN = 5,     /* BiCGSTAB breakdown (rho or omega = 0) */
+  FWI_ERR_NONFINITE = 6,     /* a non-finite value reached a reduction */
+  FWI_ERR_CANCELLED = 7,     /* fwi_cancel was called during the solve */
+  FWI_ERR_UNSUPPORTED = 8    /* grid size without a compiled FFT plan */
+} fwi_status;
+
+typedef enum fwi_precision {
+  FWI_MIXED = 0, /* c64 fields and operator, FP64 Krylov scalars/reductions */
+  FWI_FP64 = 1   /* c128 fields and operator throughout */
+} fwi_precision;
+
+/* Problem statement (Sec. II): geometry, background, array, frequencies. */
+typedef struct fwi_problem_desc {
+  int dim;                 /* 2 or 3 */
+  int n[3];                /* Nx, Ny, Nz (Ny = 1 when dim == 2).  Each of
+                              2*Nx, 2*Ny (3D), 2*Nz must be a supported FFT
+                              length: 16, 32, 64, 128, 192, 256, 320, 384,
+                              512, 640, 768, 1024. */
+  double h;                /* pixel / voxel edge [m] */
+  double c0;               /* background speed of sound [m/s], lossless */
+  int n_elem;              /* number of array elements (N_T = N_R) */
+  const double* elem_pos;  /* host [n_elem][dim], (x, z) or (x, y, z) [m];
+                              copied in fwi_create */
+  int n_freq;
+  const double* freq_hz;   /* host [n_freq]; copied in fwi_create */
+  double krylov_tol;       /* BiCGSTAB relative residual (<= 0: 1e-6) */
+  int krylov_max_it;       /* BiCGSTAB iteration cap (<= 0: 1000) */
+  int precision;           /* fwi_precision */
+  int max_batch;           /* right-hand sides per Krylov launch
+                              (<= 0: all n_elem * n_freq in one launch) */
+} fwi_problem_desc;
+
+/* Per-call Krylov report.  The caller sets n_rhs and the optional host
+   arrays (each NULL or of length n_rhs >= n_elem * n_freq); the library
+   fills them.  RHS index = freq * n_elem + elem. */
+typedef struct fwi_solve_info {
+  int n_rhs;
+  int* iters;            /* host: BiCGSTAB iterations per RHS */
+  double* rel_resid;     /* host: final ||b - A x|| / ||b|| (recursive) */
+  int* status;           /* host: FWI_OK, FWI_ERR_NOT_CONVERGED, ... */
+  int max_iters;         /* out */
+  double max_rel_resid;  /* out */
+  int n_not_converged;   /* out */
+  float device_ms;       /* out: device time of the call (CUDA events) */
+} fwi_solve_info;
+
+/* ADMM-TV parameters (Eq. 7-8, Algorithm 1). */
+typedef struct fwi_admm_params {
+  double lambda;     /* TV weight */
+  double rho;        /* ADMM penalty */
+  double gamma;      /* reference-model weight */
+  double dual_step;  /* factor of the u-update (<= 0: rho, as printed) */
+  int n_cg;          /* CG iterations of the Gauss-Newton m-step */
+  const void* m_ref; /* dev c128 [N] reference model, or NULL for 0 */
+} fwi_admm_params;
+
+typedef struct fwi_ctx fwi_ctx;
+
+/* Device bytes fwi_create will allocate for this descriptor (admission
+   control).  Returns 0 for an invalid or unsupported descriptor. */
+FWI_API size_t fwi_workspace_bytes(const fwi_problem_desc* desc);
+
+/* Create a context on the current CUDA device, bound to cuda_stream (a
+   cudaStream_t).  NULL: the context creates its own blocking stream, which
+   is implicitly ordered with the legacy default stream (the Krylov
+   iterations are CUDA graphs, and the legacy stream cannot be captured).  Allocates the workspace and
+   precomputes, per frequency, the FFT of the cell-integrated Green's
+   function on the doubled lattice (Sec. IV-A) and the incident fields
+   p0 = G(x, x_e) (Eq. 5).  On failure *out is NULL. */
+FWI_API fwi_status fwi_create(const fwi_problem_desc* desc, void* cuda_stream,
+                      fwi_ctx** out);
+FWI_API fwi_status fwi_destroy(fwi_ctx* ctx);
+/* Message of the last failure on ctx ("" if none); valid until the next
+   call on ctx.  fwi_last_error(NULL) reports fwi_create failures. */
+FWI_API const char* fwi_last_error(const fwi_ctx* ctx);
+/* Request that a running or next solve stop at its next host check
+   (thread-safe); the solve returns FWI_ERR_CANCELLED. */
+FWI_API fwi_status fwi_cancel(fwi_ctx* ctx);
+
+/* Contrast m = kappa/kappa0 - 1 (Eq. 1-3) from speed of sound and optional
+   attenuation: m = c0^2/c^2 - 1 + i alpha c0^2/(pi c).
+   sos: dev double [N] (m/s); alpha: dev double [N] (Np/m/Hz) or NULL;
+   m: dev c128 [N] (out). */
+FWI_API fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos,
+                                 const double* alpha, void* m);
+
+/* Forward simulation F(m) (Eq. 4-5; Algorithm 1 "forward simulation"):
+   solves A_l p = p0_{l,e}, A_l = I - K_l diag(m), for every transmit e and
+   frequency l by batched BiCGSTAB, and projects the data
+   P^s_{l,e,j} = k_l^2 dV sum_n G_l(x_j, x_n) m_n p_{l,e}(n).
+   m: dev c128 [N].  fields: dev cF [n_freq][n_elem][N] or NULL (out; with
+   warm_start != 0 also the initial guess, otherwise the guess is 0).
+   data: dev cF [n_freq][n_elem][n_elem] or NULL (out).  The fields stay in
+   the context for fwi_admm_tv_step.  info: host or NULL. */
+FWI_API fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields,
+                       int warm_start, void* data, fwi_solve_info* info);
+
+/* Adjoint-state solves (Sec. IV-B): (I - diag(m) K_l)^H lambda = src for
+   every (l, e).  Computed as lambda = conj(A_l^{-1} conj(src)) because K is
+   complex-symmetric.  src, lambda: dev cF [n_freq][n_elem][N]. */
+FWI_API fwi_status fwi_adjoint(fwi_ctx* ctx, const void* m, const void* src,
+                       void* lambda, fwi_solve_info* info);
+
+/* One gradient evaluation of phi = 1/2 ||F(m) - d_obs||^2 (Eq. 7, 17):
+   forward solves, residual r = F(m) - d_obs, adjoint sources
+   s_{l,e} = sum_j conj(R_{l,j}) r_{l,e,j}, adjoint solves, and
+   grad_n = sum_{l,e} conj(p_{l,e}(n)) lambda_{l,e}(n) = (J^H r)_n.
+   d_obs: dev cF [n_freq][n_elem][n_elem]; grad: dev c128 [N] (out);
+   misfit: host double (out) or NULL; data: dev cF (out, the predicted
+   data F(m)) or NULL.  The forward fields stay in the context. */
+FWI_API fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs,
+                        void* grad, double* misfit, void* data,
+                        fwi_solve_info* info_fwd, fwi_solve_info* info_adj);
+
+/* One ADMM-TV iteration after the gradient (Algorithm 1 lines 4-7,
+   Eq. 9-14): solves (J^H J + rho nabla^T nabla + gamma I) dm = b with
+   b = -grad + rho nabla^T(g + u - nabla m) + gamma (m_ref - m) by n_cg CG
+   iterations from 0 (J from the fields of the last fwi_forward /
+   fwi_gradient), m += dm, g = shrink_{lambda/rho}(nabla m - u),
+   u += dual_step (g - nabla m), and optionally c = c0 / sqrt(1 + Re m).
+   nabla: forward differences in index units, zero on the last slice.
+   m: dev c128 [N] (in/out); g, u: dev c128 [dim][N] (in/out, component
+   order x, [y], z); grad: dev c128 [N]; sos_out: dev double [N] or NULL. */
+FWI_API fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u,
+                            const void* grad, const fwi_admm_params* p,
+                            double* sos_out);
+
+/* Single operator applications (Sec. IV-A) on n_rhs vectors at frequency
+   index freq: out = K in, A in = in - K(m in), or A^H in
+   = in - conj(m) K^H in.  in, out: dev cF [n_rhs][N] (must not alias);
+   m: dev c128 [N].  1 <= n_rhs <= the context's batch. */
+FWI_API fwi_status fwi_apply_K(fwi_ctx* ctx, int freq, int n_rhs, const void* in,
+                       void* out);
+FWI_API fwi_status fwi_apply_A(fwi_ctx* ctx, const void* m, int freq, int n_rhs,
+                       const void* in, void* out);
+FWI_API fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs,
+                        const void* in, void* out);
+
+/* Implicit Jacobian products at the fields of the last forward solve
+   (Eq. 16-17, receiver fields ptilde_{l,j} = k_l^2 dV p_{l,j}):
+   (J a)_{l,e,j} = sum_n p_{l,e}(n) ptilde_{l,j}(n) a_n and
+   (J^H b)_n = sum_{l,e,j} conj(p_{l,e}(n) ptilde_{l,j}(n)) b_{l,e,j}.
+   a: dev c128 [N]; y: dev c128 [n_freq][n_elem][n_elem] (out of J, in of
+   J^H); z: dev c128 [N] (out). */
+FWI_API fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y);
+FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
+
+/* Library version string. */
+FWI_API const char* fwi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBFWI_H */

@@ -1,0 +1,373 @@
+// C entry points of libfwi (include/libfwi.h): argument checks, context
+// creation and workspace accounting, and the composition of the hot-path
+// steps into the calls of the paper's problem statement (Sec. II-III).
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "ctx.cuh"
+
+namespace fwi {
+
+static thread_local std::string g_create_error;
+
+fwi_status fail(fwi_ctx* c, fwi_status s, const std::string& msg) {
+  if (c) c->err = msg; else g_create_error = msg;
+  return s;
+}
+
+fwi_status cuda_fail(fwi_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return fail(c, FWI_ERR_CUDA, m);
+}
+
+fwi_status copy_field(fwi_ctx* c, void* dst, const void* src, long long n, int conj);
+
+namespace {
+
+bool fft_len_ok(int L) {
+  switch (L) {
+    case 16: case 32: case 64: case 128: case 192: case 256: case 320: case 384:
+    case 512: case 640: case 768: case 1024: return true;
+    default: return false;
+  }
+}
+
+// Everything fwi_create derives from the descriptor.
+struct Layout {
+  int dim, nx, ny, nz, lx, ly, lz, rows, n_elem, n_freq, n_rhs, batch, ntiles, split;
+  long long N;
+  size_t csz;
+  size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec;
+  size_t total;
+};
+
+bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
+  auto bad = [&](const char* m) { if (why) *why = m; return false; };
+  if (!d) return bad("descriptor is NULL");
+  if (d->dim != 2 && d->dim != 3) return bad("dim must be 2 or 3");
+  L.dim = d->dim;
+  L.nx = d->n[0];
+  L.ny = (d->dim == 3) ? d->n[1] : 1;
+  L.nz = d->n[2];
+  if (L.nx <= 0 || L.ny <= 0 || L.nz <= 0) return bad("grid sizes must be positive");
+  L.lx = 2 * L.nx; L.ly = (d->dim == 3) ? 2 * L.ny : 1; L.lz = 2 * L.nz;
+  if (!fft_len_ok(L.lx) || !fft_len_ok(L.lz) || (d->dim == 3 && !fft_len_ok(L.ly)))
+    return bad("2*n must be one of 16,32,64,128,192,256,320,384,512,640,768,1024");
+  if (!(d->h > 0) || !(d->c0 > 0)) return bad("h and c0 must be positive");
+  if (d->n_elem <= 0 || !d->elem_pos) return bad("n_elem must be positive with elem_pos");
+  if (d->n_freq <= 0 || !d->freq_hz) return bad("n_freq must be positive with freq_hz");
+  for (int l = 0; l < d->n_freq; ++l)
+    if (!(d->freq_hz[l] > 0)) return bad("frequencies must be positive");
+  if (d->precision != FWI_MIXED && d->precision != FWI_FP64) return bad("unknown precision");
+  L.n_elem = d->n_elem; L.n_freq = d->n_freq;
+  L.n_rhs = d->n_elem * d->n_freq;
+  L.batch = (d->max_batch > 0 && d->max_batch < L.n_rhs) ? d->max_batch : L.n_rhs;
+  L.N = (long long)L.nx * L.ny * L.nz;
+  L.rows = L.ny * L.nz;
+  L.csz = (d->precision == FWI_FP64) ? 16 : 8;
+  const int lpc = (d->precision == FWI_FP64) ? Lsop<double>::row_lines_per_cta(L.lx)
+                                             : Lsop<float>::row_lines_per_cta(L.lx);
+  L.ntiles = (L.rows + lpc - 1) / lpc;
+  const long long P = (long long)L.lx * L.ly * L.lz;
+  const long long NE2 = (long long)L.n_elem * L.n_elem;
+  const int nbe = (L.n_elem + 63) / 64;
+  // split-K partials of the pixel contractions: at most ~1024 CTAs' tiles
+  const int tiles = nbe * nbe * L.n_freq;
+  L.split = (1024 / tiles) > 1 ? 1024 / tiles : 1;
+  L.b_ghat = (size_t)L.n_freq * P * L.csz;
+  L.b_field = (size_t)L.n_rhs * L.N * L.csz;
+  L.b_kv = (size_t)L.batch * L.N * L.csz;
+  L.b_plane1 = (size_t)L.batch * L.rows * L.lx * L.csz;
+  L.b_plane2 = (d->dim == 3) ? (size_t)L.batch * L.nz * L.ly * L.lx * L.csz : 0;
+  L.b_small = (size_t)L.batch * (sizeof(Scal) + NSLOT * L.ntiles * sizeof(double2) + sizeof(int)) +
+              64 + (size_t)L.n_freq * NE2 * (16 + L.csz) + 3 * 1024 * L.csz;
+  size_t js1 = (size_t)L.split * L.n_freq * NE2 * L.csz;
+  size_t js2 = (size_t)8 * L.N * sizeof(double2);
+  L.b_jsplit = js1 > js2 ? js1 : js2;
+  L.b_zpart = (size_t)L.n_freq * nbe * L.N * L.csz;
+  L.b_vec = (size_t)L.N * L.csz * 2 + (size_t)8 * L.N * 16 + (size_t)3 * L.dim * L.N * 16 +
+            sizeof(double) * (L.n_freq + 256 + 512 + 16);
+  L.total = L.b_ghat + 4 * L.b_field + 5 * L.b_kv + L.b_plane1 + L.b_plane2 + L.b_small +
+            L.b_jsplit + L.b_zpart + L.b_vec;
+  return true;
+}
+
+}  // namespace
+
+size_t workspace_bytes(const fwi_problem_desc* d, std::string* why) {
+  Layout L;
+  if (!make_layout(d, L, why)) return 0;
+  return L.total;
+}
+
+}  // namespace fwi
+
+using namespace fwi;
+
+static void release(fwi_ctx* c) {
+  if (!c) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(c->device);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
+                  c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
+                  c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
+                  c->jsplit, c->zpart, c->aF, c->red};
+  for (void* p : bufs) if (p) cudaFree(p);
+  for (auto* p : c->vN) if (p) cudaFree(p);
+  for (auto* p : c->vD) if (p) cudaFree(p);
+  if (c->h_n_active) cudaFreeHost(c->h_n_active);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete c;
+  cudaSetDevice(cur);
+}
+
+extern "C" {
+
+const char* fwi_version(void) { return "libfwi 0.1 (sm_103a)"; }
+
+size_t fwi_workspace_bytes(const fwi_problem_desc* desc) {
+  return workspace_bytes(desc, nullptr);
+}
+
+const char* fwi_last_error(const fwi_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+fwi_status fwi_cancel(fwi_ctx* ctx) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  ctx->cancel.store(true);
+  return FWI_OK;
+}
+
+fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
+  if (!out) return fail(nullptr, FWI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  g_create_error.clear();
+  Layout L;
+  std::string why;
+  if (!make_layout(d, L, &why)) return fail(nullptr, FWI_ERR_INVALID_ARG, why);
+  fwi_ctx* c = new fwi_ctx();
+  c->dim = L.dim; c->nx = L.nx; c->ny = L.ny; c->nz = L.nz;
+  c->lx = L.lx; c->ly = L.ly; c->lz = L.lz; c->N = L.N; c->rows = L.rows;
+  c->n_elem = L.n_elem; c->n_freq = L.n_freq; c->n_rhs = L.n_rhs; c->batch = L.batch;
+  c->h = d->h; c->c0 = d->c0;
+  c->tol = d->krylov_tol > 0 ? d->krylov_tol : 1e-6;
+  c->max_it = d->krylov_max_it > 0 ? d->krylov_max_it : 1000;
+  c->fp64 = (d->precision == FWI_FP64);
+  c->csz = L.csz;
+  c->ntiles = L.ntiles;
+  c->jsplit_n = L.split;
+  c->elem.assign(d->elem_pos, d->elem_pos + (size_t)d->n_elem * d->dim);
+  c->freq.assign(d->freq_hz, d->freq_hz + d->n_freq);
+  for (double f : c->freq) c->kwave.push_back(2.0 * 3.141592653589793238462643383279502884 * f / c->c0);
+  c->stream = (cudaStream_t)stream;
+  c->bytes = L.total;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess && !stream) {
+    // The legacy default stream cannot be graph-captured; a blocking stream
+    // is implicitly ordered with it, so callers on the default stream see
+    // the same ordering.
+    e = cudaStreamCreate(&c->own_stream);
+    c->stream = c->own_stream;
+  }
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+  auto alloc = [&](void** p, size_t bytes) {
+    if (e != cudaSuccess || bytes == 0) return;
+    e = cudaMalloc(p, bytes);
+  };
+  alloc(&c->ghat, L.b_ghat);
+  alloc(&c->p0, L.b_field);
+  alloc(&c->fields, L.b_field);
+  alloc(&c->lam, L.b_field);
+  alloc(&c->asrc, L.b_field);
+  for (int i = 0; i < 5; ++i) alloc(&c->kv[i], L.b_kv);
+  alloc(&c->plane1, L.b_plane1);
+  if (L.b_plane2) alloc(&c->plane2, L.b_plane2);
+  alloc(&c->mF, (size_t)L.N * L.csz);
+  alloc((void**)&c->scal, sizeof(Scal) * L.batch);
+  alloc((void**)&c->partial, sizeof(double2) * NSLOT * (size_t)L.ntiles * L.batch);
+  alloc((void**)&c->active, sizeof(int) * L.batch);
+  alloc((void**)&c->n_active, 64);
+  const size_t NE2 = (size_t)L.n_elem * L.n_elem;
+  alloc((void**)&c->dres, 16 * L.n_freq * NE2);
+  alloc(&c->dF, L.csz * L.n_freq * NE2);
+  alloc(&c->jsplit, L.b_jsplit);
+  alloc(&c->zpart, L.b_zpart);
+  alloc(&c->aF, (size_t)L.N * L.csz);
+  for (int i = 0; i < 6; ++i) alloc((void**)&c->vN[i], (size_t)L.N * 16);
+  alloc((void**)&c->vD[0], (size_t)L.dim * L.N * 16);
+  c->red_n = L.n_freq + 256 + 512 + 16;
+  alloc((void**)&c->red, sizeof(double) * c->red_n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_n_active, 64);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scal, sizeof(Scal) * L.batch);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_red, sizeof(double) * c->red_n);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e != cudaSuccess) {
+    fwi_status st = (e == cudaErrorMemoryAllocation) ? FWI_ERR_NOMEM : FWI_ERR_CUDA;
+    fail(nullptr, st, std::string("workspace allocation: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    release(c);
+    return st;
+  }
+  // per-frequency scales k_l^2 dV for the Jacobian / data contractions
+  std::vector<double> sc(L.n_freq);
+  for (int l = 0; l < L.n_freq; ++l) sc[l] = c->kwave[l] * c->kwave[l] * std::pow(c->h, c->dim);
+  e = cudaMemcpy(c->red, sc.data(), sizeof(double) * L.n_freq, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    fail(nullptr, FWI_ERR_CUDA, std::string("scale upload: ") + cudaGetErrorString(e));
+    release(c);
+    return FWI_ERR_CUDA;
+  }
+  fwi_status st = setup_operator(c);
+  if (st != FWI_OK) {
+    g_create_error = c->err;
+    release(c);
+    return st;
+  }
+  *out = c;
+  return FWI_OK;
+}
+
+fwi_status fwi_destroy(fwi_ctx* ctx) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  cudaStreamSynchronize(ctx->stream);
+  release(ctx);
+  return FWI_OK;
+}
+
+fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos, const double* alpha, void* m) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!sos || !m) return fail(ctx, FWI_ERR_INVALID_ARG, "sos and m are required");
+  ctx->err.clear();
+  return contrast_from_sos(ctx, sos, alpha, m);
+}
+
+fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields, int warm_start, void* data,
+                       fwi_solve_info* info) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m) return fail(ctx, FWI_ERR_INVALID_ARG, "m is NULL");
+  if (warm_start && !fields) return fail(ctx, FWI_ERR_INVALID_ARG, "warm start needs fields");
+  ctx->err.clear();
+  ctx->cancel.store(false);
+  const long long nf = (long long)ctx->n_rhs * ctx->N;
+  if (warm_start) {
+    fwi_status st = copy_field(ctx, ctx->fields, fields, nf, 0);
+    if (st != FWI_OK) return st;
+  }
+  fwi_status st = forward_solve(ctx, m, warm_start != 0, info);
+  if (st != FWI_OK && st != FWI_ERR_NOT_CONVERGED) return st;
+  fwi_status st2 = FWI_OK;
+  if (fields) st2 = copy_field(ctx, fields, ctx->fields, nf, 0);
+  if (st2 == FWI_OK) st2 = project_data(ctx, m, data);
+  if (st2 == FWI_OK) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_forward");
+  }
+  return st2 != FWI_OK ? st2 : st;
+}
+
+fwi_status fwi_adjoint(fwi_ctx* ctx, const void* m, const void* src, void* lambda,
+                       fwi_solve_info* info) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m || !src || !lambda) return fail(ctx, FWI_ERR_INVALID_ARG, "m, src, lambda are required");
+  ctx->err.clear();
+  ctx->cancel.store(false);
+  fwi_status st = adjoint_solve(ctx, m, src, true, info);
+  if (st != FWI_OK && st != FWI_ERR_NOT_CONVERGED) return st;
+  fwi_status st2 = copy_field(ctx, lambda, ctx->lam, (long long)ctx->n_rhs * ctx->N, 1);
+  if (st2 == FWI_OK) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_adjoint");
+  }
+  return st2 != FWI_OK ? st2 : st;
+}
+
+fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs, void* grad,
+                        double* misfit, void* data, fwi_solve_info* info_fwd,
+                        fwi_solve_info* info_adj) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m || !d_obs || !grad) return fail(ctx, FWI_ERR_INVALID_ARG, "m, d_obs, grad are required");
+  ctx->err.clear();
+  ctx->cancel.store(false);
+  fwi_status st = forward_solve(ctx, m, false, info_fwd);
+  if (st != FWI_OK && st != FWI_ERR_NOT_CONVERGED) return st;
+  fwi_status worst = st;
+  st = project_data(ctx, m, data);
+  if (st != FWI_OK) return st;
+  st = residual_misfit(ctx, d_obs, misfit);
+  if (st != FWI_OK) return st;
+  st = adjoint_sources_conj(ctx, ctx->asrc);
+  if (st != FWI_OK) return st;
+  st = adjoint_solve(ctx, m, ctx->asrc, false, info_adj);
+  if (st != FWI_OK && st != FWI_ERR_NOT_CONVERGED) return st;
+  if (st != FWI_OK) worst = st;
+  st = assemble_gradient(ctx, grad);
+  if (st != FWI_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_gradient");
+  return worst;
+}
+
+fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void* grad,
+                            const fwi_admm_params* p, double* sos_out) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m || !g || !u || !grad || !p) return fail(ctx, FWI_ERR_INVALID_ARG, "missing argument");
+  if (!(p->rho > 0) || p->lambda < 0 || p->gamma < 0 || p->n_cg < 0)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "need rho > 0, lambda >= 0, gamma >= 0, n_cg >= 0");
+  ctx->err.clear();
+  fwi_status st = admm_step(ctx, m, g, u, grad, p, sos_out);
+  if (st != FWI_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_admm_tv_step");
+  return FWI_OK;
+}
+
+static fwi_status apply_common(fwi_ctx* ctx, int kind, const void* m, int freq, int n_rhs,
+                               const void* in, void* out) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!in || !out || (kind != 0 && !m)) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
+  if (in == out) return fail(ctx, FWI_ERR_INVALID_ARG, "in and out must not alias");
+  if (freq < 0 || freq >= ctx->n_freq) return fail(ctx, FWI_ERR_INVALID_ARG, "freq out of range");
+  if (n_rhs < 1 || n_rhs > ctx->batch) return fail(ctx, FWI_ERR_INVALID_ARG, "n_rhs out of range");
+  ctx->err.clear();
+  return apply_op(ctx, kind, m, freq, n_rhs, in, out);
+}
+
+fwi_status fwi_apply_K(fwi_ctx* ctx, int freq, int n_rhs, const void* in, void* out) {
+  return apply_common(ctx, 0, nullptr, freq, n_rhs, in, out);
+}
+fwi_status fwi_apply_A(fwi_ctx* ctx, const void* m, int freq, int n_rhs, const void* in,
+                       void* out) {
+  return apply_common(ctx, 1, m, freq, n_rhs, in, out);
+}
+fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs, const void* in,
+                        void* out) {
+  return apply_common(ctx, 2, m, freq, n_rhs, in, out);
+}
+
+fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!a || !y) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
+  if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
+  ctx->err.clear();
+  return jac_forward(ctx, a, (double2*)y);
+}
+
+fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!y || !z) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
+  if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
+  ctx->err.clear();
+  return jac_adjoint(ctx, (const double2*)y, (double2*)z);
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Host-side context of libfwi: descriptor copy, device workspace and the
+// cached CUDA graphs.  Shared by the library's translation units.
+#pragma once
+
+#include <atomic>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/libfwi.h"
+#include "common.cuh"
+
+struct fwi_ctx {
+  // ---- problem ----
+  int dim = 2;
+  int nx = 0, ny = 1, nz = 0;       // grid
+  int lx = 0, ly = 1, lz = 0;       // doubled lattice
+  long long N = 0;                  // voxels
+  int rows = 0;                     // x-lines per field (ny * nz)
+  int n_elem = 0, n_freq = 0, n_rhs = 0, batch = 0;
+  double h = 0, c0 = 0, tol = 1e-6;
+  int max_it = 1000;
+  bool fp64 = false;
+  size_t csz = 8;                   // bytes of one field element
+  std::vector<double> elem, freq, kwave;
+  // ---- device ----
+  cudaStream_t stream = nullptr;
+  cudaStream_t own_stream = nullptr;  // created when the caller passes NULL
+  int device = 0, n_sm = 0;
+  // workspace (field precision unless noted)
+  void* ghat = nullptr;             // [n_freq][lz][ly][lx], scaled k^2/(lx ly lz)
+  void* tw_x = nullptr;             // twiddle tables exp(-2 pi i j/L)
+  void* tw_y = nullptr;
+  void* tw_z = nullptr;
+  void* p0 = nullptr;               // [n_rhs][N] incident fields
+  void* fields = nullptr;           // [n_rhs][N] forward solution
+  void* lam = nullptr;              // [n_rhs][N] adjoint work / solution
+  void* asrc = nullptr;             // [n_rhs][N] adjoint right-hand sides
+  void* kv[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // R, RH, P, V, T
+  void* plane1 = nullptr;           // [batch][rows][lx]
+  void* plane2 = nullptr;           // 3D: [batch][nz][ly][lx]
+  void* mF = nullptr;               // [N] contrast in field precision
+  fwi::Scal* scal = nullptr;        // [batch]
+  double2* partial = nullptr;       // [batch][NSLOT][ntiles]
+  int ntiles = 0;
+  int* active = nullptr;            // [batch]
+  int* n_active = nullptr;          // [1]
+  int* h_n_active = nullptr;        // pinned host mirror
+  fwi::Scal* h_scal = nullptr;      // pinned host mirror [batch]
+  // Jacobian / data / ADMM workspace
+  double2* dres = nullptr;          // [n_freq][n_elem][n_elem] c128 scratch
+  void* dF = nullptr;               // [n_freq][n_elem][n_elem] field precision
+  void* jsplit = nullptr;           // split-K partials of pixel contractions
+  int jsplit_n = 0;
+  void* zpart = nullptr;            // per-(freq, e-block) partials of J^H
+  void* aF = nullptr;               // [N] field-precision vector
+  double2* vN[8] = {};              // [N] c128 ADMM / CG vectors
+  double2* vD[3] = {};              // [dim][N] c128 ADMM vectors
+  double* red = nullptr;            // reduction scratch (doubles)
+  double* h_red = nullptr;          // pinned host mirror
+  int red_n = 0;
+  bool fields_valid = false;
+  // graphs keyed by (solution pointer, batch start, batch size)
+  std::map<std::tuple<const void*, int, int>, cudaGraphExec_t> graphs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::atomic<bool> cancel{false};
+  std::string err;
+  size_t bytes = 0;
+};
+
+// Implemented in the library's units.
+namespace fwi {
+fwi_status fail(fwi_ctx* c, fwi_status s, const std::string& msg);
+fwi_status cuda_fail(fwi_ctx* c, cudaError_t e, const char* where);
+size_t workspace_bytes(const fwi_problem_desc* d, std::string* why);
+fwi_status setup_operator(fwi_ctx* c);
+fwi_status forward_solve(fwi_ctx* c, const void* m, bool warm, fwi_solve_info* info);
+fwi_status adjoint_solve(fwi_ctx* c, const void* m, const void* src, bool conj_src,
+                         fwi_solve_info* info);
+fwi_status set_contrast(fwi_ctx* c, const void* m);
+fwi_status apply_op(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
+                    const void* in, void* out);
+// data / Jacobian / ADMM
+fwi_status project_data(fwi_ctx* c, const void* m, void* data_out);
+fwi_status residual_misfit(fwi_ctx* c, const void* d_obs, double* misfit);
+fwi_status adjoint_sources_conj(fwi_ctx* c, void* out);
+fwi_status assemble_gradient(fwi_ctx* c, void* grad);
+fwi_status jac_forward(fwi_ctx* c, const void* a_c128, double2* y);
+fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z);
+fwi_status admm_step(fwi_ctx* c, void* m, void* g, void* u, const void* grad,
+                     const fwi_admm_params* p, double* sos);
+fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m);
+}  // namespace fwi
+
+#define FWI_CUDA(c, call)                                          \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return fwi::cuda_fail((c), e_, #call);  \
+  } while (0)

@@ -1,0 +1,474 @@
+// Pixel contractions of the data equation, the adjoint state and the
+// implicit Jacobian (Eq. 4, 15-17; Sec. IV-B, IV-C).  With receivers at the
+// transmit positions the receiver rows are R_{l,j} = k_l^2 dV p0_{l,j} and
+// the receiver fields ptilde_{l,j} = k_l^2 dV p_{l,j}, so every product is
+// one of two complex contractions over the field arrays [l][e][N]:
+//
+//  contract : Y_l[e][j] = s_l sum_n X_l[e][n] a[n] Q_l[j][n]
+//             (data: X = p, a = m, Q = p0; J a: X = Q = p)
+//  mix      : W_l[e][n] = s_l sum_j B_l[e][j] Q'_l[j][n]   (Q' = Q or conj Q)
+//             materialised (adjoint sources conj(s_e) = sum_j R_j conj(r_ej))
+//             or fused with z[n] += sum_e conj(X_l[e][n]) W_l[e][n]  (J^H b)
+//
+// Both are register-tiled CUDA-core kernels (64 x 64 complex output tiles,
+// 4 x 4 per thread, operands staged through shared memory).  Partial sums
+// across pixel chunks / transmit blocks are combined in FP64 in fixed order.
+#include <cmath>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace fwi {
+
+namespace {
+
+constexpr int TB = 64;   // output tile edge (complex)
+constexpr int KC = 16;   // contraction chunk
+
+inline int blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+contract_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ a,
+                const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ part, int NE,
+                long long N, int n_freq, long long chunk) {
+  using V = cplx<T>;
+  __shared__ V Xs[KC][TB + 1];
+  __shared__ V Qs[KC][TB + 1];
+  const int s = blockIdx.x;
+  const int nbe = (NE + TB - 1) / TB;
+  const int eb = blockIdx.y % nbe, jb = blockIdx.y / nbe;
+  const int l = blockIdx.z;
+  const int tid = threadIdx.x;
+  const int te = tid & 15, tj = tid >> 4;
+  const long long n_begin = (long long)s * chunk;
+  long long n_end = n_begin + chunk;
+  if (n_end > N) n_end = N;
+  const V* Xl = X + (long long)l * NE * N;
+  const V* Ql = Q + (long long)l * NE * N;
+  V acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(T(0), T(0));
+  for (long long n0 = n_begin; n0 < n_end; n0 += KC) {
+#pragma unroll
+    for (int q = 0; q < (TB * KC) / 256; ++q) {
+      const int idx = tid + q * 256;
+      const int r = idx / KC, cc = idx % KC;
+      const long long n = n0 + cc;
+      const int e = eb * TB + r, j = jb * TB + r;
+      V xv = mk<T>(T(0), T(0)), qv = mk<T>(T(0), T(0));
+      if (n < n_end) {
+        if (e < NE) {
+          xv = Xl[(long long)e * N + n];
+          if (a) xv = cmul(xv, a[n]);
+        }
+        if (j < NE) qv = Ql[(long long)j * N + n];
+      }
+      Xs[cc][r] = xv;
+      Qs[cc][r] = qv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      V xv[4], qv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xv[i] = Xs[kk][te + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) qv[j] = Qs[kk][tj + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x += xv[i].x * qv[j].x - xv[i].y * qv[j].y;
+          acc[i][j].y += xv[i].x * qv[j].y + xv[i].y * qv[j].x;
+        }
+    }
+    __syncthreads();
+  }
+  V* out = part + ((long long)s * n_freq + l) * NE * NE;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = eb * TB + te + 16 * i, jj = jb * TB + tj + 16 * j;
+      if (e < NE && jj < NE) out[(long long)e * NE + jj] = acc[i][j];
+    }
+}
+
+// Y[l][e][j] = scale_l * sum_s part[s][l][e][j]  (FP64, fixed order)
+template <typename T>
+__global__ void contract_reduce_kernel(double2* Y, const cplx<T>* part, int split,
+                                       long long per_split, int NE2, const double* scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_split;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < split; ++s) {
+      const cplx<T> v = part[(long long)s * per_split + i];
+      sx += (double)v.x;
+      sy += (double)v.y;
+    }
+    const double f = scale[i / NE2];
+    Y[i] = make_double2(sx * f, sy * f);
+  }
+}
+
+template <typename T, bool FUSED>
+__global__ void __launch_bounds__(256)
+mix_kernel(const cplx<T>* __restrict__ B, const cplx<T>* __restrict__ Q, int conjQ,
+           const cplx<T>* __restrict__ X, cplx<T>* __restrict__ out,
+           const double* __restrict__ scale, int NE, long long N) {
+  using V = cplx<T>;
+  __shared__ V Bs[KC][TB + 1];
+  __shared__ V Qs[KC][TB + 1];
+  __shared__ V red[16][TB + 1];
+  const int nbn = blockIdx.x, eb = blockIdx.y, l = blockIdx.z;
+  const int nbe = gridDim.y;
+  const int tid = threadIdx.x;
+  const int tn = tid & 15, te = tid >> 4;
+  const long long n0 = (long long)nbn * TB;
+  const V* Bl = B + (long long)l * NE * NE;
+  const V* Ql = Q + (long long)l * NE * N;
+  V acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mk<T>(T(0), T(0));
+  for (int j0 = 0; j0 < NE; j0 += KC) {
+#pragma unroll
+    for (int q = 0; q < (TB * KC) / 256; ++q) {
+      const int idx = tid + q * 256;
+      // B tile: row e (TB of them), KC consecutive j
+      {
+        const int r = idx / KC, cc = idx % KC;
+        const int e = eb * TB + r, j = j0 + cc;
+        Bs[cc][r] = (e < NE && j < NE) ? Bl[(long long)e * NE + j] : mk<T>(T(0), T(0));
+      }
+      // Q tile: row j (KC of them), TB consecutive n
+      {
+        const int kk = idx / TB, nn = idx % TB;
+        const int j = j0 + kk;
+        const long long n = n0 + nn;
+        V v = mk<T>(T(0), T(0));
+        if (j < NE && n < N) {
+          v = Ql[(long long)j * N + n];
+          if (conjQ) v.y = -v.y;
+        }
+        Qs[kk][nn] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      V bv[4], qv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) bv[i] = Bs[kk][te + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) qv[j] = Qs[kk][tn + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x += bv[i].x * qv[j].x - bv[i].y * qv[j].y;
+          acc[i][j].y += bv[i].x * qv[j].y + bv[i].y * qv[j].x;
+        }
+    }
+    __syncthreads();
+  }
+  const T f = (T)scale[l];
+  if (!FUSED) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int e = eb * TB + te + 16 * i;
+        const long long n = n0 + tn + 16 * j;
+        if (e < NE && n < N)
+          out[((long long)l * NE + e) * N + n] = mk<T>(acc[i][j].x * f, acc[i][j].y * f);
+      }
+    return;
+  }
+  // fused J^H: sum_e conj(X[e][n]) W[e][n]
+  const V* Xl = X + (long long)l * NE * N;
+  V zs[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    zs[j] = mk<T>(T(0), T(0));
+    const long long n = n0 + tn + 16 * j;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = eb * TB + te + 16 * i;
+      if (e < NE && n < N) {
+        const V x = Xl[(long long)e * N + n];
+        zs[j] = cadd(zs[j], cmulc(acc[i][j], x));  // W * conj(X)
+      }
+    }
+    red[te][tn + 16 * j] = zs[j];
+  }
+  __syncthreads();
+  if (tid < TB) {
+    V s = mk<T>(T(0), T(0));
+#pragma unroll
+    for (int r = 0; r < 16; ++r) s = cadd(s, red[r][tid]);
+    const long long n = n0 + tid;
+    if (n < N) out[((long long)l * nbe + eb) * N + n] = mk<T>(s.x * f, s.y * f);
+  }
+}
+
+// z[n] = sum_{p < np} part[p][n]  (FP64, fixed order)
+template <typename T>
+__global__ void sum_parts_kernel(double2* z, const cplx<T>* part, int np, long long N,
+                                 int conj_out) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int p = 0; p < np; ++p) {
+      const cplx<T> v = part[(long long)p * N + n];
+      sx += (double)v.x;
+      sy += (double)v.y;
+    }
+    z[n] = make_double2(sx, conj_out ? -sy : sy);
+  }
+}
+
+// Per-pixel sum over (l, e) of p * y in chunks: part[s][n] (FP64).
+template <typename T>
+__global__ void grad_partial_kernel(double2* part, const cplx<T>* P, const cplx<T>* Y,
+                                    int nle, int per, long long N) {
+  const int s = blockIdx.y;
+  const int le0 = s * per;
+  int le1 = le0 + per;
+  if (le1 > nle) le1 = nle;
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    int le = le0;
+    while (le < le1) {
+      T ax = 0, ay = 0;
+      const int stop = (le + 16 < le1) ? le + 16 : le1;
+#pragma unroll 4
+      for (; le < stop; ++le) {
+        const cplx<T> p = P[(long long)le * N + n];
+        const cplx<T> y = Y[(long long)le * N + n];
+        ax += p.x * y.x - p.y * y.y;
+        ay += p.x * y.y + p.y * y.x;
+      }
+      sx += (double)ax;
+      sy += (double)ay;
+    }
+    part[(long long)s * N + n] = make_double2(sx, sy);
+  }
+}
+
+// grad[n] = conj(sum_s part[s][n])
+__global__ void grad_reduce_kernel(double2* g, const double2* part, int ns, long long N) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      sx += part[(long long)s * N + n].x;
+      sy += part[(long long)s * N + n].y;
+    }
+    g[n] = make_double2(sx, -sy);
+  }
+}
+
+// r = d - d_obs (FP64); conj(r) in field precision for the adjoint sources;
+// block partials of |r|^2.
+template <typename T>
+__global__ void residual_kernel(double2* r, cplx<T>* rconjF, const double2* d,
+                                const cplx<T>* d_obs, long long n, double* part) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const cplx<T> o = d_obs[i];
+    const double2 v = make_double2(d[i].x - (double)o.x, d[i].y - (double)o.y);
+    r[i] = v;
+    rconjF[i] = mk<T>((T)v.x, (T)(-v.y));
+    acc += v.x * v.x + v.y * v.y;
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+template <typename T>
+__global__ void to_field_kernel(cplx<T>* dst, const double2* src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = mk<T>((T)src[i].x, (T)src[i].y);
+}
+
+// ---------------------------------------------------------------------------
+template <typename T> struct Jac {
+  static std::vector<double> scales(fwi_ctx* c) {
+    std::vector<double> s(c->n_freq);
+    const double dv = std::pow(c->h, c->dim);
+    for (int l = 0; l < c->n_freq; ++l) s[l] = c->kwave[l] * c->kwave[l] * dv;
+    return s;
+  }
+
+  static int split_for(fwi_ctx* c) {
+    const int nbe = (c->n_elem + TB - 1) / TB;
+    const int tiles = nbe * nbe * c->n_freq;
+    int split = (c->n_sm * 6 + tiles - 1) / tiles;
+    const long long max_split = (c->N + KC - 1) / KC;
+    if (split > max_split) split = (int)max_split;
+    if (split < 1) split = 1;
+    if (split > c->jsplit_n) split = c->jsplit_n;
+    return split;
+  }
+
+  // Y = scale_l * contract(X, a, Q) (c128, [l][e][j])
+  static fwi_status contract(fwi_ctx* c, const cplx<T>* X, const cplx<T>* a,
+                             const cplx<T>* Q, double2* Y) {
+    const int nbe = (c->n_elem + TB - 1) / TB;
+    const int split = split_for(c);
+    long long chunk = (c->N + split - 1) / split;
+    chunk = ((chunk + KC - 1) / KC) * KC;
+    dim3 grid(split, nbe * nbe, c->n_freq);
+    contract_kernel<T><<<grid, 256, 0, c->stream>>>(X, a, Q, (cplx<T>*)c->jsplit, c->n_elem,
+                                                    c->N, c->n_freq, chunk);
+    FWI_CUDA(c, cudaGetLastError());
+    const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
+    contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red);
+    FWI_CUDA(c, cudaGetLastError());
+    return FWI_OK;
+  }
+
+  static fwi_status upload_scales(fwi_ctx*) { return FWI_OK; }  // set in fwi_create
+};
+
+}  // namespace
+
+// Layout of c->red: [0, n_freq) per-frequency scales k_l^2 dV; then misfit
+// block partials.
+static inline double* misfit_parts(fwi_ctx* c) { return c->red + c->n_freq; }
+constexpr int kMisfitBlocks = 256;
+
+template <typename T> static fwi_status project_data_t(fwi_ctx* c, void* data_out) {
+  fwi_status st = Jac<T>::upload_scales(c);
+  if (st != FWI_OK) return st;
+  st = Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->mF,
+                        (const cplx<T>*)c->p0, c->dres);
+  if (st != FWI_OK) return st;
+  if (data_out) {
+    const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
+    to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        (cplx<T>*)data_out, c->dres, nd);
+    FWI_CUDA(c, cudaGetLastError());
+  }
+  return FWI_OK;
+}
+
+fwi_status project_data(fwi_ctx* c, const void* m, void* data_out) {
+  (void)m;  // the contrast was set by the forward solve
+  return c->fp64 ? project_data_t<double>(c, data_out) : project_data_t<float>(c, data_out);
+}
+
+template <typename T> static fwi_status residual_t(fwi_ctx* c, const void* d_obs, double* misfit) {
+  const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
+  // c->dres holds F(m); overwrite with r = F(m) - d_obs, conj(r) into dF
+  residual_kernel<T><<<kMisfitBlocks, 256, 0, c->stream>>>(
+      c->dres, (cplx<T>*)c->dF, c->dres, (const cplx<T>*)d_obs, nd, misfit_parts(c));
+  FWI_CUDA(c, cudaGetLastError());
+  if (misfit) {
+    FWI_CUDA(c, cudaMemcpyAsync(c->h_red, misfit_parts(c), sizeof(double) * kMisfitBlocks,
+                                cudaMemcpyDeviceToHost, c->stream));
+    FWI_CUDA(c, cudaStreamSynchronize(c->stream));
+    double s = 0.0;
+    for (int i = 0; i < kMisfitBlocks; ++i) s += c->h_red[i];
+    *misfit = 0.5 * s;
+  }
+  return FWI_OK;
+}
+
+fwi_status residual_misfit(fwi_ctx* c, const void* d_obs, double* misfit) {
+  return c->fp64 ? residual_t<double>(c, d_obs, misfit) : residual_t<float>(c, d_obs, misfit);
+}
+
+// conj(s_{l,e})(n) = k_l^2 dV sum_j p0_{l,j}(n) conj(r_{l,e,j}) into `out`.
+template <typename T> static fwi_status adjoint_sources_t(fwi_ctx* c, void* out) {
+  fwi_status st = Jac<T>::upload_scales(c);
+  if (st != FWI_OK) return st;
+  dim3 grid((unsigned)((c->N + TB - 1) / TB), (c->n_elem + TB - 1) / TB, c->n_freq);
+  mix_kernel<T, false><<<grid, 256, 0, c->stream>>>(
+      (const cplx<T>*)c->dF, (const cplx<T>*)c->p0, 0, nullptr, (cplx<T>*)out, c->red,
+      c->n_elem, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status adjoint_sources_conj(fwi_ctx* c, void* out) {
+  return c->fp64 ? adjoint_sources_t<double>(c, out) : adjoint_sources_t<float>(c, out);
+}
+
+// grad = sum_{l,e} conj(p) lambda with lambda = conj(y), y in c->lam.
+template <typename T> static fwi_status gradient_t(fwi_ctx* c, void* grad) {
+  const int ns = 8;
+  const int per = (c->n_rhs + ns - 1) / ns;
+  double2* part = (double2*)c->jsplit;  // needs ns * N doubles2 (checked at create)
+  dim3 grid(blocks_for(c->N, 256, 1 << 20), ns);
+  grad_partial_kernel<T><<<grid, 256, 0, c->stream>>>(part, (const cplx<T>*)c->fields,
+                                                      (const cplx<T>*)c->lam, c->n_rhs, per, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  grad_reduce_kernel<<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      (double2*)grad, part, ns, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status assemble_gradient(fwi_ctx* c, void* grad) {
+  return c->fp64 ? gradient_t<double>(c, grad) : gradient_t<float>(c, grad);
+}
+
+// (J a)_{l,e,j} = k_l^2 dV sum_n p_e(n) p_j(n) a_n
+template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a, double2* y) {
+  fwi_status st = Jac<T>::upload_scales(c);
+  if (st != FWI_OK) return st;
+  to_field_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      (cplx<T>*)c->aF, (const double2*)a, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  return Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
+                          (const cplx<T>*)c->fields, y);
+}
+
+fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {
+  return c->fp64 ? jac_forward_t<double>(c, a, y) : jac_forward_t<float>(c, a, y);
+}
+
+// (J^H b)_n = sum_l k_l^2 dV sum_e conj(p_e(n)) sum_j conj(p_j(n)) b_ej
+template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2* y, double2* z) {
+  fwi_status st = Jac<T>::upload_scales(c);
+  if (st != FWI_OK) return st;
+  const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
+  to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      (cplx<T>*)c->dF, y, nd);
+  FWI_CUDA(c, cudaGetLastError());
+  const int nbe = (c->n_elem + TB - 1) / TB;
+  dim3 grid((unsigned)((c->N + TB - 1) / TB), nbe, c->n_freq);
+  mix_kernel<T, true><<<grid, 256, 0, c->stream>>>(
+      (const cplx<T>*)c->dF, (const cplx<T>*)c->fields, 1, (const cplx<T>*)c->fields,
+      (cplx<T>*)c->zpart, c->red, c->n_elem, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      z, (const cplx<T>*)c->zpart, c->n_freq * nbe, c->N, 0);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z) {
+  return c->fp64 ? jac_adjoint_t<double>(c, y, z) : jac_adjoint_t<float>(c, y, z);
+}
+
+}  // namespace fwi

@@ -1,0 +1,527 @@
+// Batched BiCGSTAB for the Lippmann-Schwinger systems A_l p = b,
+// A_l = I - K_l diag(m) (Eq. 5; the paper solves them with a Krylov method,
+// Sec. IV-A).  All right-hand sides of a batch iterate together in one
+// persistent launch per pass; fields and operator applications are in the
+// field precision, inner products, step scalars and the stopping test in
+// FP64.  One iteration (van der Vorst's BiCGSTAB) is the pass sequence
+//
+//   col(conv) -> row_inv[v = p - K m p, <rhat,v>] -> S1 (alpha)
+//   row_fwd[s = r - alpha v] -> col(conv) -> row_inv[t = s - K m s, dots]
+//   S2 (omega, rho, beta, ||r||, convergence) -> compact
+//   row_fwd[x += alpha p + omega s; r = s - omega t; p = r + beta (p - omega v)]
+//
+// captured once in a CUDA graph and replayed; the host reads the number of
+// active right-hand sides between replays.  ||r_new||^2 = ||s||^2 -
+// |<t,s>|^2/||t||^2 and rho_new = <rhat,s> - omega <rhat,t> come from the
+// partial sums of the t-pass, so the x/r/p update fuses into the next
+// forward row pass.  The last update of each finished RHS is applied by a
+// final elementwise pass.
+#include <cmath>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace fwi {
+
+namespace {
+
+__device__ inline double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ inline double2 zsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ inline double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ inline double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ inline double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ inline bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Warp-cooperative fixed-order sum of one slot's tile partials.
+__device__ inline double2 warp_slot_sum(const double2* part, int ntiles, int lane) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = lane; i < ntiles; i += 32) s = zadd(s, part[i]);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
+    s.y += __shfl_xor_sync(0xffffffffu, s.y, off);
+  }
+  return s;
+}
+
+// S0: initial state from the INIT (slot 0 = ||b||^2) or R0 (slot 0 =
+// ||r0||^2, slot 1 = ||b||^2) partials.
+__global__ void s0_kernel(Scal* scal, const double2* partial, int ntiles, int nb,
+                          int from_r0, double tol2) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= nb) return;
+  const double2* p = partial + (long long)warp * NSLOT * ntiles;
+  const double r2 = warp_slot_sum(p, ntiles, lane).x;
+  const double b2 = from_r0 ? warp_slot_sum(p + ntiles, ntiles, lane).x : r2;
+  if (lane == 0) {
+    Scal s;
+    s.rho = make_double2(r2, 0.0);
+    s.alpha = make_double2(0.0, 0.0);
+    s.omega = make_double2(0.0, 0.0);
+    s.beta = make_double2(0.0, 0.0);
+    s.bnorm2 = b2;
+    s.rnorm2 = r2;
+    s.iters = 0;
+    s.pending = 0;
+    const bool fin = isfinite(r2) && isfinite(b2);
+    s.status = fin ? FWI_OK : FWI_ERR_NONFINITE;
+    s.active = (fin && b2 > 0.0 && r2 > tol2 * b2) ? 1 : 0;
+    scal[warp] = s;
+  }
+}
+
+// S1: alpha = rho / <rhat, v>.
+__global__ void s1_kernel(Scal* scal, const double2* partial, int ntiles,
+                          const int* active, const int* n_active) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= *n_active) return;
+  const int rhs = active[warp];
+  const double2 rv = warp_slot_sum(partial + (long long)rhs * NSLOT * ntiles, ntiles, lane);
+  if (lane == 0) {
+    Scal& s = scal[rhs];
+    if (!zfinite(rv)) {
+      s.status = FWI_ERR_NONFINITE;
+      s.alpha = make_double2(0.0, 0.0);
+    } else if (zabs2(rv) == 0.0) {
+      s.status = FWI_ERR_BREAKDOWN;
+      s.alpha = make_double2(0.0, 0.0);
+    } else {
+      s.alpha = zdiv(s.rho, rv);
+    }
+  }
+}
+
+// S2: omega, rho_new, ||r_new||^2, stopping test, beta.
+__global__ void s2_kernel(Scal* scal, const double2* partial, int ntiles,
+                          const int* active, const int* n_active, double tol2,
+                          int max_it) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= *n_active) return;
+  const int rhs = active[warp];
+  const double2* p = partial + (long long)rhs * NSLOT * ntiles;
+  const double2 ts = warp_slot_sum(p, ntiles, lane);
+  const double tt = warp_slot_sum(p + ntiles, ntiles, lane).x;
+  const double2 rt = warp_slot_sum(p + 2 * ntiles, ntiles, lane);
+  const double2 rs = warp_slot_sum(p + 3 * ntiles, ntiles, lane);
+  const double ss = warp_slot_sum(p + 4 * ntiles, ntiles, lane).x;
+  if (lane != 0) return;
+  Scal& s = scal[rhs];
+  s.iters += 1;
+  if (s.status != FWI_OK) {  // breakdown / non-finite flagged in S1
+    s.omega = make_double2(0.0, 0.0);
+    s.active = 0;
+    s.pending = (s.status == FWI_ERR_BREAKDOWN) ? 1 : 0;
+    return;
+  }
+  if (!(zfinite(ts) && isfinite(tt) && zfinite(rt) && zfinite(rs) && isfinite(ss))) {
+    s.status = FWI_ERR_NONFINITE;
+    s.active = 0;
+    s.pending = 0;
+    return;
+  }
+  double2 omega = make_double2(0.0, 0.0);
+  double rn2 = ss;
+  if (tt > 0.0) {
+    omega = make_double2(ts.x / tt, ts.y / tt);
+    rn2 = ss - zabs2(ts) / tt;
+    if (rn2 < 0.0) rn2 = 0.0;
+  }
+  const double2 rho_new = zsub(rs, zmul(omega, rt));
+  s.omega = omega;
+  s.rnorm2 = rn2;
+  s.pending = 1;
+  if (rn2 <= tol2 * s.bnorm2) {
+    s.active = 0;
+  } else if (s.iters >= max_it) {
+    s.status = FWI_ERR_NOT_CONVERGED;
+    s.active = 0;
+  } else if (zabs2(omega) == 0.0 || zabs2(s.rho) == 0.0 || zabs2(rho_new) == 0.0) {
+    s.status = FWI_ERR_BREAKDOWN;
+    s.active = 0;
+  } else {
+    s.beta = zmul(zdiv(rho_new, s.rho), zdiv(s.alpha, omega));
+    s.rho = rho_new;
+    s.pending = 0;  // the update is fused into the next forward row pass
+  }
+}
+
+// Active-list compaction in RHS order (one block).
+__global__ void compact_kernel(const Scal* scal, int nb, int* active, int* n_active) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int start = 0; start < nb; start += blockDim.x) {
+    const int i = start + threadIdx.x;
+    const int f = (i < nb && scal[i].active) ? 1 : 0;
+    int incl = f;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_tot[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const int nw = blockDim.x >> 5;
+      int v = (lane < nw) ? warp_tot[lane] : 0;
+      int inc = v;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += y;
+      }
+      if (lane < nw) warp_tot[lane] = inc - v;  // exclusive
+    }
+    __syncthreads();
+    if (f) active[base + warp_tot[warp] + incl - 1] = i;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) base += warp_tot[warp] + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_active = base;
+}
+
+// Final update x += alpha p + omega s for every RHS with a pending update.
+template <typename T>
+__global__ void finalize_kernel(cplx<T>* X, const cplx<T>* P, const cplx<T>* S,
+                                Scal* scal, int nb, long long N) {
+  const long long total = N * nb;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int rhs = (int)(id / N);
+    const Scal& s = scal[rhs];
+    if (!s.pending) continue;
+    const cplx<T> a = mk<T>((T)s.alpha.x, (T)s.alpha.y);
+    const cplx<T> w = mk<T>((T)s.omega.x, (T)s.omega.y);
+    X[id] = cadd(X[id], cadd(cmul(a, P[id]), cmul(w, S[id])));
+  }
+}
+
+template <typename T>
+__global__ void copy_conj_kernel(cplx<T>* dst, const cplx<T>* src, long long n, int conj) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cplx<T> v = src[i];
+    if (conj) v.y = -v.y;
+    dst[i] = v;
+  }
+}
+
+inline int blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+// Argument bundles for one batch.
+template <typename T> struct Batch {
+  fwi_ctx* c;
+  int rhs0, nb;
+  cplx<T>* X;
+  RowFwdArgs<T> rf;
+  RowInvArgs<T> ri;
+  ColArgs<T> cz, cy_fwd, cy_inv;
+};
+
+template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb) {
+  Batch<T> b{};
+  b.c = c; b.rhs0 = rhs0; b.nb = nb; b.X = X;
+  cplx<T>* R = (cplx<T>*)c->kv[0];
+  cplx<T>* RH = (cplx<T>*)c->kv[1];
+  cplx<T>* P = (cplx<T>*)c->kv[2];
+  cplx<T>* V = (cplx<T>*)c->kv[3];
+  cplx<T>* Tt = (cplx<T>*)c->kv[4];
+  RowFwdArgs<T>& r = b.rf;
+  r.m = (const cplx<T>*)c->mF; r.use_m = 1;
+  r.X = X; r.R = R; r.RH = RH; r.P = P; r.V = V; r.Tt = Tt;
+  r.plane = (cplx<T>*)c->plane1; r.tw = (const cplx<T>*)c->tw_x;
+  r.active = c->active; r.n_active = c->n_active; r.nb = nb;
+  r.scal = c->scal; r.partial = c->partial;
+  r.nx = c->nx; r.rows = c->rows; r.ntiles = c->ntiles; r.N = c->N;
+  RowInvArgs<T>& q = b.ri;
+  q.plane = (const cplx<T>*)c->plane1; q.m = (const cplx<T>*)c->mF;
+  q.X = X; q.R = R; q.RH = RH; q.P = P; q.V = V; q.Tt = Tt;
+  q.tw = (const cplx<T>*)c->tw_x;
+  q.active = c->active; q.n_active = c->n_active; q.nb = nb;
+  q.partial = c->partial; q.nx = c->nx; q.rows = c->rows; q.ntiles = c->ntiles; q.N = c->N;
+  const long long lyx = (long long)c->ly * c->lx;
+  if (c->dim == 2) {
+    ColArgs<T>& z = b.cz;
+    z.mode = C_CONV; z.in = (const cplx<T>*)c->plane1; z.out = (cplx<T>*)c->plane1;
+    z.in_rhs_stride = z.out_rhs_stride = (long long)c->rows * c->lx;
+    z.line_stride = c->lx; z.ncols = c->lx; z.nplanes = 1;
+  } else {
+    ColArgs<T>& y = b.cy_fwd;
+    y.mode = C_FWD; y.in = (const cplx<T>*)c->plane1; y.out = (cplx<T>*)c->plane2;
+    y.in_rhs_stride = (long long)c->rows * c->lx;
+    y.out_rhs_stride = (long long)c->nz * lyx;
+    y.in_plane_stride = (long long)c->ny * c->lx; y.out_plane_stride = lyx;
+    y.line_stride = c->lx; y.ncols = c->lx; y.nplanes = c->nz;
+    y.tw = (const cplx<T>*)c->tw_y;
+    ColArgs<T>& w = b.cy_inv;
+    w = y;
+    w.mode = C_INV; w.in = (const cplx<T>*)c->plane2; w.out = (cplx<T>*)c->plane1;
+    w.in_rhs_stride = y.out_rhs_stride; w.out_rhs_stride = y.in_rhs_stride;
+    w.in_plane_stride = lyx; w.out_plane_stride = (long long)c->ny * c->lx;
+    ColArgs<T>& z = b.cz;
+    z.mode = C_CONV; z.in = (const cplx<T>*)c->plane2; z.out = (cplx<T>*)c->plane2;
+    z.in_rhs_stride = z.out_rhs_stride = (long long)c->nz * lyx;
+    z.line_stride = lyx; z.ncols = (int)lyx; z.nplanes = 1;
+  }
+  for (ColArgs<T>* a : {&b.cz, &b.cy_fwd, &b.cy_inv}) {
+    a->active = c->active; a->n_active = c->n_active; a->nb = nb;
+    a->rhs0 = rhs0; a->n_elem = c->n_elem; a->freq_fixed = -1;
+  }
+  b.cz.tw = (const cplx<T>*)c->tw_z;
+  b.cz.ghat = (const cplx<T>*)c->ghat;
+  b.cz.ghat_freq_stride = (long long)c->lz * lyx;
+  return b;
+}
+
+// The column part of one operator application (between the row passes).
+template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list) {
+  fwi_ctx* c = b.c;
+  ColArgs<T> z = b.cz;
+  if (!use_list) z.active = nullptr;
+  if (c->dim == 2) return Lsop<T>::col(c->lz, z, c->stream);
+  ColArgs<T> y = b.cy_fwd, w = b.cy_inv;
+  if (!use_list) { y.active = nullptr; w.active = nullptr; }
+  cudaError_t e = Lsop<T>::col(c->ly, y, c->stream);
+  if (e == cudaSuccess) e = Lsop<T>::col(c->lz, z, c->stream);
+  if (e == cudaSuccess) e = Lsop<T>::col(c->ly, w, c->stream);
+  return e;
+}
+
+template <typename T> cudaError_t row_fwd(const Batch<T>& b, int mode, bool use_list,
+                                          const cplx<T>* in = nullptr, int conj_in = 0,
+                                          int use_m = 1) {
+  RowFwdArgs<T> r = b.rf;
+  r.mode = mode; r.in = in; r.conj_in = conj_in; r.use_m = use_m;
+  if (!use_list) r.active = nullptr;
+  return Lsop<T>::row_fwd(b.c->lx, r, b.c->stream);
+}
+
+template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_list,
+                                          const cplx<T>* in = nullptr, cplx<T>* out = nullptr,
+                                          const cplx<T>* B = nullptr, int conj_b = 0) {
+  RowInvArgs<T> q = b.ri;
+  q.mode = mode; q.in = in; q.out = out; q.B = B; q.conj_b = conj_b;
+  if (!use_list) q.active = nullptr;
+  return Lsop<T>::row_inv(b.c->lx, q, b.c->stream);
+}
+
+// One BiCGSTAB iteration body (from the column pass of the first
+// operator application to the fused update of the next iteration).
+template <typename T> cudaError_t iteration(const Batch<T>& b) {
+  fwi_ctx* c = b.c;
+  const int wb = blocks_for((long long)b.nb * 32, 256, 1 << 30);
+  const double tol2 = c->tol * c->tol;
+  cudaError_t e = columns(b, true);
+  if (e == cudaSuccess) e = row_inv(b, RI_V, true);
+  if (e == cudaSuccess) {
+    s1_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active, c->n_active);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = row_fwd(b, RF_S, true);
+  if (e == cudaSuccess) e = columns(b, true);
+  if (e == cudaSuccess) e = row_inv(b, RI_T, true);
+  if (e == cudaSuccess) {
+    s2_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active,
+                                        c->n_active, tol2, c->max_it);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, b.nb, c->active, c->n_active);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = row_fwd(b, RF_ITER, true);
+  return e;
+}
+
+constexpr int kGraphIters = 4;
+
+template <typename T>
+fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, bool warm,
+                       int rhs0, int nb) {
+  Batch<T> b = make_batch<T>(c, X, rhs0, nb);
+  const double tol2 = c->tol * c->tol;
+  const int wb = blocks_for((long long)nb * 32, 256, 1 << 30);
+  // ---- initial residual and first search direction ----
+  if (!warm) {
+    FWI_CUDA(c, row_fwd(b, RF_INIT, false, bvec, conj_b));
+    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 0, tol2);
+  } else {
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, X, 0));
+    FWI_CUDA(c, columns(b, false));
+    FWI_CUDA(c, row_inv(b, RI_R0, false, nullptr, nullptr, bvec, conj_b));
+    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 1, tol2);
+  }
+  FWI_CUDA(c, cudaGetLastError());
+  compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, nb, c->active, c->n_active);
+  FWI_CUDA(c, cudaGetLastError());
+  if (warm) FWI_CUDA(c, row_fwd(b, RF_START, true));
+  // ---- iterations: graph of kGraphIters bodies, replayed ----
+  auto key = std::make_tuple((const void*)X, rhs0, nb);
+  cudaGraphExec_t exec = nullptr;
+  auto it = c->graphs.find(key);
+  if (it != c->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t g = nullptr;
+    FWI_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = iteration(b);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "capturing the Krylov iteration");
+    FWI_CUDA(c, e2);
+    e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    FWI_CUDA(c, e);
+    c->graphs[key] = exec;
+  }
+  const int max_replays = (c->max_it + kGraphIters - 1) / kGraphIters + 1;
+  for (int rep = 0; rep < max_replays; ++rep) {
+    FWI_CUDA(c, cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int),
+                                cudaMemcpyDeviceToHost, c->stream));
+    FWI_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (*c->h_n_active == 0) break;
+    if (c->cancel.load()) return fail(c, FWI_ERR_CANCELLED, "solve cancelled");
+    FWI_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  }
+  // ---- pending updates ----
+  finalize_kernel<T><<<blocks_for(c->N * nb, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+      X, (const cplx<T>*)c->kv[2], (const cplx<T>*)c->kv[0], c->scal, nb, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+void fill_info(fwi_ctx* c, fwi_solve_info* info, int rhs0, int nb, bool first) {
+  if (!info) return;
+  if (first) {
+    info->max_iters = 0;
+    info->max_rel_resid = 0.0;
+    info->n_not_converged = 0;
+  }
+  for (int i = 0; i < nb; ++i) {
+    const Scal& s = c->h_scal[i];
+    const double rr = s.bnorm2 > 0 ? std::sqrt(s.rnorm2 / s.bnorm2) : 0.0;
+    const int g = rhs0 + i;
+    if (g < info->n_rhs) {
+      if (info->iters) info->iters[g] = s.iters;
+      if (info->rel_resid) info->rel_resid[g] = rr;
+      if (info->status) info->status[g] = s.status;
+    }
+    if (s.iters > info->max_iters) info->max_iters = s.iters;
+    if (rr > info->max_rel_resid) info->max_rel_resid = rr;
+    if (s.status != FWI_OK) info->n_not_converged += 1;
+  }
+}
+
+template <typename T>
+fwi_status solve_all(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, bool warm,
+                     fwi_solve_info* info) {
+  FWI_CUDA(c, cudaEventRecord(c->ev0, c->stream));
+  fwi_status worst = FWI_OK;
+  for (int rhs0 = 0; rhs0 < c->n_rhs; rhs0 += c->batch) {
+    const int nb = (c->n_rhs - rhs0 < c->batch) ? c->n_rhs - rhs0 : c->batch;
+    fwi_status st = solve_batch<T>(c, bvec + (long long)rhs0 * c->N, conj_b,
+                                   X + (long long)rhs0 * c->N, warm, rhs0, nb);
+    if (st != FWI_OK) return st;
+    FWI_CUDA(c, cudaMemcpyAsync(c->h_scal, c->scal, sizeof(Scal) * nb,
+                                cudaMemcpyDeviceToHost, c->stream));
+    FWI_CUDA(c, cudaStreamSynchronize(c->stream));
+    fill_info(c, info, rhs0, nb, rhs0 == 0);
+    for (int i = 0; i < nb; ++i) {
+      const int s = c->h_scal[i].status;
+      if (s != FWI_OK && (worst == FWI_OK || s == FWI_ERR_NONFINITE)) worst = (fwi_status)s;
+    }
+  }
+  FWI_CUDA(c, cudaEventRecord(c->ev1, c->stream));
+  FWI_CUDA(c, cudaEventSynchronize(c->ev1));
+  if (info) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    info->device_ms = ms;
+  }
+  if (worst != FWI_OK) {
+    const char* what = worst == FWI_ERR_NOT_CONVERGED ? "some right-hand sides hit krylov_max_it"
+                       : worst == FWI_ERR_BREAKDOWN   ? "BiCGSTAB breakdown"
+                                                      : "non-finite value in a Krylov reduction";
+    return fail(c, worst, what);
+  }
+  return FWI_OK;
+}
+
+template <typename T>
+fwi_status apply_op_t(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
+                      const void* in, void* out) {
+  if (m) {
+    fwi_status st = set_contrast(c, m);
+    if (st != FWI_OK) return st;
+  }
+  Batch<T> b = make_batch<T>(c, (cplx<T>*)c->kv[0], 0, n_rhs);
+  b.cz.freq_fixed = freq;  // every vector of the call is at frequency `freq`
+  const cplx<T>* src = (const cplx<T>*)in;
+  if (kind == 0) {  // K
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 0, 0));
+    FWI_CUDA(c, columns(b, false));
+    FWI_CUDA(c, row_inv(b, RI_K, false, nullptr, (cplx<T>*)out));
+  } else if (kind == 1) {  // A
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 0, 1));
+    FWI_CUDA(c, columns(b, false));
+    FWI_CUDA(c, row_inv(b, RI_A, false, src, (cplx<T>*)out));
+  } else {  // A^H
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 1, 0));
+    FWI_CUDA(c, columns(b, false));
+    FWI_CUDA(c, row_inv(b, RI_AH, false, src, (cplx<T>*)out));
+  }
+  return FWI_OK;
+}
+
+}  // namespace
+
+fwi_status forward_solve(fwi_ctx* c, const void* m, bool warm, fwi_solve_info* info) {
+  fwi_status st = set_contrast(c, m);
+  if (st != FWI_OK) return st;
+  st = c->fp64 ? solve_all<double>(c, (const double2*)c->p0, 0, (double2*)c->fields, warm, info)
+               : solve_all<float>(c, (const float2*)c->p0, 0, (float2*)c->fields, warm, info);
+  c->fields_valid = (st == FWI_OK || st == FWI_ERR_NOT_CONVERGED);
+  return st;
+}
+
+// Solves A y = conj(src) (conj_src = 1) or A y = src (conj_src = 0) into
+// c->lam.  The adjoint field is lambda = conj(y).
+fwi_status adjoint_solve(fwi_ctx* c, const void* m, const void* src, bool conj_src,
+                         fwi_solve_info* info) {
+  fwi_status st = set_contrast(c, m);
+  if (st != FWI_OK) return st;
+  return c->fp64 ? solve_all<double>(c, (const double2*)src, conj_src, (double2*)c->lam, false, info)
+                 : solve_all<float>(c, (const float2*)src, conj_src, (float2*)c->lam, false, info);
+}
+
+fwi_status apply_op(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
+                    const void* in, void* out) {
+  return c->fp64 ? apply_op_t<double>(c, kind, m, freq, n_rhs, in, out)
+                 : apply_op_t<float>(c, kind, m, freq, n_rhs, in, out);
+}
+
+fwi_status copy_field(fwi_ctx* c, void* dst, const void* src, long long n, int conj) {
+  const int blocks = blocks_for(n, 256, c->n_sm * 16);
+  if (c->fp64)
+    copy_conj_kernel<double><<<blocks, 256, 0, c->stream>>>((double2*)dst, (const double2*)src, n, conj);
+  else
+    copy_conj_kernel<float><<<blocks, 256, 0, c->stream>>>((float2*)dst, (const float2*)src, n, conj);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+}  // namespace fwi

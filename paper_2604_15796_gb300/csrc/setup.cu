@@ -1,0 +1,299 @@
+// Per-context precomputation (Sec. II, Sec. IV-A): the cell-integrated
+// Green's function on the doubled offset lattice and its spectrum, the
+// incident fields of the array elements, contrast conversions.
+//
+// Discretisation: pixel collocation with the Green's function integrated
+// exactly over a disc (2D) or ball (3D) of the pixel's area / volume:
+//   2D  Ghat(r>0) = (i pi a/(2k)) J1(ka) H0(kr),  Ghat(0) = (i pi a/(2k)) H1(ka) - 1/k^2,
+//       a = h / sqrt(pi), H_n = J_n + i Y_n
+//   3D  Ghat(r>0) = 4 pi (sin ka - ka cos ka)/k^3 * e^{ikr}/(4 pi r),
+//       Ghat(0) = ((1 - ika) e^{ika} - 1)/k^2,  a = h (3/(4 pi))^(1/3)
+// Bessel functions come from the CUDA math library (j0, j1, y0, y1).
+#include <cmath>
+#include <vector>
+
+#include "ctx.cuh"
+
+namespace fwi {
+
+namespace {
+
+__device__ inline double lattice_offset(int i, int n) {
+  // index i of a doubled axis of length 2n -> signed offset, NaN-free:
+  // i < n -> i, i > n -> i - 2n; i == n is flagged by the caller.
+  return (double)(i < n ? i : i - 2 * n);
+}
+
+__global__ void green_lattice_kernel(double2* lat, int nx, int ny, int nz, int dim,
+                                     double h, double k) {
+  const int lx = 2 * nx, ly = (dim == 3) ? 2 * ny : 1, lz = 2 * nz;
+  const long long total = (long long)lx * ly * lz;
+  const double PI = 3.141592653589793238462643383279502884;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(id % lx);
+    const long long rem = id / lx;
+    const int iy = (int)(rem % ly);
+    const int iz = (int)(rem / ly);
+    double2 out = make_double2(0.0, 0.0);
+    const bool half = (ix == nx) || (iz == nz) || (dim == 3 && iy == ny);
+    if (!half) {
+      const double ox = lattice_offset(ix, nx) * h;
+      const double oy = (dim == 3) ? lattice_offset(iy, ny) * h : 0.0;
+      const double oz = lattice_offset(iz, nz) * h;
+      const double r = sqrt(ox * ox + oy * oy + oz * oz);
+      if (dim == 2) {
+        const double a = h / sqrt(PI);
+        const double ka = k * a;
+        const double c = PI * a / (2.0 * k);  // Ghat = i c (...)
+        if (r > 0.0) {
+          const double j1a = j1(ka);
+          const double kr = k * r;
+          // i c J1(ka) (J0 + i Y0) = c J1(ka) (-Y0 + i J0)
+          out.x = -c * j1a * y0(kr);
+          out.y = c * j1a * j0(kr);
+        } else {
+          // i c (J1 + i Y1) - 1/k^2
+          out.x = -c * y1(ka) - 1.0 / (k * k);
+          out.y = c * j1(ka);
+        }
+      } else {
+        const double a = h * cbrt(3.0 / (4.0 * PI));
+        const double ka = k * a;
+        if (r > 0.0) {
+          const double vol = 4.0 * PI * (sin(ka) - ka * cos(ka)) / (k * k * k);
+          double s, cs;
+          sincos(k * r, &s, &cs);
+          const double g = vol / (4.0 * PI * r);
+          out.x = g * cs;
+          out.y = g * s;
+        } else {
+          double s, cs;
+          sincos(ka, &s, &cs);
+          // (1 - i ka)(cs + i s) - 1 = (cs + ka s - 1) + i (s - ka cs)
+          out.x = (cs + ka * s - 1.0) / (k * k);
+          out.y = (s - ka * cs) / (k * k);
+        }
+      }
+    }
+    lat[id] = out;
+  }
+}
+
+template <typename T>
+__global__ void scale_spectrum_kernel(cplx<T>* dst, const double2* src, long long n,
+                                      double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = mk<T>((T)(v.x * scale), (T)(v.y * scale));
+  }
+}
+
+// p0_{l,e}(x_n) = G_l(x_n, x_e): 2D (i/4) H0(k r), 3D e^{ikr}/(4 pi r).
+template <typename T>
+__global__ void incident_kernel(cplx<T>* p0, const double* elem, const double* kw,
+                                int n_elem, int n_freq, int nx, int ny, int nz,
+                                int dim, double h) {
+  const long long N = (long long)nx * ny * nz;
+  const long long total = N * n_elem * n_freq;
+  const double PI = 3.141592653589793238462643383279502884;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const long long n = id % N;
+    const long long le = id / N;
+    const int e = (int)(le % n_elem);
+    const int l = (int)(le / n_elem);
+    const int ix = (int)(n % nx);
+    const long long q = n / nx;
+    const int iy = (int)(q % ny);
+    const int iz = (int)(q / ny);
+    const double x = (ix + 0.5 - 0.5 * nx) * h;
+    const double z = iz * h;
+    double dx, dy = 0.0, dz;
+    if (dim == 2) {
+      dx = x - elem[2 * e];
+      dz = z - elem[2 * e + 1];
+    } else {
+      const double y = (iy + 0.5 - 0.5 * ny) * h;
+      dx = x - elem[3 * e];
+      dy = y - elem[3 * e + 1];
+      dz = z - elem[3 * e + 2];
+    }
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double k = kw[l];
+    double re, im;
+    if (dim == 2) {
+      re = -0.25 * y0(k * r);
+      im = 0.25 * j0(k * r);
+    } else {
+      double s, c;
+      sincos(k * r, &s, &c);
+      re = c / (4.0 * PI * r);
+      im = s / (4.0 * PI * r);
+    }
+    p0[id] = mk<T>((T)re, (T)im);
+  }
+}
+
+template <typename T>
+__global__ void convert_kernel(cplx<T>* dst, const double2* src, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[i] = mk<T>((T)src[i].x, (T)src[i].y);
+}
+
+// m = c0^2/c^2 - 1 + i alpha c0^2 / (pi c)   (Eq. 1-3, e^{-i omega t})
+__global__ void contrast_kernel(double2* m, const double* sos, const double* alpha,
+                                long long n, double c0) {
+  const double PI = 3.141592653589793238462643383279502884;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double c = sos[i];
+    double2 v;
+    v.x = c0 * c0 / (c * c) - 1.0;
+    v.y = alpha ? alpha[i] * c0 * c0 / (PI * c) : 0.0;
+    m[i] = v;
+  }
+}
+
+template <typename T>
+cudaError_t upload_twiddles(int L, void** dst) {
+  std::vector<cplx<T>> h(L);
+  for (int j = 0; j < L; ++j) {
+    const double a = -2.0 * kPi * (double)j / (double)L;
+    h[j] = mk<T>((T)std::cos(a), (T)std::sin(a));
+  }
+  cudaError_t e = cudaMalloc(dst, sizeof(cplx<T>) * L);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice);
+}
+
+inline int grid1d(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+template <typename T>
+fwi_status compute_spectra(fwi_ctx* c) {
+  const long long P = (long long)c->lx * c->ly * c->lz;
+  double2 *lat = nullptr, *A = nullptr, *B = nullptr;
+  void *tx = nullptr, *ty = nullptr, *tz = nullptr;
+  fwi_status st = FWI_OK;
+  cudaError_t e = cudaSuccess;
+  const int cap = c->n_sm * 16;
+  do {
+    if ((e = cudaMalloc(&lat, sizeof(double2) * P)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&A, sizeof(double2) * P)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&B, sizeof(double2) * P)) != cudaSuccess) break;
+    if ((e = upload_twiddles<double>(c->lx, &tx)) != cudaSuccess) break;
+    if ((e = upload_twiddles<double>(c->lz, &tz)) != cudaSuccess) break;
+    if (c->dim == 3 && (e = upload_twiddles<double>(c->ly, &ty)) != cudaSuccess) break;
+    for (int l = 0; l < c->n_freq && e == cudaSuccess; ++l) {
+      const double k = c->kwave[l];
+      green_lattice_kernel<<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+          lat, c->nx, c->ny, c->nz, c->dim, c->h, k);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+      // x lines (full, unpadded input)
+      RowFwdArgs<double> r{};
+      r.mode = RF_PLAIN; r.full = 1; r.use_m = 0; r.in = lat; r.plane = A;
+      r.tw = (const double2*)tx; r.nb = 1; r.nx = c->lx; r.rows = c->ly * c->lz;
+      r.ntiles = (r.rows + Lsop<double>::row_lines_per_cta(c->lx) - 1) /
+                 Lsop<double>::row_lines_per_cta(c->lx);
+      r.N = P;
+      if ((e = Lsop<double>::row_fwd(c->lx, r, c->stream)) != cudaSuccess) break;
+      double2* res = A;
+      if (c->dim == 3) {
+        ColArgs<double> y{};
+        y.mode = C_FWD; y.full = 1; y.in = A; y.out = B;
+        y.in_rhs_stride = y.out_rhs_stride = P;
+        y.in_plane_stride = y.out_plane_stride = (long long)c->ly * c->lx;
+        y.line_stride = c->lx; y.ncols = c->lx; y.nplanes = c->lz;
+        y.tw = (const double2*)ty; y.nb = 1; y.n_elem = 1;
+        if ((e = Lsop<double>::col(c->ly, y, c->stream)) != cudaSuccess) break;
+        res = B;
+      }
+      ColArgs<double> z{};
+      z.mode = C_FWD; z.full = 1; z.in = res; z.out = (res == A) ? B : A;
+      z.in_rhs_stride = z.out_rhs_stride = P;
+      z.in_plane_stride = z.out_plane_stride = 0;
+      z.line_stride = (long long)c->ly * c->lx; z.ncols = c->ly * c->lx; z.nplanes = 1;
+      z.tw = (const double2*)tz; z.nb = 1; z.n_elem = 1;
+      if ((e = Lsop<double>::col(c->lz, z, c->stream)) != cudaSuccess) break;
+      const double scale = k * k / (double)P;
+      scale_spectrum_kernel<T><<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+          (cplx<T>*)c->ghat + (long long)l * P, z.out, P, scale);
+      if ((e = cudaGetLastError()) != cudaSuccess) break;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  } while (0);
+  if (e != cudaSuccess) st = cuda_fail(c, e, "Green's function spectrum");
+  cudaFree(lat); cudaFree(A); cudaFree(B);
+  cudaFree(tx); cudaFree(ty); cudaFree(tz);
+  return st;
+}
+
+template <typename T>
+fwi_status setup_t(fwi_ctx* c) {
+  if (!Lsop<double>::supported(c->lx) || !Lsop<double>::supported(c->lz) ||
+      (c->dim == 3 && !Lsop<double>::supported(c->ly)))
+    return fail(c, FWI_ERR_UNSUPPORTED, "no FFT plan for the doubled grid");
+  FWI_CUDA(c, upload_twiddles<T>(c->lx, &c->tw_x));
+  FWI_CUDA(c, upload_twiddles<T>(c->lz, &c->tw_z));
+  if (c->dim == 3) FWI_CUDA(c, upload_twiddles<T>(c->ly, &c->tw_y));
+  FWI_CUDA(c, Lsop<T>::prepare(c->lx));
+  FWI_CUDA(c, Lsop<T>::prepare(c->lz));
+  if (c->dim == 3) FWI_CUDA(c, Lsop<T>::prepare(c->ly));
+  FWI_CUDA(c, Lsop<double>::prepare(c->lx));
+  FWI_CUDA(c, Lsop<double>::prepare(c->lz));
+  if (c->dim == 3) FWI_CUDA(c, Lsop<double>::prepare(c->ly));
+  fwi_status st = compute_spectra<T>(c);
+  if (st != FWI_OK) return st;
+  // incident fields
+  double *elem = nullptr, *kw = nullptr;
+  FWI_CUDA(c, cudaMalloc(&elem, sizeof(double) * c->elem.size()));
+  FWI_CUDA(c, cudaMalloc(&kw, sizeof(double) * c->kwave.size()));
+  cudaError_t e = cudaMemcpy(elem, c->elem.data(), sizeof(double) * c->elem.size(),
+                             cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(kw, c->kwave.data(), sizeof(double) * c->kwave.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const long long total = c->N * c->n_rhs;
+    incident_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
+        (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(elem);
+  cudaFree(kw);
+  if (e != cudaSuccess) return cuda_fail(c, e, "incident fields");
+  return FWI_OK;
+}
+
+template <typename T>
+fwi_status set_contrast_t(fwi_ctx* c, const void* m) {
+  convert_kernel<T><<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+      (cplx<T>*)c->mF, (const double2*)m, c->N);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+}  // namespace
+
+fwi_status setup_operator(fwi_ctx* c) {
+  return c->fp64 ? setup_t<double>(c) : setup_t<float>(c);
+}
+
+fwi_status set_contrast(fwi_ctx* c, const void* m) {
+  return c->fp64 ? set_contrast_t<double>(c, m) : set_contrast_t<float>(c, m);
+}
+
+fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m) {
+  contrast_kernel<<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+      (double2*)m, sos, alpha, c->N, c->c0);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
+}  // namespace fwi

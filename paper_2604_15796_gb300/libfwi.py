@@ -1,0 +1,283 @@
+"""Thin ctypes binding of libfwi (include/libfwi.h).
+
+The functions below carry the C names and only marshal arguments (integers,
+doubles and device pointers); every computational step runs in the CUDA
+kernels of libfwi.so.  There is no fallback: importing the binding without
+the compiled library raises.
+
+``Context`` is a convenience wrapper that owns a ``fwi_ctx`` and takes
+torch tensors (device memory and the current CUDA stream come from torch).
+"""
+import ctypes
+import os
+from ctypes import POINTER, Structure, byref, c_double, c_float, c_int, c_size_t, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfwi.so")
+
+FWI_OK = 0
+FWI_ERR_INVALID_ARG = 1
+FWI_ERR_NOMEM = 2
+FWI_ERR_CUDA = 3
+FWI_ERR_NOT_CONVERGED = 4
+FWI_ERR_BREAKDOWN = 5
+FWI_ERR_NONFINITE = 6
+FWI_ERR_CANCELLED = 7
+FWI_ERR_UNSUPPORTED = 8
+FWI_MIXED = 0
+FWI_FP64 = 1
+
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOMEM", 3: "CUDA", 4: "NOT_CONVERGED",
+                5: "BREAKDOWN", 6: "NONFINITE", 7: "CANCELLED", 8: "UNSUPPORTED"}
+
+
+class fwi_problem_desc(Structure):
+    _fields_ = [("dim", c_int), ("n", c_int * 3), ("h", c_double), ("c0", c_double),
+                ("n_elem", c_int), ("elem_pos", POINTER(c_double)), ("n_freq", c_int),
+                ("freq_hz", POINTER(c_double)), ("krylov_tol", c_double),
+                ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int)]
+
+
+class fwi_solve_info(Structure):
+    _fields_ = [("n_rhs", c_int), ("iters", POINTER(c_int)), ("rel_resid", POINTER(c_double)),
+                ("status", POINTER(c_int)), ("max_iters", c_int), ("max_rel_resid", c_double),
+                ("n_not_converged", c_int), ("device_ms", c_float)]
+
+
+class fwi_admm_params(Structure):
+    _fields_ = [("lambda_", c_double), ("rho", c_double), ("gamma", c_double),
+                ("dual_step", c_double), ("n_cg", c_int), ("m_ref", c_void_p)]
+
+
+EXPORTS = {
+    "fwi_workspace_bytes": (c_size_t, [POINTER(fwi_problem_desc)]),
+    "fwi_create": (c_int, [POINTER(fwi_problem_desc), c_void_p, POINTER(c_void_p)]),
+    "fwi_destroy": (c_int, [c_void_p]),
+    "fwi_last_error": (ctypes.c_char_p, [c_void_p]),
+    "fwi_cancel": (c_int, [c_void_p]),
+    "fwi_contrast_from_sos": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fwi_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                            POINTER(fwi_solve_info)]),
+    "fwi_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(fwi_solve_info)]),
+    "fwi_gradient": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_double),
+                             c_void_p, POINTER(fwi_solve_info), POINTER(fwi_solve_info)]),
+    "fwi_admm_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                 POINTER(fwi_admm_params), c_void_p]),
+    "fwi_apply_K": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "fwi_apply_A": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "fwi_apply_AH": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "fwi_jac_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fwi_jac_adjoint": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fwi_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libfwi.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise OSError("libfwi.so not built: run paper_2604_15796_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _bind(name):
+    def call(*args):
+        return getattr(load(), name)(*args)
+    call.__name__ = name
+    return call
+
+
+fwi_workspace_bytes = _bind("fwi_workspace_bytes")
+fwi_create = _bind("fwi_create")
+fwi_destroy = _bind("fwi_destroy")
+fwi_last_error = _bind("fwi_last_error")
+fwi_cancel = _bind("fwi_cancel")
+fwi_contrast_from_sos = _bind("fwi_contrast_from_sos")
+fwi_forward = _bind("fwi_forward")
+fwi_adjoint = _bind("fwi_adjoint")
+fwi_gradient = _bind("fwi_gradient")
+fwi_admm_tv_step = _bind("fwi_admm_tv_step")
+fwi_apply_K = _bind("fwi_apply_K")
+fwi_apply_A = _bind("fwi_apply_A")
+fwi_apply_AH = _bind("fwi_apply_AH")
+fwi_jac_forward = _bind("fwi_jac_forward")
+fwi_jac_adjoint = _bind("fwi_jac_adjoint")
+fwi_version = _bind("fwi_version")
+
+
+class FwiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libfwi {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1000,
+              max_batch=0):
+    """fwi_problem_desc from array-order ``shape`` ((Nz, Nx) or (Nz, Ny, Nx)).
+    Returns (desc, keepalive) -- keep the second item alive while desc is used."""
+    dim = len(shape)
+    elem = np.ascontiguousarray(elem, dtype=np.float64)
+    freqs = np.ascontiguousarray(freqs, dtype=np.float64)
+    d = fwi_problem_desc()
+    d.dim = dim
+    if dim == 2:
+        d.n[0], d.n[1], d.n[2] = shape[1], 1, shape[0]
+    else:
+        d.n[0], d.n[1], d.n[2] = shape[2], shape[1], shape[0]
+    d.h, d.c0 = h, c0
+    d.n_elem = elem.shape[0]
+    d.elem_pos = elem.ctypes.data_as(POINTER(c_double))
+    d.n_freq = len(freqs)
+    d.freq_hz = freqs.ctypes.data_as(POINTER(c_double))
+    d.krylov_tol, d.krylov_max_it = tol, max_it
+    d.precision, d.max_batch = precision, max_batch
+    return d, (elem, freqs)
+
+
+def _ptr(t):
+    return None if t is None else c_void_p(t.data_ptr())
+
+
+class SolveReport:
+    """Host arrays of an fwi_solve_info."""
+
+    def __init__(self, n_rhs):
+        self.iters = np.zeros(n_rhs, dtype=np.int32)
+        self.rel_resid = np.zeros(n_rhs, dtype=np.float64)
+        self.status = np.zeros(n_rhs, dtype=np.int32)
+        self.info = fwi_solve_info()
+        self.info.n_rhs = n_rhs
+        self.info.iters = self.iters.ctypes.data_as(POINTER(c_int))
+        self.info.rel_resid = self.rel_resid.ctypes.data_as(POINTER(c_double))
+        self.info.status = self.status.ctypes.data_as(POINTER(c_int))
+
+    @property
+    def device_ms(self):
+        return float(self.info.device_ms)
+
+    @property
+    def max_iters(self):
+        return int(self.info.max_iters)
+
+
+class Context:
+    """Owns one fwi_ctx.  Tensors are torch CUDA tensors (complex64 fields for
+    FWI_MIXED, complex128 for FWI_FP64; m, grad, g, u always complex128)."""
+
+    def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
+                 max_it=1000, max_batch=0, stream=None):
+        import torch
+        self.torch = torch
+        self.shape = tuple(shape)
+        self.dim = len(shape)
+        self.n = int(np.prod(shape))
+        self.n_elem = int(np.asarray(elem).shape[0])
+        self.n_freq = int(len(freqs))
+        self.n_rhs = self.n_elem * self.n_freq
+        self.precision = precision
+        self.field_dtype = torch.complex128 if precision == FWI_FP64 else torch.complex64
+        self.desc, self._keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it,
+                                          max_batch)
+        self.workspace_bytes = int(fwi_workspace_bytes(byref(self.desc)))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        handle = c_void_p()
+        st = fwi_create(byref(self.desc), c_void_p(stream.cuda_stream), byref(handle))
+        if st != FWI_OK:
+            raise FwiError(st, fwi_last_error(None).decode())
+        self.handle = handle
+
+    # -- helpers ---------------------------------------------------------
+    def _check(self, st, ok=(FWI_OK,)):
+        if st not in ok:
+            raise FwiError(st, fwi_last_error(self.handle).decode())
+        return st
+
+    def empty_fields(self):
+        return self.torch.empty((self.n_freq, self.n_elem) + self.shape,
+                                dtype=self.field_dtype, device="cuda")
+
+    def empty_data(self):
+        return self.torch.empty((self.n_freq, self.n_elem, self.n_elem),
+                                dtype=self.field_dtype, device="cuda")
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            fwi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls -----------------------------------------------------------
+    def contrast_from_sos(self, sos, alpha=None):
+        m = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
+        self._check(fwi_contrast_from_sos(self.handle, _ptr(sos), _ptr(alpha), _ptr(m)))
+        return m
+
+    def forward(self, m, fields=None, warm_start=False, data=None, allow_nonconverged=False):
+        rep = SolveReport(self.n_rhs)
+        ok = (FWI_OK, FWI_ERR_NOT_CONVERGED) if allow_nonconverged else (FWI_OK,)
+        st = fwi_forward(self.handle, _ptr(m), _ptr(fields), int(warm_start), _ptr(data),
+                         byref(rep.info))
+        self._check(st, ok)
+        rep.code = st
+        return rep
+
+    def adjoint(self, m, src, lam):
+        rep = SolveReport(self.n_rhs)
+        self._check(fwi_adjoint(self.handle, _ptr(m), _ptr(src), _ptr(lam), byref(rep.info)))
+        return rep
+
+    def gradient(self, m, d_obs, grad, data=None):
+        rf, ra = SolveReport(self.n_rhs), SolveReport(self.n_rhs)
+        mis = c_double(0.0)
+        self._check(fwi_gradient(self.handle, _ptr(m), _ptr(d_obs), _ptr(grad), byref(mis),
+                                 _ptr(data), byref(rf.info), byref(ra.info)))
+        return float(mis.value), rf, ra
+
+    def admm_tv_step(self, m, g, u, grad, lam=1e-4, rho=1e-3, gamma=1e-5, n_cg=10,
+                     dual_step=0.0, m_ref=None, sos=None):
+        p = fwi_admm_params()
+        p.lambda_, p.rho, p.gamma, p.dual_step, p.n_cg = lam, rho, gamma, dual_step, n_cg
+        p.m_ref = None if m_ref is None else m_ref.data_ptr()
+        self._check(fwi_admm_tv_step(self.handle, _ptr(m), _ptr(g), _ptr(u), _ptr(grad),
+                                     byref(p), _ptr(sos)))
+
+    def apply(self, kind, vin, freq, m=None):
+        out = self.torch.empty_like(vin)
+        nb = vin.shape[0]
+        if kind == "K":
+            st = fwi_apply_K(self.handle, freq, nb, _ptr(vin), _ptr(out))
+        elif kind == "A":
+            st = fwi_apply_A(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
+        else:
+            st = fwi_apply_AH(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
+        self._check(st)
+        return out
+
+    def jac_forward(self, a):
+        y = self.torch.empty((self.n_freq, self.n_elem, self.n_elem),
+                             dtype=self.torch.complex128, device="cuda")
+        self._check(fwi_jac_forward(self.handle, _ptr(a), _ptr(y)))
+        return y
+
+    def jac_adjoint(self, y):
+        z = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
+        self._check(fwi_jac_adjoint(self.handle, _ptr(y), _ptr(z)))
+        return z
