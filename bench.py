@@ -1,0 +1,448 @@
+"""Benchmark of the FWI hot path on one GB300 (per process).
+
+One step = one pass of the whole hot path over the batch of the workload:
+fwi_gradient (forward BiCGSTAB solves for every transmit x frequency, data,
+misfit, adjoint sources, adjoint solves, gradient assembly) followed by
+fwi_admm_tv_step (Gauss-Newton CG with implicit Jacobian products, isotropic
+shrink, dual update, SoS map).  Every step starts from the same iterate
+(m_k, g_k, u_k) so that all steps do the same work.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload thyroid256|large512|volume3d|disc64]
+
+Prints one JSON line (rank 0).  Multi-GPU: independent replicas, one per
+rank (the solves shard by right-hand side with no exchange step).
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS solves/s & gradient evals/s at rel err <=1e-4; p50/p99 recon latency"
+UNIT = "RHS solves/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(name):
+    from paper_2604_15796_gb300 import phantoms
+    return {"thyroid256": phantoms.thyroid_256, "large512": phantoms.large_512,
+            "volume3d": phantoms.volume_3d, "disc64": phantoms.disc_phantom}[name]()
+
+
+def describe(w):
+    grid = "x".join(str(s) for s in reversed(w.shape))
+    return (f"{w.name}: {grid} grid, h={w.h * 1e3:.2f} mm, {w.n_elem} elements x "
+            f"{w.n_freq} freqs ({w.n_rhs} RHS), per step 1 forward + 1 adjoint BiCGSTAB solve "
+            f"per RHS + data + gradient + ADMM-TV step (n_cg=10)")
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "jac.cu"):
+        with open(os.path.join(ROOT, "paper_2604_15796_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel, wname):
+    """DRAM bytes per launch recorded from an ncu capture in profiles/, if
+    the kernel sources have not changed since (hash match); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    pat = re.compile(r"^traffic\s+(\S+)\s+(\S+)\s+bytes_per_launch=([0-9.eE+]+)\s+"
+                     r"units_per_launch=([0-9.eE+]+)\s+src=(\w+)")
+    for line in open(path):
+        m = pat.match(line.strip())
+        if m and m.group(1) == kernel and m.group(2) == wname and \
+                m.group(5) == kernel_source_hash():
+            return float(m.group(3)), float(m.group(4))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_solves_per_s(w, budget_s=15.0, seed=0, keep=0):
+    """FP64 oracle (numpy/scipy, all host cores) on a bounded sample of the
+    workload: BiCGSTAB solves (tol 1e-10) of transmit/frequency pairs drawn
+    from the workload at the benchmark's iterate m = 0.8 m_true, until the
+    time budget is spent.  The first ``keep`` solutions and their data rows
+    are returned for the accuracy check of the GPU result."""
+    import oracle
+    from oracle import inverse, model, operator
+    prob = oracle.Problem(tuple(w.shape), w.h, w.c0, w.elem, np.asarray(w.freqs))
+    m = 0.8 * model.contrast_from_sos(w.sos, w.c0)
+    rng = np.random.default_rng(seed)
+    specs = {}
+    kept = []
+    n, t0 = 0, time.perf_counter()
+    while True:
+        l = int(rng.integers(0, w.n_freq))
+        e = int(rng.integers(0, w.n_elem))
+        if l not in specs:
+            specs[l] = operator.kernel_spectrum(prob, l)
+        sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem[[e]],
+                             np.asarray([w.freqs[l]]))
+        b = operator.incident_fields(sub)[0, 0]
+        spec = specs[l]
+        x, _, _ = operator.bicgstab(lambda v: operator.apply_A(v.reshape(prob.shape), m, prob,
+                                                              l, spec).ravel(), b.ravel(), 1e-10)
+        if len(kept) < keep:
+            subr = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]))
+            row = inverse.forward_data(m, x.reshape((1, 1) + prob.shape), subr)[0, 0]
+            kept.append((l, e, x.reshape(prob.shape), row))
+        n += 1
+        if time.perf_counter() - t0 > budget_s and n >= keep:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt, kept
+
+
+def run_reference(args, rank):
+    """Reference arm: the FP64 oracle, timed on the host cores."""
+    if rank != 0:
+        return None
+    w = workload(args.workload)
+    per_step = []
+    solves = 0
+    for i in range(args.warmup + args.steps):
+        rate, n, dt, _ = oracle_solves_per_s(w, budget_s=args.ref_step_s, seed=i)
+        if i >= args.warmup:
+            per_step.append(dt)
+            solves += n
+    total = sum(per_step)
+    value = solves / total
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (FP64 oracle)",
+            "data": "synthetic", "config": {"workload": describe(w)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{solves} FP64 BiCGSTAB solves (tol 1e-10) of random "
+                                       f"transmit/frequency pairs of the workload, "
+                                       f"~{args.ref_step_s:.0f} s per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    return line
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, samples):
+    import torch
+    from paper_2604_15796_gb300 import libfwi
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    w = workload(args.workload)
+    stream = torch.cuda.Stream()
+    peaks, peak_kind = load_peaks()
+    with torch.cuda.stream(stream):
+        ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6, stream=stream,
+                             max_batch=args.max_batch)
+        c128 = torch.complex128
+        sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
+        m_true = ctx.contrast_from_sos(sos_true)
+        m0 = (0.8 * m_true).contiguous()
+        # observed data: forward data of the true model + 2% complex noise
+        d_obs = ctx.empty_data()
+        ctx.forward(m_true, data=d_obs)
+        from paper_2604_15796_gb300 import phantoms
+        noise = phantoms.complex_normal(tuple(d_obs.shape), 4242)
+        dn = float(torch.linalg.vector_norm(d_obs).item())
+        scale = 0.02 * dn / np.sqrt(2.0 * d_obs.numel())
+        d_obs += torch.from_numpy(noise * scale).to(device="cuda", dtype=d_obs.dtype)
+        # ADMM parameters scaled to ||J^H J|| (power iteration at m0)
+        ctx.forward(m0)
+        v = torch.from_numpy(phantoms.complex_normal(w.shape, 7)).cuda()
+        nrm = 1.0
+        for _ in range(4):
+            v = v / torch.linalg.vector_norm(v)
+            v = ctx.jac_adjoint(ctx.jac_forward(v))
+            nrm = float(torch.linalg.vector_norm(v).item())
+        params = dict(lam=1e-4 * nrm, rho=1e-2 * nrm, gamma=1e-5 * nrm, n_cg=10)
+        g0, u0 = ctx.admm_init(m0)  # g0 = nabla m0, u0 = 0 (Algorithm 1)
+        m0h = m0.cpu().numpy()
+        m = torch.empty_like(m0)
+        g = torch.empty_like(g0)
+        u = torch.empty_like(u0)
+        grad = torch.empty(w.shape, dtype=c128, device="cuda")
+        sos = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+        reports = []
+
+        def step():
+            m.copy_(m0)
+            g.copy_(g0)
+            u.copy_(u0)
+            mis, rf, ra = ctx.gradient(m, d_obs, grad)
+            ctx.admm_tv_step(m, g, u, grad, sos=sos, **params)
+            reports.append((mis, rf.max_iters, ra.max_iters, float(np.mean(rf.iters)),
+                            float(np.mean(ra.iters))))
+
+        for _ in range(args.warmup):
+            step()
+        reports.clear()
+        launches0, _ = ctx.stats()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(dev) as clk:
+            e0.record(stream)
+            for _ in range(args.steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        launches1, _ = ctx.stats()
+        if world > 1:
+            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        solves = 2.0 * w.n_rhs * args.steps * world
+        value = solves / (ms / 1e3)
+
+        # ---- end to end through the C ABI with host buffers ----
+        e2e = None
+        if not args.no_e2e:
+            m_h = torch.from_numpy(m0h).pin_memory()
+            d_h = d_obs.cpu().pin_memory()
+            g_h = g0.cpu().pin_memory()
+            u_h = u0.cpu().pin_memory()
+            sos_h = torch.empty(w.shape, dtype=torch.float64).pin_memory()
+            mo_h = torch.empty_like(m_h).pin_memory()
+            d_dev = torch.empty_like(d_obs)
+            ke = max(3, min(args.steps, 20))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(ke):
+                m.copy_(m_h, non_blocking=True)
+                d_dev.copy_(d_h, non_blocking=True)
+                g.copy_(g_h, non_blocking=True)
+                u.copy_(u_h, non_blocking=True)
+                ctx.gradient(m, d_dev, grad)
+                ctx.admm_tv_step(m, g, u, grad, sos=sos, **params)
+                sos_h.copy_(sos, non_blocking=True)
+                mo_h.copy_(m, non_blocking=True)
+                stream.synchronize()
+            dt = time.perf_counter() - t0
+            h2d = (m_h.numel() * 16 + d_h.numel() * d_h.element_size()
+                   + (g_h.numel() + u_h.numel()) * 16)
+            d2h = sos_h.numel() * 8 + mo_h.numel() * 16
+            e2e = {"value": 2.0 * w.n_rhs * ke * world / dt, "unit": UNIT,
+                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                   "steps": ke, "ms_per_step": 1e3 * dt / ke}
+
+        # ---- live per-kernel timing (CUDA events, profiling mode) ----
+        ctx.reset_stats()
+        ctx.set_profiling(True)
+        step()
+        ctx.set_profiling(False)
+        _, kst = ctx.stats()
+        torch.cuda.synchronize()
+
+        # ---- sampled error against the FP64 oracle solutions of the CPU leg ----
+        err = sampled_error(ctx, m0, samples) if samples else None
+
+    tot_ms = sum(k["ms"] for k in kst.values())
+    op_classes = [k for k in kst if k.startswith(("row_", "col_"))]
+    dominant = max(kst, key=lambda k: kst[k]["ms"])
+    roof = roofline(dominant, kst[dominant], peaks, peak_kind, w.name, clk.summary())
+    share = {k: round(v["ms"] / tot_ms, 4) for k, v in sorted(kst.items(),
+                                                             key=lambda kv: -kv[1]["ms"])}
+    op_ms = sum(kst[k]["ms"] for k in op_classes)
+    op_bytes = sum(kst[k]["bytes"] for k in op_classes)
+    its = np.array([r[1:] for r in reports])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 fields / FP64 Krylov scalars", "data": "synthetic",
+        "config": {"workload": describe(w), "l2": "inputs larger than L2 (fields "
+                   f"{w.n_rhs * w.n * 8 / 1e6:.0f} MB per array)",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "krylov_tol": 1e-6, "admm": {k: v for k, v in params.items()}},
+        "gradient_evals_per_s": args.steps * world / (ms / 1e3),
+        "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
+                           "fwd_mean": float(its[:, 2].mean()),
+                           "adj_mean": float(its[:, 3].mean())},
+        "rel_err_vs_oracle": err,
+        "roofline": roof,
+        "operator_passes": {"ms": op_ms, "achieved_gbs": op_bytes / (op_ms * 1e6) if op_ms else None,
+                            "frac_of_hbm": (op_bytes / (op_ms * 1e6)) / peaks["hbm_gbs"]
+                            if op_ms else None},
+        "kernel_time_share": share,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+    }
+    ctx.close()
+    return line
+
+
+def roofline(name, k, peaks, peak_kind, wname, clocks):
+    avg_ms = k["ms"] / k["launches"]
+    rec = recorded_traffic(name, wname)
+    if k["bytes"] > 0 and (name.startswith(("row_", "col_", "gradient")) or k["flops"] == 0):
+        achieved = k["bytes"] / k["launches"] / (avg_ms * 1e6)
+        peak = peaks["hbm_gbs"]
+        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+               "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"}
+    else:
+        achieved = k["flops"] / k["launches"] / (avg_ms * 1e9)
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
+        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak,
+               "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+    out.update({"kernel": name, "launches": k["launches"], "avg_launch_ms": avg_ms,
+                "algorithmic_bytes_per_launch": k["bytes"] / k["launches"],
+                "traffic": None})
+    if rec is not None:
+        bpl, units = rec
+        out["traffic"] = bpl
+        out["traffic_units_per_launch"] = units
+    return out
+
+
+def sampled_error(ctx, m0, samples):
+    """Relative L2 error of sampled forward fields and of their data rows
+    against the FP64 oracle solutions (BiCGSTAB tol 1e-10) computed in the
+    CPU-baseline leg, at full size."""
+    import torch
+    fields = ctx.empty_fields()
+    data = ctx.empty_data()
+    ctx.forward(m0, fields=fields, data=data)
+    torch.cuda.synchronize()
+    errs_f, errs_d = [], []
+    for l, e, ref, refd in samples:
+        got = fields[l, e].cpu().numpy()
+        errs_f.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        gotd = data[l, e].cpu().numpy()
+        errs_d.append(float(np.linalg.norm(gotd - refd) / np.linalg.norm(refd)))
+    return {"fields_max": max(errs_f), "data_row_max": max(errs_d),
+            "samples": len(samples), "tolerance": 1e-4}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="thyroid256",
+                    choices=["thyroid256", "large512", "volume3d", "disc64"])
+    ap.add_argument("--max-batch", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--check-samples", type=int, default=2)
+    ap.add_argument("--ref-step-s", type=float, default=2.0)
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group(
+            "nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0"))))
+    cpu = None
+    samples = []
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # oracle timed on the host cores before the GPU work starts
+        w = workload(args.workload)
+        rate, n, dt, samples = oracle_solves_per_s(w, budget_s=args.cpu_budget_s,
+                                                   keep=args.check_samples)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} FP64 BiCGSTAB solves (tol 1e-10) of random transmit/frequency "
+                         f"pairs of {w.name}, {dt:.1f} s, scipy.fft over all host cores"}
+    line = run_ours(args, rank, world, samples)
+    if rank == 0:
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,10 @@ FWI_API fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u,
                             const void* grad, const fwi_admm_params* p,
                             double* sos_out);
 
+/* ADMM initialisation (Algorithm 1): g = nabla m0, u = 0.
+   m0: dev c128 [N]; g, u: dev c128 [dim][N] (out). */
+FWI_API fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u);
+
 /* Single operator applications (Sec. IV-A) on n_rhs vectors at frequency
    index freq: out = K in, A in = in - K(m in), or A^H in
    = in - conj(m) K^H in.  in, out: dev cF [n_rhs][N] (must not alias);
@@ -201,6 +205,29 @@ FWI_API fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs
    J^H); z: dev c128 [N] (out). */
 FWI_API fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y);
 FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
+
+/* ---- Instrumentation (no counterpart in the paper) ----------------------
+   Kernel launch counting is always on.  With profiling on, the Krylov
+   iterations run without CUDA graphs and every kernel launch of the
+   library is bracketed by CUDA events on the context stream; durations,
+   launch counts and algorithmic bytes (operator passes) or flops
+   (contractions) are accumulated per kernel class. */
+#define FWI_MAX_KERNEL_STATS 24
+typedef struct fwi_kernel_stat {
+  char name[40];       /* kernel class, e.g. "col_conv" */
+  double ms;           /* summed device time (profiling mode) */
+  long long launches;  /* launches timed */
+  double bytes;        /* algorithmic HBM bytes of those launches */
+  double flops;        /* algorithmic flops of those launches */
+} fwi_kernel_stat;
+typedef struct fwi_stats {
+  long long kernel_launches;  /* kernels launched so far (graph nodes counted) */
+  int n_kernel_stats;
+  fwi_kernel_stat kernels[FWI_MAX_KERNEL_STATS];
+} fwi_stats;
+FWI_API fwi_status fwi_set_profiling(fwi_ctx* ctx, int on);
+FWI_API fwi_status fwi_get_stats(const fwi_ctx* ctx, fwi_stats* out);
+FWI_API fwi_status fwi_reset_stats(fwi_ctx* ctx);
 
 /* Library version string. */
 FWI_API const char* fwi_version(void);

@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include "ctx.cuh"
+#include "prof.cuh"
 
 namespace fwi {
 
@@ -214,12 +215,36 @@ __global__ void shrink_dual_kernel(double2* g, double2* u, const double2* m, dou
   }
 }
 
+// g_q = (nabla m)_q ; u_q = 0
+__global__ void admm_init_kernel(double2* g, double2* u, const double2* m, Grid3 G, int dim) {
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N;
+       n += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    coords(G, n, ix, iy, iz);
+    for (int q = 0; q < dim; ++q) {
+      long long s; int i, nq;
+      axis(G, dim, q, ix, iy, iz, s, i, nq);
+      g[q * G.N + n] = (i < nq - 1) ? m[n + s] - m[n] : z2(0.0, 0.0);
+      u[q * G.N + n] = z2(0.0, 0.0);
+    }
+  }
+}
+
 inline int blocks_for(long long n, int threads, int cap) {
   long long b = (n + threads - 1) / threads;
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 }  // namespace
+
+fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u) {
+  Grid3 G{c->nx, c->ny, c->nz, c->N};
+  Prof pf(c, KC_ADMM);
+  admm_init_kernel<<<blocks_for(c->N, 256, kRedBlocks), 256, 0, c->stream>>>(
+      (double2*)g, (double2*)u, (const double2*)m0, G, c->dim);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
 
 fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv,
                      const fwi_admm_params* p, double* sos) {
@@ -243,31 +268,61 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   double2* w = c->vD[0];
   cudaStream_t s = c->stream;
   const double rho = p->rho, gamma = p->gamma;
-  w_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(w, g, u, m, G, dim);
+  {
+    Prof pf(c, KC_ADMM);
+    w_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(w, g, u, m, G, dim);
+  }
   FWI_CUDA(c, cudaGetLastError());
-  rhs_kernel<<<nb, 256, 0, s>>>(b, x, r, d, grad, w, m, (const double2*)p->m_ref, rho, gamma,
-                                G, dim, part);
+  {
+    Prof pf(c, KC_ADMM);
+    rhs_kernel<<<nb, 256, 0, s>>>(b, x, r, d, grad, w, m, (const double2*)p->m_ref, rho, gamma,
+                                  G, dim, part);
+  }
   FWI_CUDA(c, cudaGetLastError());
-  cg_init_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+  {
+    Prof pf(c, KC_ADMM);
+    cg_init_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+  }
   FWI_CUDA(c, cudaGetLastError());
   for (int it = 0; it < p->n_cg; ++it) {
     fwi_status st = jac_forward(c, d, c->dres);
     if (st != FWI_OK) return st;
     st = jac_adjoint(c, c->dres, z);
     if (st != FWI_OK) return st;
-    q_kernel<<<nb, 256, 0, s>>>(q, z, d, rho, gamma, G, dim, part);
+    {
+      Prof pf(c, KC_ADMM);
+      q_kernel<<<nb, 256, 0, s>>>(q, z, d, rho, gamma, G, dim, part);
+    }
     FWI_CUDA(c, cudaGetLastError());
-    cg_alpha_scalar<<<1, 1, 0, s>>>(sc, part, nb);
-    xr_kernel<<<nb, 256, 0, s>>>(x, r, d, q, sc, c->N, part);
-    cg_beta_scalar<<<1, 1, 0, s>>>(sc, part, nb);
-    d_kernel<<<nb, 256, 0, s>>>(d, r, sc, c->N);
+    {
+      Prof pf(c, KC_ADMM);
+      cg_alpha_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+    }
+    {
+      Prof pf(c, KC_ADMM);
+      xr_kernel<<<nb, 256, 0, s>>>(x, r, d, q, sc, c->N, part);
+    }
+    {
+      Prof pf(c, KC_ADMM);
+      cg_beta_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+    }
+    {
+      Prof pf(c, KC_ADMM);
+      d_kernel<<<nb, 256, 0, s>>>(d, r, sc, c->N);
+    }
     FWI_CUDA(c, cudaGetLastError());
   }
-  add_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(m, x, c->N);
+  {
+    Prof pf(c, KC_ADMM);
+    add_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(m, x, c->N);
+  }
   const double tau = p->lambda / p->rho;
   const double step = p->dual_step > 0.0 ? p->dual_step : p->rho;
-  shrink_dual_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(g, u, m, sos, tau, step, c->c0,
-                                                             G, dim);
+  {
+    Prof pf(c, KC_ADMM);
+    shrink_dual_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(g, u, m, sos, tau, step, c->c0,
+                                                               G, dim);
+  }
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
 }

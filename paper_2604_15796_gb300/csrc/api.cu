@@ -6,6 +6,7 @@
 #include <string>
 
 #include "ctx.cuh"
+#include "prof.cuh"
 
 namespace fwi {
 
@@ -110,7 +111,9 @@ static void release(fwi_ctx* c) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(c->device);
-  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  prof_flush(c);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
@@ -331,6 +334,13 @@ fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void*
   return FWI_OK;
 }
 
+fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m0 || !g || !u) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
+  ctx->err.clear();
+  return admm_init(ctx, m0, g, u);
+}
+
 static fwi_status apply_common(fwi_ctx* ctx, int kind, const void* m, int freq, int n_rhs,
                                const void* in, void* out) {
   if (!ctx) return FWI_ERR_INVALID_ARG;
@@ -368,6 +378,40 @@ fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
   ctx->err.clear();
   return jac_adjoint(ctx, (const double2*)y, (double2*)z);
+}
+
+fwi_status fwi_set_profiling(fwi_ctx* ctx, int on) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  ctx->profiling = (on != 0);
+  return FWI_OK;
+}
+
+fwi_status fwi_get_stats(const fwi_ctx* ctx, fwi_stats* out) {
+  if (!ctx || !out) return FWI_ERR_INVALID_ARG;
+  prof_flush(const_cast<fwi_ctx*>(ctx));
+  std::memset(out, 0, sizeof(*out));
+  out->kernel_launches = ctx->launches;
+  int n = 0;
+  for (int k = 0; k < KC_COUNT && n < FWI_MAX_KERNEL_STATS; ++k) {
+    const auto& s = ctx->kstats[k];
+    if (s.launches == 0) continue;
+    fwi_kernel_stat& o = out->kernels[n++];
+    std::strncpy(o.name, kclass_name(k), sizeof(o.name) - 1);
+    o.ms = s.ms;
+    o.launches = s.launches;
+    o.bytes = s.bytes;
+    o.flops = s.flops;
+  }
+  out->n_kernel_stats = n;
+  return FWI_OK;
+}
+
+fwi_status fwi_reset_stats(fwi_ctx* ctx) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  prof_flush(ctx);
+  ctx->launches = 0;
+  for (auto& s : ctx->kstats) s = fwi_ctx::KStat{};
+  return FWI_OK;
 }
 
 }  // extern "C"

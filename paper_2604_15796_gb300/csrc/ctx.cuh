@@ -61,8 +61,20 @@ struct fwi_ctx {
   double* h_red = nullptr;          // pinned host mirror
   int red_n = 0;
   bool fields_valid = false;
-  // graphs keyed by (solution pointer, batch start, batch size)
-  std::map<std::tuple<const void*, int, int>, cudaGraphExec_t> graphs;
+  // graphs keyed by (solution pointer, batch start, batch size), with the
+  // number of kernel nodes each replay launches
+  struct GraphRec { cudaGraphExec_t exec; long long nodes; };
+  std::map<std::tuple<const void*, int, int>, GraphRec> graphs;
+  // instrumentation (launch counts always; event timing when profiling)
+  long long launches = 0;
+  bool capturing = false;
+  long long capture_nodes = 0;
+  bool profiling = false;
+  struct KStat { double ms = 0, bytes = 0, flops = 0; long long launches = 0; };
+  KStat kstats[32];
+  struct Pending { int cls; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::atomic<bool> cancel{false};
   std::string err;
@@ -88,6 +100,7 @@ fwi_status adjoint_sources_conj(fwi_ctx* c, void* out);
 fwi_status assemble_gradient(fwi_ctx* c, void* grad);
 fwi_status jac_forward(fwi_ctx* c, const void* a_c128, double2* y);
 fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z);
+fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u);
 fwi_status admm_step(fwi_ctx* c, void* m, void* g, void* u, const void* grad,
                      const fwi_admm_params* p, double* sos);
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m);

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "prof.cuh"
 
 namespace fwi {
 
@@ -336,12 +337,20 @@ template <typename T> struct Jac {
     long long chunk = (c->N + split - 1) / split;
     chunk = ((chunk + KC - 1) / KC) * KC;
     dim3 grid(split, nbe * nbe, c->n_freq);
-    contract_kernel<T><<<grid, 256, 0, c->stream>>>(X, a, Q, (cplx<T>*)c->jsplit, c->n_elem,
-                                                    c->N, c->n_freq, chunk);
+    const double fe = (double)c->n_freq * c->n_elem * c->N;
+    {
+      Prof p(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(cplx<T>),
+             8.0 * fe * c->n_elem);
+      contract_kernel<T><<<grid, 256, 0, c->stream>>>(X, a, Q, (cplx<T>*)c->jsplit, c->n_elem,
+                                                      c->N, c->n_freq, chunk);
+    }
     FWI_CUDA(c, cudaGetLastError());
     const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
-    contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-        Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red);
+    {
+      Prof p(c, KC_MISC);
+      contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+          Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red);
+    }
     FWI_CUDA(c, cudaGetLastError());
     return FWI_OK;
   }
@@ -364,6 +373,7 @@ template <typename T> static fwi_status project_data_t(fwi_ctx* c, void* data_ou
   if (st != FWI_OK) return st;
   if (data_out) {
     const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
+    Prof p(c, KC_MISC);
     to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
         (cplx<T>*)data_out, c->dres, nd);
     FWI_CUDA(c, cudaGetLastError());
@@ -379,8 +389,11 @@ fwi_status project_data(fwi_ctx* c, const void* m, void* data_out) {
 template <typename T> static fwi_status residual_t(fwi_ctx* c, const void* d_obs, double* misfit) {
   const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
   // c->dres holds F(m); overwrite with r = F(m) - d_obs, conj(r) into dF
-  residual_kernel<T><<<kMisfitBlocks, 256, 0, c->stream>>>(
-      c->dres, (cplx<T>*)c->dF, c->dres, (const cplx<T>*)d_obs, nd, misfit_parts(c));
+  {
+    Prof p(c, KC_MISC);
+    residual_kernel<T><<<kMisfitBlocks, 256, 0, c->stream>>>(
+        c->dres, (cplx<T>*)c->dF, c->dres, (const cplx<T>*)d_obs, nd, misfit_parts(c));
+  }
   FWI_CUDA(c, cudaGetLastError());
   if (misfit) {
     FWI_CUDA(c, cudaMemcpyAsync(c->h_red, misfit_parts(c), sizeof(double) * kMisfitBlocks,
@@ -402,6 +415,8 @@ template <typename T> static fwi_status adjoint_sources_t(fwi_ctx* c, void* out)
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
   dim3 grid((unsigned)((c->N + TB - 1) / TB), (c->n_elem + TB - 1) / TB, c->n_freq);
+  const double fe = (double)c->n_freq * c->n_elem * c->N;
+  Prof p(c, KC_MIX_SOURCES, 2.0 * fe * sizeof(cplx<T>), 8.0 * fe * c->n_elem);
   mix_kernel<T, false><<<grid, 256, 0, c->stream>>>(
       (const cplx<T>*)c->dF, (const cplx<T>*)c->p0, 0, nullptr, (cplx<T>*)out, c->red,
       c->n_elem, c->N);
@@ -419,9 +434,13 @@ template <typename T> static fwi_status gradient_t(fwi_ctx* c, void* grad) {
   const int per = (c->n_rhs + ns - 1) / ns;
   double2* part = (double2*)c->jsplit;  // needs ns * N doubles2 (checked at create)
   dim3 grid(blocks_for(c->N, 256, 1 << 20), ns);
-  grad_partial_kernel<T><<<grid, 256, 0, c->stream>>>(part, (const cplx<T>*)c->fields,
-                                                      (const cplx<T>*)c->lam, c->n_rhs, per, c->N);
+  {
+    Prof p(c, KC_GRADIENT, 2.0 * c->n_rhs * c->N * sizeof(cplx<T>), 8.0 * c->n_rhs * c->N);
+    grad_partial_kernel<T><<<grid, 256, 0, c->stream>>>(
+        part, (const cplx<T>*)c->fields, (const cplx<T>*)c->lam, c->n_rhs, per, c->N);
+  }
   FWI_CUDA(c, cudaGetLastError());
+  Prof p(c, KC_MISC);
   grad_reduce_kernel<<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
       (double2*)grad, part, ns, c->N);
   FWI_CUDA(c, cudaGetLastError());
@@ -436,8 +455,11 @@ fwi_status assemble_gradient(fwi_ctx* c, void* grad) {
 template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a, double2* y) {
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
-  to_field_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-      (cplx<T>*)c->aF, (const double2*)a, c->N);
+  {
+    Prof p(c, KC_MISC);
+    to_field_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        (cplx<T>*)c->aF, (const double2*)a, c->N);
+  }
   FWI_CUDA(c, cudaGetLastError());
   return Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
                           (const cplx<T>*)c->fields, y);
@@ -452,15 +474,23 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
   const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
-  to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-      (cplx<T>*)c->dF, y, nd);
+  {
+    Prof p(c, KC_MISC);
+    to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        (cplx<T>*)c->dF, y, nd);
+  }
   FWI_CUDA(c, cudaGetLastError());
   const int nbe = (c->n_elem + TB - 1) / TB;
   dim3 grid((unsigned)((c->N + TB - 1) / TB), nbe, c->n_freq);
-  mix_kernel<T, true><<<grid, 256, 0, c->stream>>>(
-      (const cplx<T>*)c->dF, (const cplx<T>*)c->fields, 1, (const cplx<T>*)c->fields,
-      (cplx<T>*)c->zpart, c->red, c->n_elem, c->N);
+  {
+    const double fe = (double)c->n_freq * c->n_elem * c->N;
+    Prof p(c, KC_MIX_JH, 2.0 * fe * sizeof(cplx<T>), 8.0 * fe * c->n_elem + 8.0 * fe);
+    mix_kernel<T, true><<<grid, 256, 0, c->stream>>>(
+        (const cplx<T>*)c->dF, (const cplx<T>*)c->fields, 1, (const cplx<T>*)c->fields,
+        (cplx<T>*)c->zpart, c->red, c->n_elem, c->N);
+  }
   FWI_CUDA(c, cudaGetLastError());
+  Prof p(c, KC_MISC);
   sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
       z, (const cplx<T>*)c->zpart, c->n_freq * nbe, c->N, 0);
   FWI_CUDA(c, cudaGetLastError());

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "prof.cuh"
 
 namespace fwi {
 
@@ -287,63 +288,124 @@ template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int 
   return b;
 }
 
+// Algorithmic HBM bytes of one pass for one right-hand side: every vector
+// and plane element the pass must read or write once.
+template <typename T> double pass_bytes(const fwi_ctx* c, int kind) {
+  const double N = (double)c->N, e = (double)sizeof(cplx<T>);
+  const double p1 = (double)c->rows * c->lx;
+  const double p2 = (c->dim == 3) ? (double)c->nz * c->ly * c->lx : 0.0;
+  switch (kind) {
+    case KC_ROW_FWD_INIT: return (5 * N + p1) * e;   // b -> x, r, rhat, p; plane
+    case KC_ROW_FWD_ITER: return (8 * N + p1) * e;   // x p s t v -> x r p; plane
+    case KC_ROW_FWD_S: return (3 * N + p1) * e;      // r v -> s; plane
+    case KC_ROW_FWD_PLAIN: return (N + p1) * e;
+    case KC_COL_CONV: return (c->dim == 2 ? 2 * p1 : 2 * p2) * e;
+    case KC_COL_FWD:
+    case KC_COL_INV: return (p1 + p2) * e;
+    case KC_ROW_INV_V:                               // plane p rhat -> v
+    case KC_ROW_INV_T: return (3 * N + p1) * e;      // plane s rhat -> t
+    default: return 0.0;
+  }
+}
+
+// Ghat reads of one convolution launch (once per frequency).
+template <typename T> double ghat_bytes(const fwi_ctx* c) {
+  return (double)c->n_freq * c->lx * c->ly * c->lz * sizeof(cplx<T>);
+}
+
 // The column part of one operator application (between the row passes).
-template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list) {
+// `units`: right-hand sides the launch processes (for the byte count).
+template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list, double units) {
   fwi_ctx* c = b.c;
   ColArgs<T> z = b.cz;
   if (!use_list) z.active = nullptr;
-  if (c->dim == 2) return Lsop<T>::col(c->lz, z, c->stream);
+  if (c->dim == 2) {
+    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
+    return Lsop<T>::col(c->lz, z, c->stream);
+  }
   ColArgs<T> y = b.cy_fwd, w = b.cy_inv;
   if (!use_list) { y.active = nullptr; w.active = nullptr; }
-  cudaError_t e = Lsop<T>::col(c->ly, y, c->stream);
-  if (e == cudaSuccess) e = Lsop<T>::col(c->lz, z, c->stream);
-  if (e == cudaSuccess) e = Lsop<T>::col(c->ly, w, c->stream);
+  cudaError_t e;
+  {
+    Prof p(c, KC_COL_FWD, units * pass_bytes<T>(c, KC_COL_FWD));
+    e = Lsop<T>::col(c->ly, y, c->stream);
+  }
+  if (e == cudaSuccess) {
+    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
+    e = Lsop<T>::col(c->lz, z, c->stream);
+  }
+  if (e == cudaSuccess) {
+    Prof p(c, KC_COL_INV, units * pass_bytes<T>(c, KC_COL_INV));
+    e = Lsop<T>::col(c->ly, w, c->stream);
+  }
   return e;
 }
 
 template <typename T> cudaError_t row_fwd(const Batch<T>& b, int mode, bool use_list,
-                                          const cplx<T>* in = nullptr, int conj_in = 0,
-                                          int use_m = 1) {
+                                          double units, const cplx<T>* in = nullptr,
+                                          int conj_in = 0, int use_m = 1) {
   RowFwdArgs<T> r = b.rf;
   r.mode = mode; r.in = in; r.conj_in = conj_in; r.use_m = use_m;
   if (!use_list) r.active = nullptr;
+  const int k = mode == RF_INIT ? KC_ROW_FWD_INIT : mode == RF_ITER ? KC_ROW_FWD_ITER
+              : mode == RF_S ? KC_ROW_FWD_S : KC_ROW_FWD_PLAIN;
+  Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
   return Lsop<T>::row_fwd(b.c->lx, r, b.c->stream);
 }
 
 template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_list,
-                                          const cplx<T>* in = nullptr, cplx<T>* out = nullptr,
-                                          const cplx<T>* B = nullptr, int conj_b = 0) {
+                                          double units, const cplx<T>* in = nullptr,
+                                          cplx<T>* out = nullptr, const cplx<T>* B = nullptr,
+                                          int conj_b = 0) {
   RowInvArgs<T> q = b.ri;
   q.mode = mode; q.in = in; q.out = out; q.B = B; q.conj_b = conj_b;
   if (!use_list) q.active = nullptr;
+  const int k = mode == RI_V ? KC_ROW_INV_V : mode == RI_T ? KC_ROW_INV_T : KC_ROW_INV_OTHER;
+  Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
   return Lsop<T>::row_inv(b.c->lx, q, b.c->stream);
+}
+
+// Host copy of the active count (profiling mode only: synchronises).
+inline int read_active(fwi_ctx* c) {
+  if (cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
+    return 0;
+  cudaStreamSynchronize(c->stream);
+  return *c->h_n_active;
 }
 
 // One BiCGSTAB iteration body (from the column pass of the first
 // operator application to the fused update of the next iteration).
-template <typename T> cudaError_t iteration(const Batch<T>& b) {
+// `units`: active right-hand sides (byte accounting in profiling mode).
+template <typename T> cudaError_t iteration(const Batch<T>& b, double units) {
   fwi_ctx* c = b.c;
   const int wb = blocks_for((long long)b.nb * 32, 256, 1 << 30);
   const double tol2 = c->tol * c->tol;
-  cudaError_t e = columns(b, true);
-  if (e == cudaSuccess) e = row_inv(b, RI_V, true);
+  cudaError_t e = columns(b, true, units);
+  if (e == cudaSuccess) e = row_inv(b, RI_V, true, units);
   if (e == cudaSuccess) {
+    Prof p(c, KC_KRYLOV_SCALAR);
     s1_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active, c->n_active);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = row_fwd(b, RF_S, true);
-  if (e == cudaSuccess) e = columns(b, true);
-  if (e == cudaSuccess) e = row_inv(b, RI_T, true);
+  if (e == cudaSuccess) e = row_fwd(b, RF_S, true, units);
+  if (e == cudaSuccess) e = columns(b, true, units);
+  if (e == cudaSuccess) e = row_inv(b, RI_T, true, units);
   if (e == cudaSuccess) {
+    Prof p(c, KC_KRYLOV_SCALAR);
     s2_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active,
                                         c->n_active, tol2, c->max_it);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
+    Prof p(c, KC_KRYLOV_SCALAR);
     compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, b.nb, c->active, c->n_active);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = row_fwd(b, RF_ITER, true);
+  if (e == cudaSuccess) {
+    const double u2 = (c->profiling && !c->capturing) ? (double)read_active(c) : units;
+    e = row_fwd(b, RF_ITER, true, u2);
+  }
   return e;
 }
 
@@ -357,49 +419,76 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
   const int wb = blocks_for((long long)nb * 32, 256, 1 << 30);
   // ---- initial residual and first search direction ----
   if (!warm) {
-    FWI_CUDA(c, row_fwd(b, RF_INIT, false, bvec, conj_b));
+    FWI_CUDA(c, row_fwd(b, RF_INIT, false, nb, bvec, conj_b));
+    Prof p(c, KC_KRYLOV_SCALAR);
     s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 0, tol2);
   } else {
-    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, X, 0));
-    FWI_CUDA(c, columns(b, false));
-    FWI_CUDA(c, row_inv(b, RI_R0, false, nullptr, nullptr, bvec, conj_b));
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, nb, X, 0));
+    FWI_CUDA(c, columns(b, false, nb));
+    FWI_CUDA(c, row_inv(b, RI_R0, false, nb, nullptr, nullptr, bvec, conj_b));
+    Prof p(c, KC_KRYLOV_SCALAR);
     s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 1, tol2);
   }
   FWI_CUDA(c, cudaGetLastError());
-  compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, nb, c->active, c->n_active);
+  {
+    Prof p(c, KC_KRYLOV_SCALAR);
+    compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, nb, c->active, c->n_active);
+  }
   FWI_CUDA(c, cudaGetLastError());
-  if (warm) FWI_CUDA(c, row_fwd(b, RF_START, true));
-  // ---- iterations: graph of kGraphIters bodies, replayed ----
-  auto key = std::make_tuple((const void*)X, rhs0, nb);
-  cudaGraphExec_t exec = nullptr;
-  auto it = c->graphs.find(key);
-  if (it != c->graphs.end()) {
-    exec = it->second;
-  } else {
-    cudaGraph_t g = nullptr;
-    FWI_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaSuccess;
-    for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = iteration(b);
-    cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-    if (e != cudaSuccess) return cuda_fail(c, e, "capturing the Krylov iteration");
-    FWI_CUDA(c, e2);
-    e = cudaGraphInstantiate(&exec, g, 0);
-    cudaGraphDestroy(g);
-    FWI_CUDA(c, e);
-    c->graphs[key] = exec;
+  if (warm) {
+    const double u = c->profiling ? (double)read_active(c) : nb;
+    FWI_CUDA(c, row_fwd(b, RF_START, true, u));
   }
   const int max_replays = (c->max_it + kGraphIters - 1) / kGraphIters + 1;
-  for (int rep = 0; rep < max_replays; ++rep) {
-    FWI_CUDA(c, cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int),
-                                cudaMemcpyDeviceToHost, c->stream));
-    FWI_CUDA(c, cudaStreamSynchronize(c->stream));
-    if (*c->h_n_active == 0) break;
-    if (c->cancel.load()) return fail(c, FWI_ERR_CANCELLED, "solve cancelled");
-    FWI_CUDA(c, cudaGraphLaunch(exec, c->stream));
+  if (c->profiling) {
+    // eager iterations, every pass bracketed by events
+    for (int it = 0; it < c->max_it + 1; ++it) {
+      const int na = read_active(c);
+      if (na == 0) break;
+      if (c->cancel.load()) return fail(c, FWI_ERR_CANCELLED, "solve cancelled");
+      FWI_CUDA(c, iteration(b, (double)na));
+      prof_flush(c);
+    }
+  } else {
+    // ---- iterations: graph of kGraphIters bodies, replayed ----
+    auto key = std::make_tuple((const void*)X, rhs0, nb);
+    fwi_ctx::GraphRec rec{nullptr, 0};
+    auto it = c->graphs.find(key);
+    if (it != c->graphs.end()) {
+      rec = it->second;
+    } else {
+      cudaGraph_t g = nullptr;
+      FWI_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      c->capturing = true;
+      c->capture_nodes = 0;
+      cudaError_t e = cudaSuccess;
+      for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = iteration(b, nb);
+      c->capturing = false;
+      cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(c, e, "capturing the Krylov iteration");
+      FWI_CUDA(c, e2);
+      e = cudaGraphInstantiate(&rec.exec, g, 0);
+      cudaGraphDestroy(g);
+      FWI_CUDA(c, e);
+      rec.nodes = c->capture_nodes;
+      c->graphs[key] = rec;
+    }
+    for (int rep = 0; rep < max_replays; ++rep) {
+      FWI_CUDA(c, cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int),
+                                  cudaMemcpyDeviceToHost, c->stream));
+      FWI_CUDA(c, cudaStreamSynchronize(c->stream));
+      if (*c->h_n_active == 0) break;
+      if (c->cancel.load()) return fail(c, FWI_ERR_CANCELLED, "solve cancelled");
+      FWI_CUDA(c, cudaGraphLaunch(rec.exec, c->stream));
+      c->launches += rec.nodes;
+    }
   }
   // ---- pending updates ----
-  finalize_kernel<T><<<blocks_for(c->N * nb, 256, c->n_sm * 16), 256, 0, c->stream>>>(
-      X, (const cplx<T>*)c->kv[2], (const cplx<T>*)c->kv[0], c->scal, nb, c->N);
+  {
+    Prof p(c, KC_FINALIZE);
+    finalize_kernel<T><<<blocks_for(c->N * nb, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+        X, (const cplx<T>*)c->kv[2], (const cplx<T>*)c->kv[0], c->scal, nb, c->N);
+  }
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
 }
@@ -447,6 +536,7 @@ fwi_status solve_all(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, bo
   }
   FWI_CUDA(c, cudaEventRecord(c->ev1, c->stream));
   FWI_CUDA(c, cudaEventSynchronize(c->ev1));
+  prof_flush(c);
   if (info) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -472,17 +562,17 @@ fwi_status apply_op_t(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
   b.cz.freq_fixed = freq;  // every vector of the call is at frequency `freq`
   const cplx<T>* src = (const cplx<T>*)in;
   if (kind == 0) {  // K
-    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 0, 0));
-    FWI_CUDA(c, columns(b, false));
-    FWI_CUDA(c, row_inv(b, RI_K, false, nullptr, (cplx<T>*)out));
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, n_rhs, src, 0, 0));
+    FWI_CUDA(c, columns(b, false, n_rhs));
+    FWI_CUDA(c, row_inv(b, RI_K, false, n_rhs, nullptr, (cplx<T>*)out));
   } else if (kind == 1) {  // A
-    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 0, 1));
-    FWI_CUDA(c, columns(b, false));
-    FWI_CUDA(c, row_inv(b, RI_A, false, src, (cplx<T>*)out));
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, n_rhs, src, 0, 1));
+    FWI_CUDA(c, columns(b, false, n_rhs));
+    FWI_CUDA(c, row_inv(b, RI_A, false, n_rhs, src, (cplx<T>*)out));
   } else {  // A^H
-    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, src, 1, 0));
-    FWI_CUDA(c, columns(b, false));
-    FWI_CUDA(c, row_inv(b, RI_AH, false, src, (cplx<T>*)out));
+    FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, n_rhs, src, 1, 0));
+    FWI_CUDA(c, columns(b, false, n_rhs));
+    FWI_CUDA(c, row_inv(b, RI_AH, false, n_rhs, src, (cplx<T>*)out));
   }
   return FWI_OK;
 }
@@ -516,6 +606,7 @@ fwi_status apply_op(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
 
 fwi_status copy_field(fwi_ctx* c, void* dst, const void* src, long long n, int conj) {
   const int blocks = blocks_for(n, 256, c->n_sm * 16);
+  Prof p(c, KC_MISC, 2.0 * n * c->csz);
   if (c->fp64)
     copy_conj_kernel<double><<<blocks, 256, 0, c->stream>>>((double2*)dst, (const double2*)src, n, conj);
   else

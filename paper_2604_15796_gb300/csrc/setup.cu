@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "prof.cuh"
 
 namespace fwi {
 
@@ -273,6 +274,7 @@ fwi_status setup_t(fwi_ctx* c) {
 
 template <typename T>
 fwi_status set_contrast_t(fwi_ctx* c, const void* m) {
+  Prof p(c, KC_MISC);
   convert_kernel<T><<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
       (cplx<T>*)c->mF, (const double2*)m, c->N);
   FWI_CUDA(c, cudaGetLastError());
@@ -290,6 +292,7 @@ fwi_status set_contrast(fwi_ctx* c, const void* m) {
 }
 
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m) {
+  Prof p(c, KC_MISC);
   contrast_kernel<<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
       (double2*)m, sos, alpha, c->N, c->c0);
   FWI_CUDA(c, cudaGetLastError());

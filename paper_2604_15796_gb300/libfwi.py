@@ -46,6 +46,19 @@ class fwi_solve_info(Structure):
                 ("n_not_converged", c_int), ("device_ms", c_float)]
 
 
+class fwi_kernel_stat(Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("ms", c_double), ("launches", ctypes.c_longlong),
+                ("bytes", c_double), ("flops", c_double)]
+
+
+FWI_MAX_KERNEL_STATS = 24
+
+
+class fwi_stats(Structure):
+    _fields_ = [("kernel_launches", ctypes.c_longlong), ("n_kernel_stats", c_int),
+                ("kernels", fwi_kernel_stat * FWI_MAX_KERNEL_STATS)]
+
+
 class fwi_admm_params(Structure):
     _fields_ = [("lambda_", c_double), ("rho", c_double), ("gamma", c_double),
                 ("dual_step", c_double), ("n_cg", c_int), ("m_ref", c_void_p)]
@@ -65,11 +78,15 @@ EXPORTS = {
                              c_void_p, POINTER(fwi_solve_info), POINTER(fwi_solve_info)]),
     "fwi_admm_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  POINTER(fwi_admm_params), c_void_p]),
+    "fwi_admm_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fwi_apply_K": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_apply_A": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_apply_AH": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_jac_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
     "fwi_jac_adjoint": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fwi_set_profiling": (c_int, [c_void_p, c_int]),
+    "fwi_get_stats": (c_int, [c_void_p, POINTER(fwi_stats)]),
+    "fwi_reset_stats": (c_int, [c_void_p]),
     "fwi_version": (ctypes.c_char_p, []),
 }
 
@@ -108,11 +125,15 @@ fwi_forward = _bind("fwi_forward")
 fwi_adjoint = _bind("fwi_adjoint")
 fwi_gradient = _bind("fwi_gradient")
 fwi_admm_tv_step = _bind("fwi_admm_tv_step")
+fwi_admm_init = _bind("fwi_admm_init")
 fwi_apply_K = _bind("fwi_apply_K")
 fwi_apply_A = _bind("fwi_apply_A")
 fwi_apply_AH = _bind("fwi_apply_AH")
 fwi_jac_forward = _bind("fwi_jac_forward")
 fwi_jac_adjoint = _bind("fwi_jac_adjoint")
+fwi_set_profiling = _bind("fwi_set_profiling")
+fwi_get_stats = _bind("fwi_get_stats")
+fwi_reset_stats = _bind("fwi_reset_stats")
 fwi_version = _bind("fwi_version")
 
 
@@ -251,6 +272,14 @@ class Context:
                                  _ptr(data), byref(rf.info), byref(ra.info)))
         return float(mis.value), rf, ra
 
+    def admm_init(self, m0):
+        """(g, u) = (nabla m0, 0) on the device (Algorithm 1 initialisation)."""
+        g = self.torch.empty((self.dim,) + self.shape, dtype=self.torch.complex128,
+                             device="cuda")
+        u = self.torch.empty_like(g)
+        self._check(fwi_admm_init(self.handle, _ptr(m0), _ptr(g), _ptr(u)))
+        return g, u
+
     def admm_tv_step(self, m, g, u, grad, lam=1e-4, rho=1e-3, gamma=1e-5, n_cg=10,
                      dual_step=0.0, m_ref=None, sos=None):
         p = fwi_admm_params()
@@ -270,6 +299,23 @@ class Context:
             st = fwi_apply_AH(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
         self._check(st)
         return out
+
+    def set_profiling(self, on):
+        self._check(fwi_set_profiling(self.handle, int(bool(on))))
+
+    def stats(self):
+        """(kernel launches so far, {class: dict(ms, launches, bytes, flops)})."""
+        st = fwi_stats()
+        self._check(fwi_get_stats(self.handle, byref(st)))
+        ks = {}
+        for i in range(st.n_kernel_stats):
+            k = st.kernels[i]
+            ks[k.name.decode()] = dict(ms=k.ms, launches=int(k.launches), bytes=k.bytes,
+                                       flops=k.flops)
+        return int(st.kernel_launches), ks
+
+    def reset_stats(self):
+        self._check(fwi_reset_stats(self.handle))
 
     def jac_forward(self, a):
         y = self.torch.empty((self.n_freq, self.n_elem, self.n_elem),

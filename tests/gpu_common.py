@@ -8,8 +8,8 @@ from paper_2604_15796_gb300 import phantoms
 
 
 def rel_l2(a, b):
-    a = np.asarray(a)
-    b = np.asarray(b)
+    a = np.asarray(a).ravel()
+    b = np.asarray(b).ravel()
     nb = np.linalg.norm(b)
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
