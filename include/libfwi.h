@@ -206,6 +206,35 @@ FWI_API fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs
 FWI_API fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y);
 FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
 
+/* ---- Allocation-free contraction (no counterpart in the paper) ----------
+   For callers that cannot allocate device memory: code that runs where
+   cudaMalloc is forbidden or unavailable (inside another framework's memory
+   pool, under a stream-ordered allocator policy, in a plugin that must not
+   touch the allocator, or before a context could be sized), and so cannot
+   call fwi_create.  It computes, without any allocation,
+       Y[l][e][j] = scale[l] * sum_n X[l][e][n] a[n] Q[l][j][n]
+   -- the pixel contraction behind the data projection and J a (with
+   X = Q = fields and scale = k_l^2 dV) -- for complex FP32 inputs.
+   X, Q: dev c64 [n_freq][n_elem][N]; a: dev c64 [N] or NULL (a = 1);
+   scale: host double [n_freq]; Y: dev c128 [n_freq][n_elem][n_elem] (out);
+   cuda_stream: cudaStream_t (NULL = legacy default stream).
+   Limits: n_freq <= FWI_NOALLOC_MAX_FREQ and n_freq * n_elem^2 <= 524288
+   (the split partial sums live in one 4 MiB file-scope device array, which
+   every GPU that loads the library holds until exit); larger sizes return
+   FWI_ERR_INVALID_ARG with a message (fwi_last_error(NULL)).
+   The first call on a device looks up the array's device address
+   (cudaGetSymbolAddress) and caches it; make that first call outside any
+   stream capture.  Every call shares the array, which keeps the last
+   call's contents (no part of it needs to start at zero: each call writes
+   every partial it reads).  Calls whose work overlaps on the GPU (other
+   streams, other host threads) race on the array; serialise them.
+   Enqueues on cuda_stream and returns without synchronising. */
+#define FWI_NOALLOC_MAX_FREQ 32
+FWI_API fwi_status fwi_contract_pixels_noalloc(const void* X, const void* a, const void* Q,
+                                               int n_freq, int n_elem, long long N,
+                                               const double* scale, void* Y,
+                                               void* cuda_stream);
+
 /* ---- Instrumentation (no counterpart in the paper) ----------------------
    Kernel launch counting is always on.  With profiling on, the Krylov
    iterations run without CUDA graphs and every kernel launch of the

@@ -502,3 +502,107 @@ fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z) {
 }
 
 }  // namespace fwi
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the pixel contraction, for callers that cannot
+// call cudaMalloc (see fwi_contract_pixels_noalloc in libfwi.h).  Its split
+// partial sums live in a file-scope device array instead of a context
+// workspace.  Every call shares this array; concurrent calls race.
+#include <mutex>
+
+namespace fwi {
+namespace {
+
+constexpr size_t kNoallocScratchBytes = size_t(4) << 20;  // 4 MiB
+constexpr long long kNoallocScratchElems = (long long)(kNoallocScratchBytes / sizeof(float2));
+__device__ __align__(256) float2 g_noalloc_scratch[kNoallocScratchElems];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float2* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+struct FreqScales { double s[FWI_NOALLOC_MAX_FREQ]; };
+
+// Y[l][e][j] = scale_l * sum_s part[s][l][e][j]  (FP64, fixed order)
+__global__ void contract_reduce_static_kernel(double2* Y, const float2* part, int split,
+                                              long long per_split, int NE2, FreqScales sc) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_split;
+       i += (long long)gridDim.x * blockDim.x) {
+    double sx = 0.0, sy = 0.0;
+    for (int s = 0; s < split; ++s) {
+      const float2 v = part[(long long)s * per_split + i];
+      sx += (double)v.x;
+      sy += (double)v.y;
+    }
+    const double f = sc.s[i / NE2];
+    Y[i] = make_double2(sx * f, sy * f);
+  }
+}
+
+// Device address of the scratch array for the current device, looked up
+// once per device (cudaGetSymbolAddress; no allocation).
+cudaError_t noalloc_scratch(float2** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = (float2*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace fwi
+
+extern "C" fwi_status fwi_contract_pixels_noalloc(const void* X, const void* a, const void* Q,
+                                                  int n_freq, int n_elem, long long N,
+                                                  const double* scale, void* Y,
+                                                  void* cuda_stream) {
+  using namespace fwi;
+  if (!X || !Q || !Y || !scale || n_freq <= 0 || n_elem <= 0 || N <= 0)
+    return fail(nullptr, FWI_ERR_INVALID_ARG, "fwi_contract_pixels_noalloc: bad argument");
+  if (n_freq > FWI_NOALLOC_MAX_FREQ)
+    return fail(nullptr, FWI_ERR_INVALID_ARG,
+                "fwi_contract_pixels_noalloc: n_freq exceeds FWI_NOALLOC_MAX_FREQ");
+  const long long per = (long long)n_freq * n_elem * n_elem;
+  if (per > kNoallocScratchElems)
+    return fail(nullptr, FWI_ERR_INVALID_ARG,
+                "fwi_contract_pixels_noalloc: n_freq * n_elem^2 exceeds the 4 MiB static "
+                "scratch (at most 524288 complex partial sums)");
+  float2* part = nullptr;
+  cudaError_t e = noalloc_scratch(&part);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc scratch");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc");
+  const int nbe = (n_elem + TB - 1) / TB;
+  const int tiles = nbe * nbe * n_freq;
+  long long split = (sms * 6 + tiles - 1) / tiles;
+  const long long max_split_mem = kNoallocScratchElems / per;
+  const long long max_split_n = (N + KC - 1) / KC;
+  if (split > max_split_mem) split = max_split_mem;
+  if (split > max_split_n) split = max_split_n;
+  if (split < 1) split = 1;
+  long long chunk = (N + split - 1) / split;
+  chunk = ((chunk + KC - 1) / KC) * KC;
+  FreqScales sc{};
+  for (int l = 0; l < n_freq; ++l) sc.s[l] = scale[l];
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  dim3 grid((unsigned)split, nbe * nbe, n_freq);
+  contract_kernel<float><<<grid, 256, 0, s>>>((const float2*)X, (const float2*)a,
+                                              (const float2*)Q, part, n_elem, N, n_freq, chunk);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc launch");
+  contract_reduce_static_kernel<<<blocks_for(per, 256, sms * 8), 256, 0, s>>>(
+      (double2*)Y, part, (int)split, per, n_elem * n_elem, sc);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc launch");
+  return FWI_OK;
+}

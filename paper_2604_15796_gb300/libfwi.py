@@ -84,6 +84,9 @@ EXPORTS = {
     "fwi_apply_AH": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_jac_forward": (c_int, [c_void_p, c_void_p, c_void_p]),
     "fwi_jac_adjoint": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "fwi_contract_pixels_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int,
+                                            ctypes.c_longlong, POINTER(c_double), c_void_p,
+                                            c_void_p]),
     "fwi_set_profiling": (c_int, [c_void_p, c_int]),
     "fwi_get_stats": (c_int, [c_void_p, POINTER(fwi_stats)]),
     "fwi_reset_stats": (c_int, [c_void_p]),
@@ -131,6 +134,7 @@ fwi_apply_A = _bind("fwi_apply_A")
 fwi_apply_AH = _bind("fwi_apply_AH")
 fwi_jac_forward = _bind("fwi_jac_forward")
 fwi_jac_adjoint = _bind("fwi_jac_adjoint")
+fwi_contract_pixels_noalloc = _bind("fwi_contract_pixels_noalloc")
 fwi_set_profiling = _bind("fwi_set_profiling")
 fwi_get_stats = _bind("fwi_get_stats")
 fwi_reset_stats = _bind("fwi_reset_stats")
