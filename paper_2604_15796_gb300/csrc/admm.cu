@@ -129,21 +129,35 @@ __global__ void q_kernel(double2* q, const double2* z, const double2* d, double 
   block_reduce_store(acc, part);
 }
 
+// Fixed-order block sum of np partials (one block of 256 threads).
+__device__ inline double block_total(const double* part, int np) {
+  __shared__ double sh[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) t += part[i];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
 // scalars: s[0] = rr, s[1] = alpha, s[2] = beta, s[3] = flag (1: stop)
 __global__ void cg_init_scalar(double* s, const double* part, int np) {
-  double t = 0.0;
-  for (int i = 0; i < np; ++i) t += part[i];
-  s[0] = t;
-  s[3] = (t == 0.0) ? 1.0 : 0.0;
+  const double t = block_total(part, np);
+  if (threadIdx.x == 0) {
+    s[0] = t;
+    s[3] = (t == 0.0) ? 1.0 : 0.0;
+  }
 }
 __global__ void cg_alpha_scalar(double* s, const double* part, int np) {
-  double t = 0.0;
-  for (int i = 0; i < np; ++i) t += part[i];
-  s[1] = (s[3] == 0.0 && t != 0.0) ? s[0] / t : 0.0;
+  const double t = block_total(part, np);
+  if (threadIdx.x == 0) s[1] = (s[3] == 0.0 && t != 0.0) ? s[0] / t : 0.0;
 }
 __global__ void cg_beta_scalar(double* s, const double* part, int np) {
-  double t = 0.0;
-  for (int i = 0; i < np; ++i) t += part[i];
+  const double t = block_total(part, np);
+  if (threadIdx.x != 0) return;
   if (s[3] != 0.0 || s[0] == 0.0) {
     s[2] = 0.0;
     s[3] = 1.0;
@@ -281,7 +295,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   FWI_CUDA(c, cudaGetLastError());
   {
     Prof pf(c, KC_ADMM);
-    cg_init_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+    cg_init_scalar<<<1, 256, 0, s>>>(sc, part, nb);
   }
   FWI_CUDA(c, cudaGetLastError());
   for (int it = 0; it < p->n_cg; ++it) {
@@ -296,7 +310,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
     FWI_CUDA(c, cudaGetLastError());
     {
       Prof pf(c, KC_ADMM);
-      cg_alpha_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+      cg_alpha_scalar<<<1, 256, 0, s>>>(sc, part, nb);
     }
     {
       Prof pf(c, KC_ADMM);
@@ -304,7 +318,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
     }
     {
       Prof pf(c, KC_ADMM);
-      cg_beta_scalar<<<1, 1, 0, s>>>(sc, part, nb);
+      cg_beta_scalar<<<1, 256, 0, s>>>(sc, part, nb);
     }
     {
       Prof pf(c, KC_ADMM);

@@ -326,4 +326,47 @@ FWI_HD void phaseD_load(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Radix-2 split of an R = 2Q point DFT over a pair of lanes that differ by 16
+// (device only: the pair exchanges values with warp shuffles).
+//
+// split_dft : lane h holds x[2m + h] (m < Q); on return it holds
+//             X[k + Q h] (k < Q) of the direction INV.
+// split_idft: lane h holds X[k + Q h]; on return it holds x[2m + h] of the
+//             direction INV (unnormalised).
+#if defined(__CUDACC__)
+template <typename V> __device__ __forceinline__ V shfl_pair(V a) {
+  V o;
+  o.x = __shfl_xor_sync(0xffffffffu, a.x, 16);
+  o.y = __shfl_xor_sync(0xffffffffu, a.y, 16);
+  return o;
+}
+
+template <int Q, bool INV, typename T>
+__device__ __forceinline__ void split_dft(cplx<T>* u, int h) {
+  Dft<Q, INV, T>::run(u);
+  SFor<Q>::run([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const cplx<T> o = shfl_pair(u[k]);
+    const cplx<T> u0 = h ? o : u[k];
+    const cplx<T> u1 = twiddle_ct<k, 2 * Q, INV>(h ? u[k] : o);
+    u[k] = h ? csub(u0, u1) : cadd(u0, u1);
+  });
+}
+
+template <int Q, bool INV, typename T>
+__device__ __forceinline__ void split_idft(cplx<T>* u, int h) {
+  SFor<Q>::run([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const cplx<T> o = shfl_pair(u[k]);
+    const cplx<T> xa = h ? o : u[k];  // X[k]
+    const cplx<T> xb = h ? u[k] : o;  // X[k + Q]
+    cplx<T> z = h ? csub(xa, xb) : cadd(xa, xb);
+    if (h) z = twiddle_ct<k, 2 * Q, INV>(z);
+    u[k] = z;
+  });
+  Dft<Q, INV, T>::run(u);
+}
+#endif
+
 }  // namespace fwi

@@ -61,61 +61,217 @@ __device__ __forceinline__ Coef<T> load_coef(const Scal* sc) {
 }
 
 // --------------------------------------------------------------------------
-// Row forward pass.  Thread t of a line owns columns n2 = t + i*TL; the
-// sample x = R2*n1 + n2 of the row feeds v[i*R1 + n1].
+// Split plans: L = R1 * R2 where an R-point DFT with R = 32 is shared by a
+// lane pair (S = 2, lanes differing by 16) so that no thread holds more
+// than 16 complex values.  TL = R2 * S1 = R1 * S2 threads per line.
+template <int L_, int R1_, int R2_, int S1_, int S2_> struct SPlan {
+  static constexpr int L = L_, R1 = R1_, R2 = R2_, S1 = S1_, S2 = S2_;
+  static constexpr int TL = R2 * S1;
+  static_assert(TL == R1 * S2, "split plan thread count");
+  static_assert(R1 * R2 == L, "plan factors");
+  static constexpr int Q1 = R1 / S1, Q2 = R2 / S2;
+  static constexpr int H1 = R1 / 2;
+  static constexpr int E = Q1 > Q2 ? Q1 : Q2;
+  static constexpr bool split = true;
+  static constexpr int CA = 1, MA = Q1, CB = 1, MB = Q2;
+  static constexpr int span(int pad) { return R2 * (R1 + pad); }
+};
+
+template <class P> struct PlanTraits {  // unsplit plans (fft_core.cuh Plan)
+  static constexpr bool split = false;
+  static constexpr int CA = P::C1, MA = P::R1, CB = P::C3, MB = P::R2;
+};
+template <int L, int R1, int R2, int S1, int S2> struct PlanTraits<SPlan<L, R1, R2, S1, S2>> {
+  static constexpr bool split = true;
+  static constexpr int CA = 1, MA = R1 / S1, CB = 1, MB = R2 / S2;
+};
+
+// Line-thread index g -> (index, half) for a split phase.  GP = consecutive
+// g values per warp (32 for row lines, 32/TC for interleaved columns); the
+// two halves of a pair sit 16 lanes apart and each half-warp reads
+// consecutive shared-memory positions.
+template <int S, int GP> __device__ __forceinline__ void decode(int g, int& idx, int& s) {
+  if constexpr (S == 1) {
+    idx = g;
+    s = 0;
+  } else {
+    s = (g / (GP / 2)) & 1;
+    idx = (g / GP) * (GP / 2) + (g % (GP / 2));
+  }
+}
+
+// Phase-A slot (outer i, inner m) of thread t -> (n2, n1); false if idle.
+template <class P, int GP>
+__device__ __forceinline__ bool slotA(int t, int i, int m, int& n2, int& n1) {
+  if constexpr (PlanTraits<P>::split) {
+    int s;
+    decode<P::S1, GP>(t, n2, s);
+    n1 = (P::S1 == 1) ? m : 2 * m + s;
+    return true;
+  } else {
+    n2 = t + i * P::TL;
+    n1 = m;
+    return P::C1 * P::TL == P::R2 || n2 < P::R2;
+  }
+}
+
+// Phase-B slot (outer i, inner kp) of thread t -> (k1, k2); false if idle.
+template <class P, int GP>
+__device__ __forceinline__ bool slotB(int t, int i, int kp, int& k1, int& k2) {
+  if constexpr (PlanTraits<P>::split) {
+    int s;
+    decode<P::S2, GP>(t, k1, s);
+    k2 = (P::S2 == 1) ? kp : kp + P::Q2 * s;
+    return true;
+  } else {
+    k1 = t + i * P::TL;
+    k2 = kp;
+    return P::C3 * P::TL == P::R1 || k1 < P::R1;
+  }
+}
+
+template <class P, int GP, typename T>
+__device__ __forceinline__ void ph_A(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
+                                     const cplx<T>* tw) {
+  if constexpr (PlanTraits<P>::split) {
+    int n2, s;
+    decode<P::S1, GP>(t, n2, s);
+    if constexpr (P::S1 == 1) Dft<P::R1, false, T>::run(v);
+    else split_dft<P::Q1, false, T>(v, s);
+#pragma unroll
+    for (int kp = 0; kp < P::Q1; ++kp) {
+      const int k1 = (P::S1 == 1) ? kp : kp + P::Q1 * s;
+      cplx<T> z = v[kp];
+      if (k1 > 0 && n2 > 0) z = cmul(z, FWI_LDG(tw + n2 * k1));
+      sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
+    }
+  } else {
+    phaseA_store<P, T>(t, v, sm, sj, pad, tw);
+  }
+}
+
+template <class P, int GP, typename T>
+__device__ __forceinline__ void ph_B(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
+  if constexpr (PlanTraits<P>::split) {
+    int k1, s;
+    decode<P::S2, GP>(t, k1, s);
+#pragma unroll
+    for (int m = 0; m < P::Q2; ++m) {
+      const int n2 = (P::S2 == 1) ? m : 2 * m + s;
+      v[m] = sm[(n2 * (P::R1 + pad) + k1) * sj];
+    }
+    if constexpr (P::S2 == 1) Dft<P::R2, false, T>::run(v);
+    else split_dft<P::Q2, false, T>(v, s);
+  } else {
+    phaseB_load<P, T>(t, v, sm, sj, pad);
+  }
+}
+
+template <class P, int GP, typename T>
+__device__ __forceinline__ void ph_C(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
+                                     const cplx<T>* tw) {
+  if constexpr (PlanTraits<P>::split) {
+    int k1, s;
+    decode<P::S2, GP>(t, k1, s);
+    if constexpr (P::S2 == 1) Dft<P::R2, true, T>::run(v);
+    else split_idft<P::Q2, true, T>(v, s);
+#pragma unroll
+    for (int m = 0; m < P::Q2; ++m) {
+      const int n2 = (P::S2 == 1) ? m : 2 * m + s;
+      cplx<T> z = v[m];
+      if (k1 > 0 && n2 > 0) z = cmulc(z, FWI_LDG(tw + n2 * k1));
+      sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
+    }
+  } else {
+    phaseC_store<P, T>(t, v, sm, sj, pad, tw);
+  }
+}
+
+template <class P, int GP, typename T>
+__device__ __forceinline__ void ph_D(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
+  if constexpr (PlanTraits<P>::split) {
+    int n2, s;
+    decode<P::S1, GP>(t, n2, s);
+#pragma unroll
+    for (int kp = 0; kp < P::Q1; ++kp) {
+      const int k1 = (P::S1 == 1) ? kp : kp + P::Q1 * s;
+      v[kp] = sm[(n2 * (P::R1 + pad) + k1) * sj];
+    }
+    if constexpr (P::S1 == 1) Dft<P::R1, true, T>::run(v);
+    else split_idft<P::Q1, true, T>(v, s);
+  } else {
+    phaseD_load<P, T>(t, v, sm, sj, pad);
+  }
+}
+
+// Lines of a row CTA span whole warps when TL >= 32 (GP = 32); shorter
+// lines never use the split phases.
+template <class P> constexpr int row_gp() { return 32; }
+
+// --------------------------------------------------------------------------
+// Row forward pass.  Phase-A slot (i, m) of thread t holds the sample
+// x = R2*n1 + n2 of the row in v[i*MA + m].
 template <class P, typename T, int MODE>
-__device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs,
-                                        int row, cplx<T>* v, T& acc) {
+__device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, int row,
+                                        cplx<T>* v, T& acc) {
   using V = cplx<T>;
+  constexpr int GP = row_gp<P>();
+  const V* __restrict__ in = a.in;
+  const V* __restrict__ mm = a.m;
+  V* __restrict__ X = a.X;
+  V* __restrict__ R = a.R;
+  V* __restrict__ RH = a.RH;
+  V* __restrict__ Pp = a.P;
+  const V* __restrict__ Vv = a.V;
+  const V* __restrict__ Tt = a.Tt;
   const long long vb = (long long)rhs * a.N + (long long)row * a.nx;
   const long long mb = (long long)row * a.nx;
   const int nin1 = a.full ? P::R1 : P::H1;
   Coef<T> c;
   if (MODE == RF_ITER || MODE == RF_S) c = load_coef<T>(a.scal + rhs);
 #pragma unroll
-  for (int i = 0; i < P::C1; ++i) {
-    const int n2 = t + i * P::TL;
-    if (P::C1 * P::TL == P::R2 || n2 < P::R2) {
+  for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-      for (int n1 = 0; n1 < P::R1; ++n1) {
-        V w = mk<T>(T(0), T(0));
-        if (n1 < nin1) {
-          const int x = P::R2 * n1 + n2;
-          const long long idx = vb + x;
-          V u;
-          if (MODE == RF_PLAIN) {
-            u = a.in[idx];
-            if (a.conj_in) u = cconj(u);
-          } else if (MODE == RF_INIT) {
-            u = a.in[idx];
-            if (a.conj_in) u = cconj(u);
-            a.X[idx] = mk<T>(T(0), T(0));
-            a.R[idx] = u;
-            a.RH[idx] = u;
-            a.P[idx] = u;
-            acc += u.x * u.x + u.y * u.y;
-          } else if (MODE == RF_START) {
-            u = a.P[idx];
-          } else if (MODE == RF_ITER) {
-            // x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
-            V xx = a.X[idx], p = a.P[idx], s = a.R[idx], tt = a.Tt[idx], vv = a.V[idx];
-            xx = cadd(xx, cadd(cmul(c.alpha, p), cmul(c.omega, s)));
-            V r = csub(s, cmul(c.omega, tt));
-            p = cadd(r, cmul(c.beta, csub(p, cmul(c.omega, vv))));
-            a.X[idx] = xx;
-            a.R[idx] = r;
-            a.P[idx] = p;
-            u = p;
-          } else {  // RF_S: s = r - alpha v, stored over r
-            V s = csub(a.R[idx], cmul(c.alpha, a.V[idx]));
-            a.R[idx] = s;
-            u = s;
-          }
-          if (a.use_m) u = cmul(a.m[mb + x], u);
-          w = u;
+    for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+      int n2, n1;
+      const bool ok = slotA<P, GP>(t, i, m, n2, n1);
+      V w = mk<T>(T(0), T(0));
+      if (ok && n1 < nin1) {
+        const int x = P::R2 * n1 + n2;
+        const long long idx = vb + x;
+        V u;
+        if (MODE == RF_PLAIN) {
+          u = in[idx];
+          if (a.conj_in) u = cconj(u);
+        } else if (MODE == RF_INIT) {
+          u = in[idx];
+          if (a.conj_in) u = cconj(u);
+          X[idx] = mk<T>(T(0), T(0));
+          R[idx] = u;
+          RH[idx] = u;
+          Pp[idx] = u;
+          acc += u.x * u.x + u.y * u.y;
+        } else if (MODE == RF_START) {
+          u = Pp[idx];
+        } else if (MODE == RF_ITER) {
+          // x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
+          V xx = X[idx], p = Pp[idx], s = R[idx], tt = Tt[idx], vv = Vv[idx];
+          xx = cadd(xx, cadd(cmul(c.alpha, p), cmul(c.omega, s)));
+          const V r = csub(s, cmul(c.omega, tt));
+          p = cadd(r, cmul(c.beta, csub(p, cmul(c.omega, vv))));
+          X[idx] = xx;
+          R[idx] = r;
+          Pp[idx] = p;
+          u = p;
+        } else {  // RF_S: s = r - alpha v, stored over r
+          const V s = csub(R[idx], cmul(c.alpha, Vv[idx]));
+          R[idx] = s;
+          u = s;
         }
-        v[i * P::R1 + n1] = w;
+        if (a.use_m) u = cmul(mm[mb + x], u);
+        w = u;
       }
+      v[i * PlanTraits<P>::MA + m] = w;
     }
   }
 }
@@ -124,6 +280,7 @@ template <class P, typename T, int LPC>
 __global__ void __launch_bounds__(LPC * P::TL)
 row_fwd_kernel(const RowFwdArgs<T> a) {
   using V = cplx<T>;
+  constexpr int GP = row_gp<P>();
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   constexpr int LSTR = P::span(1) + 1;
@@ -150,17 +307,18 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
       }
     }
     __syncthreads();  // shared memory of the previous item fully consumed
-    if (valid) phaseA_store<P, T>(t, v, sml, 1, 1, a.tw);
+    if (valid) ph_A<P, GP, T>(t, v, sml, 1, 1, a.tw);
     __syncthreads();
     if (valid) {
-      phaseB_load<P, T>(t, v, sml, 1, 1);
-      V* out = a.plane + ((long long)rhs * a.rows + row) * P::L;
+      ph_B<P, GP, T>(t, v, sml, 1, 1);
+      V* __restrict__ out = a.plane + ((long long)rhs * a.rows + row) * P::L;
 #pragma unroll
-      for (int i = 0; i < P::C3; ++i) {
-        const int k1 = t + i * P::TL;
-        if (P::C3 * P::TL == P::R1 || k1 < P::R1) {
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-          for (int k2 = 0; k2 < P::R2; ++k2) out[k1 + P::R1 * k2] = v[i * P::R2 + k2];
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2))
+            out[k1 + P::R1 * k2] = v[i * PlanTraits<P>::MB + kp];
         }
       }
     }
@@ -180,56 +338,66 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
 //   RI_T : 0 <t, s>, 1 <t, t>, 2 <rhat, t>, 3 <rhat, s>, 4 <s, s>
 //   RI_R0: 0 <r, r>, 1 <b, b>
 template <class P, typename T, int MODE>
-__device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs,
-                                         int row, const cplx<T>* v,
-                                         T (&acc)[2 * NSLOT]) {
+__device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs, int row,
+                                         const cplx<T>* v, T (&acc)[2 * NSLOT]) {
   using V = cplx<T>;
+  constexpr int GP = row_gp<P>();
+  const V* __restrict__ in = a.in;
+  V* __restrict__ out = a.out;
+  const V* __restrict__ mm = a.m;
+  const V* __restrict__ Bv = a.B;
+  V* __restrict__ X = a.X;
+  V* __restrict__ R = a.R;
+  V* __restrict__ RH = a.RH;
+  V* __restrict__ Pp = a.P;
+  V* __restrict__ Vv = a.V;
+  V* __restrict__ Tt = a.Tt;
   const long long vb = (long long)rhs * a.N + (long long)row * a.nx;
   const long long mb = (long long)row * a.nx;
 #pragma unroll
-  for (int i = 0; i < P::C1; ++i) {
-    const int n2 = t + i * P::TL;
-    if (P::C1 * P::TL == P::R2 || n2 < P::R2) {
+  for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-      for (int n1 = 0; n1 < P::H1; ++n1) {
-        const int x = P::R2 * n1 + n2;
-        const long long idx = vb + x;
-        const V y = v[i * P::R1 + n1];
-        if (MODE == RI_K) {
-          a.out[idx] = y;
-        } else if (MODE == RI_A) {
-          a.out[idx] = csub(a.in[idx], y);
-        } else if (MODE == RI_AH) {
-          a.out[idx] = csub(a.in[idx], cconj(cmul(a.m[mb + x], y)));
-        } else if (MODE == RI_V) {
-          const V vv = csub(a.P[idx], y);
-          a.V[idx] = vv;
-          const V rh = a.RH[idx];
-          acc[0] += rh.x * vv.x + rh.y * vv.y;
-          acc[1] += rh.x * vv.y - rh.y * vv.x;
-        } else if (MODE == RI_T) {
-          const V s = a.R[idx];
-          const V tt = csub(s, y);
-          a.Tt[idx] = tt;
-          const V rh = a.RH[idx];
-          acc[0] += tt.x * s.x + tt.y * s.y;   // <t, s>
-          acc[1] += tt.x * s.y - tt.y * s.x;
-          acc[2] += tt.x * tt.x + tt.y * tt.y; // <t, t>
-          acc[4] += rh.x * tt.x + rh.y * tt.y; // <rhat, t>
-          acc[5] += rh.x * tt.y - rh.y * tt.x;
-          acc[6] += rh.x * s.x + rh.y * s.y;   // <rhat, s>
-          acc[7] += rh.x * s.y - rh.y * s.x;
-          acc[8] += s.x * s.x + s.y * s.y;     // <s, s>
-        } else {  // RI_R0: r = b - (x - K m x)
-          V b = a.B[idx];
-          if (a.conj_b) b = cconj(b);
-          const V r = csub(b, csub(a.X[idx], y));
-          a.R[idx] = r;
-          a.RH[idx] = r;
-          a.P[idx] = r;
-          acc[0] += r.x * r.x + r.y * r.y;
-          acc[2] += b.x * b.x + b.y * b.y;
-        }
+    for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+      int n2, n1;
+      const bool ok = slotA<P, GP>(t, i, m, n2, n1);
+      if (!ok || n1 >= P::H1) continue;
+      const int x = P::R2 * n1 + n2;
+      const long long idx = vb + x;
+      const V y = v[i * PlanTraits<P>::MA + m];
+      if (MODE == RI_K) {
+        out[idx] = y;
+      } else if (MODE == RI_A) {
+        out[idx] = csub(in[idx], y);
+      } else if (MODE == RI_AH) {
+        out[idx] = csub(in[idx], cconj(cmul(mm[mb + x], y)));
+      } else if (MODE == RI_V) {
+        const V vv = csub(Pp[idx], y);
+        Vv[idx] = vv;
+        const V rh = RH[idx];
+        acc[0] += rh.x * vv.x + rh.y * vv.y;
+        acc[1] += rh.x * vv.y - rh.y * vv.x;
+      } else if (MODE == RI_T) {
+        const V s = R[idx];
+        const V tt = csub(s, y);
+        Tt[idx] = tt;
+        const V rh = RH[idx];
+        acc[0] += tt.x * s.x + tt.y * s.y;    // <t, s>
+        acc[1] += tt.x * s.y - tt.y * s.x;
+        acc[2] += tt.x * tt.x + tt.y * tt.y;  // <t, t>
+        acc[4] += rh.x * tt.x + rh.y * tt.y;  // <rhat, t>
+        acc[5] += rh.x * tt.y - rh.y * tt.x;
+        acc[6] += rh.x * s.x + rh.y * s.y;    // <rhat, s>
+        acc[7] += rh.x * s.y - rh.y * s.x;
+        acc[8] += s.x * s.x + s.y * s.y;      // <s, s>
+      } else {  // RI_R0: r = b - (x - K m x)
+        V b = Bv[idx];
+        if (a.conj_b) b = cconj(b);
+        const V r = csub(b, csub(X[idx], y));
+        R[idx] = r;
+        RH[idx] = r;
+        Pp[idx] = r;
+        acc[0] += r.x * r.x + r.y * r.y;
+        acc[2] += b.x * b.x + b.y * b.y;
       }
     }
   }
@@ -239,6 +407,7 @@ template <class P, typename T, int LPC>
 __global__ void __launch_bounds__(LPC * P::TL)
 row_inv_kernel(const RowInvArgs<T> a) {
   using V = cplx<T>;
+  constexpr int GP = row_gp<P>();
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   constexpr int LSTR = P::span(1) + 1;
@@ -256,24 +425,25 @@ row_inv_kernel(const RowInvArgs<T> a) {
     const bool valid = row < a.rows;
     V v[P::E];
     if (valid) {
-      const V* in = a.plane + ((long long)rhs * a.rows + row) * P::L;
+      const V* __restrict__ in = a.plane + ((long long)rhs * a.rows + row) * P::L;
 #pragma unroll
-      for (int i = 0; i < P::C3; ++i) {
-        const int k1 = t + i * P::TL;
-        if (P::C3 * P::TL == P::R1 || k1 < P::R1) {
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-          for (int k2 = 0; k2 < P::R2; ++k2) v[i * P::R2 + k2] = in[k1 + P::R1 * k2];
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2))
+            v[i * PlanTraits<P>::MB + kp] = in[k1 + P::R1 * k2];
         }
       }
     }
     __syncthreads();
-    if (valid) phaseC_store<P, T>(t, v, sml, 1, 1, a.tw);
+    if (valid) ph_C<P, GP, T>(t, v, sml, 1, 1, a.tw);
     __syncthreads();
     T acc[2 * NSLOT];
 #pragma unroll
     for (int k = 0; k < 2 * NSLOT; ++k) acc[k] = T(0);
     if (valid) {
-      phaseD_load<P, T>(t, v, sml, 1, 1);
+      ph_D<P, GP, T>(t, v, sml, 1, 1);
       switch (a.mode) {
         case RI_K: ri_store<P, T, RI_K>(a, t, rhs, row, v, acc); break;
         case RI_A: ri_store<P, T, RI_A>(a, t, rhs, row, v, acc); break;
@@ -297,14 +467,15 @@ row_inv_kernel(const RowInvArgs<T> a) {
 }
 
 // --------------------------------------------------------------------------
-// Column pass over tiles of TC adjacent columns; thread (c, t) handles
-// column c of the tile as thread t of its line.  Shared-memory positions
+// Column pass over tiles of TC adjacent columns; thread (c, g) handles
+// column c of the tile as thread g of its line.  Shared-memory positions
 // are interleaved across the tile's columns (stride TC), which keeps the
 // exchange free of bank conflicts.
 template <class P, typename T, int TC>
-__global__ void __launch_bounds__(TC * P::TL)
+__global__ void __launch_bounds__(TC * P::TL, (TC * P::TL >= 256) ? 2 : 4)
 col_kernel(const ColArgs<T> a) {
   using V = cplx<T>;
+  constexpr int GP = 32 / TC;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int c = threadIdx.x % TC;
@@ -322,73 +493,75 @@ col_kernel(const ColArgs<T> a) {
     const int tile = (int)(rem - (long long)plane * ntile);
     const int rhs = a.active ? a.active[slot] : slot;
     const int j = tile * TC + c;
-    const V* in = a.in + rhs * a.in_rhs_stride + plane * a.in_plane_stride + j;
-    V* out = a.out + rhs * a.out_rhs_stride + plane * a.out_plane_stride + j;
+    const V* __restrict__ in = a.in + rhs * a.in_rhs_stride + plane * a.in_plane_stride + j;
+    V* __restrict__ out = a.out + rhs * a.out_rhs_stride + plane * a.out_plane_stride + j;
     V v[P::E];
     if (a.mode == C_INV) {
 #pragma unroll
-      for (int i = 0; i < P::C3; ++i) {
-        const int k1 = t + i * P::TL;
-        if (P::C3 * P::TL == P::R1 || k1 < P::R1) {
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-          for (int k2 = 0; k2 < P::R2; ++k2)
-            v[i * P::R2 + k2] = in[(long long)(k1 + P::R1 * k2) * ls];
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2))
+            v[i * PlanTraits<P>::MB + kp] = in[(long long)(k1 + P::R1 * k2) * ls];
         }
       }
     } else {
       const int nin1 = a.full ? P::R1 : P::H1;
 #pragma unroll
-      for (int i = 0; i < P::C1; ++i) {
-        const int n2 = t + i * P::TL;
-        if (P::C1 * P::TL == P::R2 || n2 < P::R2) {
+      for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-          for (int n1 = 0; n1 < P::R1; ++n1)
-            v[i * P::R1 + n1] = (n1 < nin1) ? in[(long long)(P::R2 * n1 + n2) * ls]
-                                            : mk<T>(T(0), T(0));
+        for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+          int n2, n1;
+          const bool ok = slotA<P, GP>(t, i, m, n2, n1);
+          v[i * PlanTraits<P>::MA + m] = (ok && n1 < nin1)
+                                             ? in[(long long)(P::R2 * n1 + n2) * ls]
+                                             : mk<T>(T(0), T(0));
         }
       }
     }
     __syncthreads();
     if (a.mode != C_INV) {
-      phaseA_store<P, T>(t, v, smc, TC, 0, a.tw);
+      ph_A<P, GP, T>(t, v, smc, TC, 0, a.tw);
       __syncthreads();
-      phaseB_load<P, T>(t, v, smc, TC, 0);
+      ph_B<P, GP, T>(t, v, smc, TC, 0);
       if (a.mode == C_FWD) {
 #pragma unroll
-        for (int i = 0; i < P::C3; ++i) {
-          const int k1 = t + i * P::TL;
-          if (P::C3 * P::TL == P::R1 || k1 < P::R1) {
+        for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-            for (int k2 = 0; k2 < P::R2; ++k2)
-              out[(long long)(k1 + P::R1 * k2) * ls] = v[i * P::R2 + k2];
+          for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+            int k1, k2;
+            if (slotB<P, GP>(t, i, kp, k1, k2))
+              out[(long long)(k1 + P::R1 * k2) * ls] = v[i * PlanTraits<P>::MB + kp];
           }
         }
         continue;
       }
       const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs) / a.n_elem;
-      const V* g = a.ghat + (long long)l * a.ghat_freq_stride + j;
+      const V* __restrict__ g = a.ghat + (long long)l * a.ghat_freq_stride + j;
 #pragma unroll
-      for (int i = 0; i < P::C3; ++i) {
-        const int k1 = t + i * P::TL;
-        if (P::C3 * P::TL == P::R1 || k1 < P::R1) {
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-          for (int k2 = 0; k2 < P::R2; ++k2)
-            v[i * P::R2 + k2] = cmul(v[i * P::R2 + k2],
-                                     FWI_LDG(g + (long long)(k1 + P::R1 * k2) * a.ncols));
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2)) {
+            const int r = i * PlanTraits<P>::MB + kp;
+            v[r] = cmul(v[r], FWI_LDG(g + (long long)(k1 + P::R1 * k2) * a.ncols));
+          }
         }
       }
       __syncthreads();
     }
-    phaseC_store<P, T>(t, v, smc, TC, 0, a.tw);
+    ph_C<P, GP, T>(t, v, smc, TC, 0, a.tw);
     __syncthreads();
-    phaseD_load<P, T>(t, v, smc, TC, 0);
+    ph_D<P, GP, T>(t, v, smc, TC, 0);
 #pragma unroll
-    for (int i = 0; i < P::C1; ++i) {
-      const int n2 = t + i * P::TL;
-      if (P::C1 * P::TL == P::R2 || n2 < P::R2) {
+    for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-        for (int n1 = 0; n1 < P::H1; ++n1)
-          out[(long long)(P::R2 * n1 + n2) * ls] = v[i * P::R1 + n1];
+      for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+        int n2, n1;
+        if (slotA<P, GP>(t, i, m, n2, n1) && n1 < P::H1)
+          out[(long long)(P::R2 * n1 + n2) * ls] = v[i * PlanTraits<P>::MA + m];
       }
     }
   }
@@ -405,10 +578,10 @@ template <> struct PlanFor<192> { using type = Plan<192, 12, 16, 16>; };
 template <> struct PlanFor<256> { using type = Plan<256, 16, 16, 16>; };
 template <> struct PlanFor<320> { using type = Plan<320, 20, 16, 20>; };
 template <> struct PlanFor<384> { using type = Plan<384, 24, 16, 24>; };
-template <> struct PlanFor<512> { using type = Plan<512, 16, 32, 16>; };
+template <> struct PlanFor<512> { using type = SPlan<512, 16, 32, 1, 2>; };
 template <> struct PlanFor<640> { using type = Plan<640, 20, 32, 32>; };
 template <> struct PlanFor<768> { using type = Plan<768, 24, 32, 32>; };
-template <> struct PlanFor<1024> { using type = Plan<1024, 32, 32, 32>; };
+template <> struct PlanFor<1024> { using type = SPlan<1024, 32, 32, 2, 2>; };
 
 #define FWI_FOR_EACH_L(X) \
   X(16) X(32) X(64) X(128) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
@@ -424,7 +597,7 @@ template <int L, typename T> constexpr size_t row_smem() {
 }
 
 // Columns per tile: 128-byte row segments for FP32 up to L = 512; eight
-// columns otherwise, so that a tile is at most 256 threads.
+// columns otherwise (at most 512 threads per tile).
 template <int L, typename T> constexpr int col_tc() {
   return (sizeof(T) == 4 && L <= 512) ? 16 : 8;
 }

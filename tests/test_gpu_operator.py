@@ -15,7 +15,8 @@ from paper_2604_15796_gb300 import phantoms
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(32, 32), (8, 16), (32, 96), (16, 160), (96, 32), (8, 8, 16), (16, 8, 8)]
+SHAPES = [(32, 32), (8, 16), (32, 96), (16, 160), (96, 32), (8, 8, 16), (16, 8, 8),
+          (16, 256), (256, 16), (8, 512), (512, 8), (8, 16, 256)]
 
 
 @pytest.fixture(scope="module")

@@ -30,7 +30,8 @@ def _oracle_fields(w, m):
 
 
 CASES = [((32, 32), 6, (1.5e6, 3.0e6)), ((16, 64), 5, (2.0e6,)), ((32, 96), 8, (1e6, 2.5e6)),
-         ((8, 8, 16), 4, (1.0e6, 2.0e6))]
+         ((8, 8, 16), 4, (1.0e6, 2.0e6)), ((16, 256), 6, (2.0e6, 3.0e6)),
+         ((256, 16), 4, (1.5e6,)), ((8, 512), 4, (2.5e6,))]
 
 
 @pytest.mark.parametrize("shape,n_elem,freqs", CASES)
