@@ -306,6 +306,26 @@ def run_ours(args, rank, world, samples):
                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                    "steps": ke, "ms_per_step": 1e3 * dt / ke}
 
+        # ---- comparator: plain unbatched per-RHS FP64 path (same kernels,
+        # complex128 fields, one right-hand side per launch) on a subset of
+        # the array (every 8th element, all frequencies) ----
+        comp = None
+        if not args.no_comparator:
+            sub = np.ascontiguousarray(w.elem[::8])
+            c64 = libfwi.Context(w.shape, w.h, w.c0, sub, w.freqs, precision=libfwi.FWI_FP64,
+                                 tol=1e-6, max_batch=1, stream=stream)
+            c64.forward(m0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rep = c64.forward(m0)
+            torch.cuda.synchronize()
+            dtc = time.perf_counter() - t0
+            comp = {"value": c64.n_rhs / dtc, "unit": UNIT, "rhs": c64.n_rhs,
+                    "kind": "FP64 fields, one RHS per launch (max_batch=1), same operator",
+                    "mean_iters": float(np.mean(rep.iters))}
+            comp["speedup_solves_per_s"] = value / comp["value"]
+            c64.close()
+
         # ---- live per-kernel timing (CUDA events, profiling mode) ----
         ctx.reset_stats()
         ctx.set_profiling(True)
@@ -348,6 +368,7 @@ def run_ours(args, rank, world, samples):
         "gpu_launches": int(launches1 - launches0),
         "clocks": clk.summary(),
         "e2e": e2e,
+        "comparator_fp64_unbatched": comp,
     }
     ctx.close()
     return line
@@ -397,6 +418,83 @@ def sampled_error(ctx, m0, samples):
             "samples": len(samples), "tolerance": 1e-4}
 
 
+def run_serving(args):
+    """Serving stream: Poisson arrivals of whole reconstructions (5 ADMM-TV
+    iterations each) over grids {128^2, 256^2, 384^2, 512^2, 96^3}, 64-192
+    elements, 2-12 frequencies; continuous batching with admission by HBM
+    footprint.  Arrival rate: 80 % of the capacity measured on a burst."""
+    import threading
+    import torch
+    from paper_2604_15796_gb300 import libfwi, phantoms
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    specs = phantoms.serving_requests(n_req=args.requests + 8, seed=1004, rate_hz=1.0)
+
+    def build(sp):
+        w = phantoms.tissue_phantom(sp["shape"], sp["h"], sp["n_elem"], sp["pitch"],
+                                    sp["freqs"], sp["seed"], inclusions=[1520.0, 1580.0])
+        sos0 = w.c0 + 0.5 * (w.sos - w.c0)
+        d = 1e-6 * phantoms.complex_normal((w.n_freq, w.n_elem, w.n_elem), sp["seed"])
+        return w, sos0, d.astype(np.complex64)
+
+    params = dict(n_iter=5, lam=1e-9, rho=1e-6, gamma=1e-8, n_cg=10)
+    srv = libfwi.Server(max_active=args.max_active)
+    # capacity on a burst of 8 requests
+    burst = [build(sp) for sp in specs[:8]]
+    t0 = time.perf_counter()
+    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, s0, d, **params)
+           for w, s0, d in burst]
+    burst_solves = 0
+    for i in ids:
+        _, r = srv.wait(i)
+        burst_solves += r["rhs_solves"]
+    cap = len(ids) / (time.perf_counter() - t0)
+    rate = 0.8 * cap
+    rng = np.random.default_rng(77)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.requests))
+    work = [build(sp) for sp in specs[8:8 + args.requests]]
+    results = [None] * len(work)
+    lock = threading.Lock()
+    start = time.perf_counter()
+
+    def waiter(k, rid):
+        sos, r = srv.wait(rid)
+        with lock:
+            results[k] = r
+
+    threads = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for k, ((w, s0, d), ta) in enumerate(zip(work, arrivals)):
+            delay = start + ta - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            rid = srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, s0, d, **params)
+            th = threading.Thread(target=waiter, args=(k, rid))
+            th.start()
+            threads.append(th)
+        for th in threads:
+            th.join()
+    wall = time.perf_counter() - start
+    srv.close()
+    lat = np.array([r["latency_ms"] for r in results])
+    solves = sum(r["rhs_solves"] for r in results)
+    return {"metric": METRIC, "value": solves / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": len(work), "warmup": 8, "ms_per_step": 1e3 * wall / len(work),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 fields / FP64 Krylov scalars", "data": "synthetic",
+            "config": {"workload": f"serving stream: {len(work)} reconstruction requests, "
+                                   "Poisson arrivals at 80% of burst capacity, grids "
+                                   "{128^2,256^2,384^2,512^2,96^3}, 64-192 elements, 2-12 "
+                                   "frequencies in 0.3-5 MHz, 5 ADMM-TV iterations each",
+                       "max_active": args.max_active, "arrival_rate_hz": rate,
+                       "burst_capacity_req_per_s": cap},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                           "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_ms_mean": float(np.mean([r["queue_ms"] for r in results])),
+            "requests_per_s": len(work) / wall,
+            "clocks": clk.summary()}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -404,10 +502,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thyroid256",
-                    choices=["thyroid256", "large512", "volume3d", "disc64"])
+                    choices=["thyroid256", "large512", "volume3d", "disc64", "serving"])
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--requests", type=int, default=32)
+    ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--check-samples", type=int, default=2)
     ap.add_argument("--ref-step-s", type=float, default=2.0)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
@@ -416,6 +517,10 @@ def main():
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.workload == "serving" and args.impl == "ours":
+        if rank == 0:
+            print(json.dumps(run_serving(args)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank)
         if line is not None:

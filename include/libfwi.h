@@ -206,6 +206,52 @@ FWI_API fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs
 FWI_API fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y);
 FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
 
+/* ---- Serving: continuous batching of reconstructions -------------------
+   A server runs whole reconstructions (Algorithm 1: contrast from the
+   starting SoS, g0 = nabla m0, u0 = 0, then n_iter x [fwi_gradient,
+   fwi_admm_tv_step]) for requests of different grids, arrays and frequency
+   sets.  Requests wait in FIFO order and are admitted, first fit, as soon as
+   a worker slot is free and their device footprint (fwi_workspace_bytes of
+   the request plus its vectors) fits in the remaining HBM budget.  Each
+   admitted request owns a context and a non-blocking CUDA stream, so the
+   work of concurrent requests overlaps on the device; its fields, Krylov
+   state and ADMM state stay device-resident until it completes.  Results
+   are independent of the mix: each request computes exactly what it would
+   compute alone. */
+typedef struct fwi_server fwi_server;
+typedef struct fwi_request {
+  fwi_problem_desc problem;  /* host arrays are copied at submit */
+  const double* sos0;        /* host double [N]: starting speed of sound */
+  const void* d_obs;         /* host cF [n_freq][n_elem][n_elem]: observed data */
+  fwi_admm_params admm;      /* m_ref must be NULL */
+  int n_iter;                /* ADMM-TV iterations (>= 1) */
+} fwi_request;
+typedef struct fwi_request_result {
+  int status;                /* fwi_status of the reconstruction */
+  double queue_ms;           /* submit -> admission */
+  double run_ms;             /* admission -> completion */
+  double latency_ms;         /* submit -> completion */
+  double misfit_first;       /* 1/2 ||F(m0) - d||^2 */
+  double misfit_last;        /* misfit at the last iterate's forward solve */
+  long long rhs_solves;      /* forward + adjoint BiCGSTAB solves */
+  size_t bytes;              /* admitted device footprint */
+} fwi_request_result;
+/* hbm_budget: bytes the server may hold for admitted requests (0: 90 % of
+   the free device memory at creation); max_active: worker slots (>= 1).
+   Uses the current CUDA device. */
+FWI_API fwi_status fwi_server_create(size_t hbm_budget, int max_active, fwi_server** out);
+/* Queue a request (inputs copied); *id identifies it.  A request whose
+   footprint exceeds the whole budget is rejected (FWI_ERR_NOMEM). */
+FWI_API fwi_status fwi_server_submit(fwi_server* s, const fwi_request* r, long long* id);
+/* Block until request id completes; sos_out: host double [N] (final SoS) or
+   NULL; res: host or NULL.  Each id can be waited for once. */
+FWI_API fwi_status fwi_server_wait(fwi_server* s, long long id, double* sos_out,
+                                   fwi_request_result* res);
+/* Current admitted count, queued count and admitted bytes (any may be NULL). */
+FWI_API fwi_status fwi_server_stats(fwi_server* s, int* active, int* queued, size_t* bytes);
+/* Finish every submitted request, then release the workers. */
+FWI_API fwi_status fwi_server_destroy(fwi_server* s);
+
 /* ---- Allocation-free contraction (no counterpart in the paper) ----------
    For callers that cannot allocate device memory: code that runs where
    cudaMalloc is forbidden or unavailable (inside another framework's memory

@@ -16,7 +16,7 @@ LIB = os.path.join(PKG, "lib", "libfwi.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
 UNITS = ["lsop_f32.cu", "lsop_f64.cu", "setup.cu", "krylov.cu", "jac.cu", "admm.cu",
-         "api.cu"]
+         "api.cu", "serve.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--expt-relaxed-constexpr", "-O3", "-lineinfo",

@@ -118,9 +118,12 @@ static void release(fwi_ctx* c) {
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
                   c->jsplit, c->zpart, c->aF, c->red};
-  for (void* p : bufs) if (p) cudaFree(p);
-  for (auto* p : c->vN) if (p) cudaFree(p);
-  for (auto* p : c->vD) if (p) cudaFree(p);
+  // stream-ordered frees: no device-wide synchronisation, so a context can be
+  // retired while other contexts' work runs
+  for (void* p : bufs) if (p) cudaFreeAsync(p, c->stream);
+  for (auto* p : c->vN) if (p) cudaFreeAsync(p, c->stream);
+  for (auto* p : c->vD) if (p) cudaFreeAsync(p, c->stream);
+  cudaStreamSynchronize(c->stream);
   if (c->h_n_active) cudaFreeHost(c->h_n_active);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_red) cudaFreeHost(c->h_red);
@@ -182,9 +185,10 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   }
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device);
+  // stream-ordered allocations from the device's default memory pool
   auto alloc = [&](void** p, size_t bytes) {
     if (e != cudaSuccess || bytes == 0) return;
-    e = cudaMalloc(p, bytes);
+    e = cudaMallocAsync(p, bytes, c->stream);
   };
   alloc(&c->ghat, L.b_ghat);
   alloc(&c->p0, L.b_field);

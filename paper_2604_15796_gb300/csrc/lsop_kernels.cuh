@@ -15,6 +15,9 @@
 // (grid-stride loop over (active RHS, tile) work items).
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include "common.cuh"
 
 namespace fwi {
@@ -606,8 +609,13 @@ template <int L, typename T> constexpr size_t col_smem() {
   return (size_t)L * col_tc<L, T>() * sizeof(cplx<T>);
 }
 
-// Persistent grid: resident CTAs per SM (occupancy) x SMs, cached per kernel.
-struct GridCache { int blocks = 0; };
+// Persistent grid: resident CTAs per SM (occupancy) x SMs, cached per kernel
+// (initialised once, thread-safe: contexts may run on several host threads).
+struct GridCache { std::atomic<int> blocks{0}; };
+inline std::mutex& grid_mutex() {
+  static std::mutex m;
+  return m;
+}
 template <int L, typename T, int KIND> GridCache& gcache() {
   static GridCache g;
   return g;
@@ -615,7 +623,9 @@ template <int L, typename T, int KIND> GridCache& gcache() {
 
 template <typename K>
 inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
-  if (gc.blocks > 0) return cudaSuccess;
+  if (gc.blocks.load(std::memory_order_acquire) > 0) return cudaSuccess;
+  std::lock_guard<std::mutex> lock(grid_mutex());
+  if (gc.blocks.load(std::memory_order_relaxed) > 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -626,7 +636,7 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
   if (e != cudaSuccess) return e;
-  gc.blocks = (per > 0 ? per : 1) * sms;
+  gc.blocks.store((per > 0 ? per : 1) * sms, std::memory_order_release);
   return cudaSuccess;
 }
 
@@ -683,7 +693,7 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
     GridCache& gc = gcache<LL, FWI_T, 0>();                                          \
     cudaError_t e = grid_for(k, lpc * P::TL, row_smem<LL, FWI_T>(), gc);             \
     if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks, lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                      \
+    k<<<gc.blocks.load(), lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                 \
     return cudaGetLastError();                                                       \
   }
 
@@ -695,7 +705,7 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
     GridCache& gc = gcache<LL, FWI_T, 1>();                                          \
     cudaError_t e = grid_for(k, lpc * P::TL, row_smem<LL, FWI_T>(), gc);             \
     if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks, lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                      \
+    k<<<gc.blocks.load(), lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                 \
     return cudaGetLastError();                                                       \
   }
 
@@ -707,7 +717,7 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
     GridCache& gc = gcache<LL, FWI_T, 2>();                                          \
     cudaError_t e = grid_for(k, tc * P::TL, col_smem<LL, FWI_T>(), gc);              \
     if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks, tc * P::TL, col_smem<LL, FWI_T>(), s>>>(a);                       \
+    k<<<gc.blocks.load(), tc * P::TL, col_smem<LL, FWI_T>(), s>>>(a);                 \
     return cudaGetLastError();                                                       \
   }
 

@@ -159,15 +159,17 @@ __global__ void contrast_kernel(double2* m, const double* sos, const double* alp
 }
 
 template <typename T>
-cudaError_t upload_twiddles(int L, void** dst) {
+cudaError_t upload_twiddles(int L, void** dst, cudaStream_t s) {
   std::vector<cplx<T>> h(L);
   for (int j = 0; j < L; ++j) {
     const double a = -2.0 * kPi * (double)j / (double)L;
     h[j] = mk<T>((T)std::cos(a), (T)std::sin(a));
   }
-  cudaError_t e = cudaMalloc(dst, sizeof(cplx<T>) * L);
+  cudaError_t e = cudaMallocAsync(dst, sizeof(cplx<T>) * L, s);
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(*dst, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice);
+  e = cudaMemcpyAsync(*dst, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);  // h is released on return
 }
 
 inline int grid1d(long long n, int threads, int cap) {
@@ -184,12 +186,12 @@ fwi_status compute_spectra(fwi_ctx* c) {
   cudaError_t e = cudaSuccess;
   const int cap = c->n_sm * 16;
   do {
-    if ((e = cudaMalloc(&lat, sizeof(double2) * P)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&A, sizeof(double2) * P)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&B, sizeof(double2) * P)) != cudaSuccess) break;
-    if ((e = upload_twiddles<double>(c->lx, &tx)) != cudaSuccess) break;
-    if ((e = upload_twiddles<double>(c->lz, &tz)) != cudaSuccess) break;
-    if (c->dim == 3 && (e = upload_twiddles<double>(c->ly, &ty)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&lat, sizeof(double2) * P, c->stream)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&A, sizeof(double2) * P, c->stream)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(&B, sizeof(double2) * P, c->stream)) != cudaSuccess) break;
+    if ((e = upload_twiddles<double>(c->lx, &tx, c->stream)) != cudaSuccess) break;
+    if ((e = upload_twiddles<double>(c->lz, &tz, c->stream)) != cudaSuccess) break;
+    if (c->dim == 3 && (e = upload_twiddles<double>(c->ly, &ty, c->stream)) != cudaSuccess) break;
     for (int l = 0; l < c->n_freq && e == cudaSuccess; ++l) {
       const double k = c->kwave[l];
       green_lattice_kernel<<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
@@ -229,8 +231,9 @@ fwi_status compute_spectra(fwi_ctx* c) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   } while (0);
   if (e != cudaSuccess) st = cuda_fail(c, e, "Green's function spectrum");
-  cudaFree(lat); cudaFree(A); cudaFree(B);
-  cudaFree(tx); cudaFree(ty); cudaFree(tz);
+  for (void* p : {(void*)lat, (void*)A, (void*)B, tx, ty, tz})
+    if (p) cudaFreeAsync(p, c->stream);
+  cudaStreamSynchronize(c->stream);
   return st;
 }
 
@@ -239,9 +242,9 @@ fwi_status setup_t(fwi_ctx* c) {
   if (!Lsop<double>::supported(c->lx) || !Lsop<double>::supported(c->lz) ||
       (c->dim == 3 && !Lsop<double>::supported(c->ly)))
     return fail(c, FWI_ERR_UNSUPPORTED, "no FFT plan for the doubled grid");
-  FWI_CUDA(c, upload_twiddles<T>(c->lx, &c->tw_x));
-  FWI_CUDA(c, upload_twiddles<T>(c->lz, &c->tw_z));
-  if (c->dim == 3) FWI_CUDA(c, upload_twiddles<T>(c->ly, &c->tw_y));
+  FWI_CUDA(c, upload_twiddles<T>(c->lx, &c->tw_x, c->stream));
+  FWI_CUDA(c, upload_twiddles<T>(c->lz, &c->tw_z, c->stream));
+  if (c->dim == 3) FWI_CUDA(c, upload_twiddles<T>(c->ly, &c->tw_y, c->stream));
   FWI_CUDA(c, Lsop<T>::prepare(c->lx));
   FWI_CUDA(c, Lsop<T>::prepare(c->lz));
   if (c->dim == 3) FWI_CUDA(c, Lsop<T>::prepare(c->ly));
@@ -252,22 +255,22 @@ fwi_status setup_t(fwi_ctx* c) {
   if (st != FWI_OK) return st;
   // incident fields
   double *elem = nullptr, *kw = nullptr;
-  FWI_CUDA(c, cudaMalloc(&elem, sizeof(double) * c->elem.size()));
-  FWI_CUDA(c, cudaMalloc(&kw, sizeof(double) * c->kwave.size()));
-  cudaError_t e = cudaMemcpy(elem, c->elem.data(), sizeof(double) * c->elem.size(),
-                             cudaMemcpyHostToDevice);
+  FWI_CUDA(c, cudaMallocAsync(&elem, sizeof(double) * c->elem.size(), c->stream));
+  FWI_CUDA(c, cudaMallocAsync(&kw, sizeof(double) * c->kwave.size(), c->stream));
+  cudaError_t e = cudaMemcpyAsync(elem, c->elem.data(), sizeof(double) * c->elem.size(),
+                                  cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpy(kw, c->kwave.data(), sizeof(double) * c->kwave.size(),
-                   cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(kw, c->kwave.data(), sizeof(double) * c->kwave.size(),
+                        cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
     const long long total = c->N * c->n_rhs;
     incident_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
         (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
     e = cudaGetLastError();
   }
+  cudaFreeAsync(elem, c->stream);
+  cudaFreeAsync(kw, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(elem);
-  cudaFree(kw);
   if (e != cudaSuccess) return cuda_fail(c, e, "incident fields");
   return FWI_OK;
 }

@@ -64,6 +64,17 @@ class fwi_admm_params(Structure):
                 ("dual_step", c_double), ("n_cg", c_int), ("m_ref", c_void_p)]
 
 
+class fwi_request(Structure):
+    _fields_ = [("problem", fwi_problem_desc), ("sos0", POINTER(c_double)),
+                ("d_obs", c_void_p), ("admm", fwi_admm_params), ("n_iter", c_int)]
+
+
+class fwi_request_result(Structure):
+    _fields_ = [("status", c_int), ("queue_ms", c_double), ("run_ms", c_double),
+                ("latency_ms", c_double), ("misfit_first", c_double), ("misfit_last", c_double),
+                ("rhs_solves", ctypes.c_longlong), ("bytes", c_size_t)]
+
+
 EXPORTS = {
     "fwi_workspace_bytes": (c_size_t, [POINTER(fwi_problem_desc)]),
     "fwi_create": (c_int, [POINTER(fwi_problem_desc), c_void_p, POINTER(c_void_p)]),
@@ -87,6 +98,12 @@ EXPORTS = {
     "fwi_contract_pixels_noalloc": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_int,
                                             ctypes.c_longlong, POINTER(c_double), c_void_p,
                                             c_void_p]),
+    "fwi_server_create": (c_int, [c_size_t, c_int, POINTER(c_void_p)]),
+    "fwi_server_submit": (c_int, [c_void_p, POINTER(fwi_request), POINTER(ctypes.c_longlong)]),
+    "fwi_server_wait": (c_int, [c_void_p, ctypes.c_longlong, POINTER(c_double),
+                                POINTER(fwi_request_result)]),
+    "fwi_server_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_size_t)]),
+    "fwi_server_destroy": (c_int, [c_void_p]),
     "fwi_set_profiling": (c_int, [c_void_p, c_int]),
     "fwi_get_stats": (c_int, [c_void_p, POINTER(fwi_stats)]),
     "fwi_reset_stats": (c_int, [c_void_p]),
@@ -135,6 +152,11 @@ fwi_apply_AH = _bind("fwi_apply_AH")
 fwi_jac_forward = _bind("fwi_jac_forward")
 fwi_jac_adjoint = _bind("fwi_jac_adjoint")
 fwi_contract_pixels_noalloc = _bind("fwi_contract_pixels_noalloc")
+fwi_server_create = _bind("fwi_server_create")
+fwi_server_submit = _bind("fwi_server_submit")
+fwi_server_wait = _bind("fwi_server_wait")
+fwi_server_stats = _bind("fwi_server_stats")
+fwi_server_destroy = _bind("fwi_server_destroy")
 fwi_set_profiling = _bind("fwi_set_profiling")
 fwi_get_stats = _bind("fwi_get_stats")
 fwi_reset_stats = _bind("fwi_reset_stats")
@@ -331,3 +353,66 @@ class Context:
         z = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
         self._check(fwi_jac_adjoint(self.handle, _ptr(y), _ptr(z)))
         return z
+
+
+class Server:
+    """Owns one fwi_server (continuous batching of reconstructions)."""
+
+    def __init__(self, hbm_budget=0, max_active=4):
+        h = c_void_p()
+        st = fwi_server_create(c_size_t(int(hbm_budget)), int(max_active), byref(h))
+        if st != FWI_OK:
+            raise FwiError(st, fwi_last_error(None).decode())
+        self.handle = h
+        self._pending = {}
+
+    def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
+               gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6):
+        """Queue a reconstruction; host numpy inputs (sos0 float64 of ``shape``,
+        d_obs complex64 [n_freq][n_elem][n_elem]).  Returns the request id."""
+        req = fwi_request()
+        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol)
+        req.problem = desc
+        sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
+        cdt = np.complex128 if precision == FWI_FP64 else np.complex64
+        d_obs = np.ascontiguousarray(d_obs, dtype=cdt)
+        req.sos0 = sos0.ctypes.data_as(POINTER(c_double))
+        req.d_obs = d_obs.ctypes.data
+        req.admm.lambda_, req.admm.rho, req.admm.gamma = lam, rho, gamma
+        req.admm.dual_step, req.admm.n_cg, req.admm.m_ref = dual_step, n_cg, None
+        req.n_iter = n_iter
+        rid = ctypes.c_longlong()
+        st = fwi_server_submit(self.handle, byref(req), byref(rid))
+        if st != FWI_OK:
+            raise FwiError(st, fwi_last_error(None).decode())
+        self._pending[rid.value] = tuple(shape)
+        del keep
+        return rid.value
+
+    def wait(self, rid):
+        """Block until request ``rid`` completes: (sos ndarray, result dict)."""
+        shape = self._pending.pop(rid)
+        sos = np.empty(shape, dtype=np.float64)
+        res = fwi_request_result()
+        st = fwi_server_wait(self.handle, ctypes.c_longlong(rid),
+                             sos.ctypes.data_as(POINTER(c_double)), byref(res))
+        out = {k: getattr(res, k) for k, _ in fwi_request_result._fields_}
+        if st != FWI_OK:
+            raise FwiError(st, fwi_last_error(None).decode())
+        return sos, out
+
+    def stats(self):
+        a, q, b = c_int(), c_int(), c_size_t()
+        fwi_server_stats(self.handle, byref(a), byref(q), byref(b))
+        return a.value, q.value, b.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            fwi_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

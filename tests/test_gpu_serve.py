@@ -1,0 +1,110 @@
+"""Serving runtime (continuous batching of whole reconstructions) through the
+C ABI: every request's result is the same alone and in a concurrent mix,
+a one-iteration request matches the oracle's Algorithm-1 iteration, and
+admission respects the HBM budget."""
+import numpy as np
+import pytest
+
+from gpu_common import oracle_problem, rel_l2, small_workload
+from oracle import admm, inverse, model
+from paper_2604_15796_gb300 import phantoms
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import torch
+    from paper_2604_15796_gb300 import build, libfwi
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return libfwi
+
+
+def _requests():
+    specs = [((32, 32), 6, (1.5e6, 3.0e6), 1), ((64, 64), 8, (1.0e6, 2.0e6, 3.0e6), 2),
+             ((16, 64), 5, (2.0e6,), 3), ((8, 8, 16), 4, (1.0e6, 2.0e6), 4),
+             ((32, 32), 4, (2.5e6,), 5)]
+    reqs = []
+    for shape, ne, freqs, seed in specs:
+        w = small_workload(shape, n_elem=ne, freqs=freqs, seed=seed)
+        sos0 = np.full(w.shape, w.c0) + 0.5 * (w.sos - w.c0)
+        d = 1e-6 * phantoms.complex_normal((w.n_freq, w.n_elem, w.n_elem), 100 + seed)
+        reqs.append((w, sos0, d.astype(np.complex64)))
+    return reqs
+
+
+PARAMS = dict(n_iter=2, lam=1e-9, rho=1e-6, gamma=1e-8, n_cg=4)
+
+
+def test_results_are_the_same_alone_and_in_the_mix(lib):
+    reqs = _requests()
+    alone = []
+    srv = lib.Server(max_active=1)
+    for w, sos0, d in reqs:
+        rid = srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+        alone.append(srv.wait(rid)[0])
+    srv.close()
+    srv = lib.Server(max_active=4)
+    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+           for w, sos0, d in reqs]
+    mix = [srv.wait(i) for i in ids]
+    srv.close()
+    for a, (b, res) in zip(alone, mix):
+        assert res["status"] == 0
+        assert np.all(np.isfinite(b))
+        assert rel_l2(b - a, a) < 1e-12
+        assert res["rhs_solves"] > 0 and res["latency_ms"] >= res["run_ms"]
+
+
+def test_one_iteration_matches_the_oracle(lib):
+    w = small_workload((32, 32), n_elem=6, freqs=(1.5e6, 3.0e6), seed=8)
+    prob = oracle_problem(w)
+    sos0 = np.full(w.shape, w.c0) + 0.5 * (w.sos - w.c0)
+    m0 = model.contrast_from_sos(sos0, w.c0)
+    m_true = model.contrast_from_sos(w.sos, w.c0)
+    fields_t, d_true = inverse.forward_model(m_true, prob, "lu")
+    d = d_true.astype(np.complex64)
+    ref = inverse.gradient(m0, d.astype(np.complex128), prob, "bicgstab", tol=1e-12)
+    scale = float(np.abs(ref["grad"]).max())
+    p = admm.AdmmParams(lam=1e-3 * scale, rho=0.5 * scale, gamma=1e-3 * scale, n_cg=6)
+    kk = (2 * np.pi * np.asarray(w.freqs) / w.c0) ** 2 * w.h ** 2
+    rf = ref["fields"] * kk[:, None, None, None]
+    g0 = admm.grad_op(m0, w.shape)
+    _, _, _, sos1, _ = admm.admm_tv_step(m0, g0, np.zeros_like(g0), ref["grad"], ref["fields"],
+                                         rf, prob, p)
+    srv = lib.Server(max_active=2)
+    rid = srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, n_iter=1, lam=p.lam,
+                     rho=p.rho, gamma=p.gamma, n_cg=p.n_cg)
+    sos, res = srv.wait(rid)
+    srv.close()
+    assert res["status"] == 0
+    assert rel_l2(sos - sos0, sos1 - sos0) < 1e-3
+    assert abs(res["misfit_first"] - ref["misfit"]) <= 1e-3 * ref["misfit"]
+
+
+def test_admission_respects_the_budget(lib):
+    reqs = _requests()[:3]
+    import ctypes
+    from paper_2604_15796_gb300.libfwi import FwiError
+    sizes = []
+    for w, _, _ in reqs:
+        desc, keep = lib.make_desc(w.shape, w.h, w.c0, w.elem, w.freqs)
+        sizes.append(int(lib.fwi_workspace_bytes(ctypes.byref(desc))))
+        del keep
+    big = max(sizes)
+    budget = int(1.6 * big) + (8 << 20)
+    srv = lib.Server(hbm_budget=budget, max_active=3)
+    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+           for w, sos0, d in reqs]
+    for i in ids:
+        _, res = srv.wait(i)
+        assert res["status"] == 0 and res["bytes"] <= budget
+    w, sos0, d = _requests()[1]
+    small = lib.Server(hbm_budget=1 << 20, max_active=1)
+    with pytest.raises(FwiError) as e:
+        small.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+    assert e.value.status == lib.FWI_ERR_NOMEM
+    small.close()
+    srv.close()
