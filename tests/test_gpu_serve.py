@@ -22,33 +22,45 @@ def lib():
     return libfwi
 
 
+_CACHE = {}
+
+
 def _requests():
+    """Small reconstructions: observed data = oracle forward data of the
+    phantom; start = half the phantom's SoS perturbation; ADMM weights
+    scaled to the oracle gradient at the start."""
+    if "reqs" in _CACHE:
+        return _CACHE["reqs"]
     specs = [((32, 32), 6, (1.5e6, 3.0e6), 1), ((64, 64), 8, (1.0e6, 2.0e6, 3.0e6), 2),
              ((16, 64), 5, (2.0e6,), 3), ((8, 8, 16), 4, (1.0e6, 2.0e6), 4),
              ((32, 32), 4, (2.5e6,), 5)]
     reqs = []
     for shape, ne, freqs, seed in specs:
         w = small_workload(shape, n_elem=ne, freqs=freqs, seed=seed)
+        prob = oracle_problem(w)
         sos0 = np.full(w.shape, w.c0) + 0.5 * (w.sos - w.c0)
-        d = 1e-6 * phantoms.complex_normal((w.n_freq, w.n_elem, w.n_elem), 100 + seed)
-        reqs.append((w, sos0, d.astype(np.complex64)))
+        _, d = inverse.forward_model(model.contrast_from_sos(w.sos, w.c0), prob, "bicgstab",
+                                     tol=1e-12)
+        g = inverse.gradient(model.contrast_from_sos(sos0, w.c0), d, prob, "bicgstab",
+                             tol=1e-10)["grad"]
+        sc = float(np.abs(g).max())
+        params = dict(n_iter=2, lam=1e-3 * sc, rho=0.5 * sc, gamma=1e-3 * sc, n_cg=4)
+        reqs.append((w, sos0, d.astype(np.complex64), params))
+    _CACHE["reqs"] = reqs
     return reqs
-
-
-PARAMS = dict(n_iter=2, lam=1e-9, rho=1e-6, gamma=1e-8, n_cg=4)
 
 
 def test_results_are_the_same_alone_and_in_the_mix(lib):
     reqs = _requests()
     alone = []
     srv = lib.Server(max_active=1)
-    for w, sos0, d in reqs:
-        rid = srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+    for w, sos0, d, prm in reqs:
+        rid = srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **prm)
         alone.append(srv.wait(rid)[0])
     srv.close()
     srv = lib.Server(max_active=4)
-    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
-           for w, sos0, d in reqs]
+    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **prm)
+           for w, sos0, d, prm in reqs]
     mix = [srv.wait(i) for i in ids]
     srv.close()
     for a, (b, res) in zip(alone, mix):
@@ -89,22 +101,22 @@ def test_admission_respects_the_budget(lib):
     import ctypes
     from paper_2604_15796_gb300.libfwi import FwiError
     sizes = []
-    for w, _, _ in reqs:
+    for w, _, _, _ in reqs:
         desc, keep = lib.make_desc(w.shape, w.h, w.c0, w.elem, w.freqs)
         sizes.append(int(lib.fwi_workspace_bytes(ctypes.byref(desc))))
         del keep
     big = max(sizes)
     budget = int(1.6 * big) + (8 << 20)
     srv = lib.Server(hbm_budget=budget, max_active=3)
-    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
-           for w, sos0, d in reqs]
+    ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **prm)
+           for w, sos0, d, prm in reqs]
     for i in ids:
         _, res = srv.wait(i)
         assert res["status"] == 0 and res["bytes"] <= budget
-    w, sos0, d = _requests()[1]
+    w, sos0, d, prm = _requests()[1]
     small = lib.Server(hbm_budget=1 << 20, max_active=1)
     with pytest.raises(FwiError) as e:
-        small.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **PARAMS)
+        small.submit(w.shape, w.h, w.c0, w.elem, w.freqs, sos0, d, **prm)
     assert e.value.status == lib.FWI_ERR_NOMEM
     small.close()
     srv.close()
