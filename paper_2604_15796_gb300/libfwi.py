@@ -367,11 +367,11 @@ class Server:
         self._pending = {}
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
-               gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6):
+               gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000):
         """Queue a reconstruction; host numpy inputs (sos0 float64 of ``shape``,
         d_obs complex64 [n_freq][n_elem][n_elem]).  Returns the request id."""
         req = fwi_request()
-        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol)
+        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
@@ -390,16 +390,17 @@ class Server:
         return rid.value
 
     def wait(self, rid):
-        """Block until request ``rid`` completes: (sos ndarray, result dict)."""
+        """Block until request ``rid`` completes: (sos ndarray or None, result
+        dict with the reconstruction's fwi_status in "status")."""
         shape = self._pending.pop(rid)
-        sos = np.empty(shape, dtype=np.float64)
+        sos = np.full(shape, np.nan, dtype=np.float64)
         res = fwi_request_result()
         st = fwi_server_wait(self.handle, ctypes.c_longlong(rid),
                              sos.ctypes.data_as(POINTER(c_double)), byref(res))
         out = {k: getattr(res, k) for k, _ in fwi_request_result._fields_}
-        if st != FWI_OK:
+        if st == FWI_ERR_INVALID_ARG and res.status == FWI_OK:
             raise FwiError(st, fwi_last_error(None).decode())
-        return sos, out
+        return (sos if out["status"] == FWI_OK else None), out
 
     def stats(self):
         a, q, b = c_int(), c_int(), c_size_t()

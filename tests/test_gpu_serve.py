@@ -66,7 +66,7 @@ def test_results_are_the_same_alone_and_in_the_mix(lib):
     for a, (b, res) in zip(alone, mix):
         assert res["status"] == 0
         assert np.all(np.isfinite(b))
-        assert rel_l2(b - a, a) < 1e-12
+        assert rel_l2(b, a) < 1e-12  # bitwise in practice: independent contexts
         assert res["rhs_solves"] > 0 and res["latency_ms"] >= res["run_ms"]
 
 
