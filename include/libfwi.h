@@ -304,6 +304,23 @@ FWI_API fwi_status fwi_set_profiling(fwi_ctx* ctx, int on);
 FWI_API fwi_status fwi_get_stats(const fwi_ctx* ctx, fwi_stats* out);
 FWI_API fwi_status fwi_reset_stats(fwi_ctx* ctx);
 
+/* Tile-shape tuning of the operator passes.  fwi_create times every
+   variant on the context's batch (unless the environment variable
+   LIBFWI_AUTOTUNE=0) and keeps the fastest; choices are cached in
+   $LIBFWI_TUNE_CACHE (default ~/.cache/libfwi/autotune.txt).  Variants change
+   only how many lines / columns a thread block holds: results are
+   bitwise identical for every variant.  fwi_set_tuning forces variants. */
+typedef struct fwi_tuning {
+  int row_fwd_variant;  /* 0: 128 threads per CTA, 1: 64, 2: 256 */
+  int row_inv_variant;
+  int col_variant;      /* 0: default column tile, 1: half width */
+  int col_y_variant;    /* 3-D y passes */
+  int tuned;            /* 1 if chosen by timing */
+  float ms[4][4];       /* measured ms per pass kind and variant (0: not timed) */
+} fwi_tuning;
+FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
+FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);
+
 /* Library version string. */
 FWI_API const char* fwi_version(void);
 

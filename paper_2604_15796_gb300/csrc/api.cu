@@ -69,7 +69,7 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.csz = (d->precision == FWI_FP64) ? 16 : 8;
   const int lpc = (d->precision == FWI_FP64) ? Lsop<double>::row_lines_per_cta(L.lx)
                                              : Lsop<float>::row_lines_per_cta(L.lx);
-  L.ntiles = (L.rows + lpc - 1) / lpc;
+  L.ntiles = (L.rows + lpc - 1) / lpc;  // default tile shape (informational)
   const long long P = (long long)L.lx * L.ly * L.lz;
   const long long NE2 = (long long)L.n_elem * L.n_elem;
   const int nbe = (L.n_elem + 63) / 64;
@@ -81,7 +81,8 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.b_kv = (size_t)L.batch * L.N * L.csz;
   L.b_plane1 = (size_t)L.batch * L.rows * L.lx * L.csz;
   L.b_plane2 = (d->dim == 3) ? (size_t)L.batch * L.nz * L.ly * L.lx * L.csz : 0;
-  L.b_small = (size_t)L.batch * (sizeof(Scal) + NSLOT * L.ntiles * sizeof(double2) + sizeof(int)) +
+  L.b_small = (size_t)L.batch * (sizeof(Scal) + NSLOT * (size_t)L.rows * sizeof(double2) +
+                                 sizeof(int)) +
               64 + (size_t)L.n_freq * NE2 * (16 + L.csz) + 3 * 1024 * L.csz;
   size_t js1 = (size_t)L.split * L.n_freq * NE2 * L.csz;
   size_t js2 = (size_t)8 * L.N * sizeof(double2);
@@ -200,7 +201,7 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   if (L.b_plane2) alloc(&c->plane2, L.b_plane2);
   alloc(&c->mF, (size_t)L.N * L.csz);
   alloc((void**)&c->scal, sizeof(Scal) * L.batch);
-  alloc((void**)&c->partial, sizeof(double2) * NSLOT * (size_t)L.ntiles * L.batch);
+  alloc((void**)&c->partial, sizeof(double2) * NSLOT * (size_t)L.rows * L.batch);
   alloc((void**)&c->active, sizeof(int) * L.batch);
   alloc((void**)&c->n_active, 64);
   const size_t NE2 = (size_t)L.n_elem * L.n_elem;
@@ -235,6 +236,7 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
     return FWI_ERR_CUDA;
   }
   fwi_status st = setup_operator(c);
+  if (st == FWI_OK) st = autotune(c);
   if (st != FWI_OK) {
     g_create_error = c->err;
     release(c);
@@ -382,6 +384,39 @@ fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
   ctx->err.clear();
   return jac_adjoint(ctx, (const double2*)y, (double2*)z);
+}
+
+fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
+  if (!ctx || !out) return FWI_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->row_fwd_variant = ctx->var_rf;
+  out->row_inv_variant = ctx->var_ri;
+  out->col_variant = ctx->var_cz;
+  out->col_y_variant = ctx->var_cy;
+  out->tuned = ctx->tuned;
+  for (int k = 0; k < 4; ++k)
+    for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
+  return FWI_OK;
+}
+
+fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
+  if (!ctx || !in) return FWI_ERR_INVALID_ARG;
+  const int lims[4] = {ctx->fp64 ? 1 : Lsop<float>::variants(ctx->lx, 0),
+                       ctx->fp64 ? 1 : Lsop<float>::variants(ctx->lx, 1),
+                       ctx->fp64 ? 1 : Lsop<float>::variants(ctx->lz, 2),
+                       (ctx->fp64 || ctx->dim != 3) ? 1 : Lsop<float>::variants(ctx->ly, 2)};
+  const int req[4] = {in->row_fwd_variant, in->row_inv_variant, in->col_variant,
+                      in->col_y_variant};
+  for (int k = 0; k < 4; ++k)
+    if (req[k] < 0 || req[k] >= lims[k]) return fail(ctx, FWI_ERR_INVALID_ARG, "variant out of range");
+  ctx->var_rf = req[0];
+  ctx->var_ri = req[1];
+  ctx->var_cz = req[2];
+  ctx->var_cy = req[3];
+  ctx->tuned = 0;
+  for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second.exec);
+  ctx->graphs.clear();  // captured launches carry the old variants
+  return FWI_OK;
 }
 
 fwi_status fwi_set_profiling(fwi_ctx* ctx, int on) {

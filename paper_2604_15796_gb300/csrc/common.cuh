@@ -48,7 +48,7 @@ template <typename T> struct RowFwdArgs {
   const int* n_active;
   int nb;
   const Scal* scal;
-  double2* partial;    // [B][NSLOT][ntiles]
+  double2* partial;    // [B][NSLOT][rows] per-row partial sums
   int nx;              // samples per input row (L/2, or L if full)
   int rows;            // lines per RHS
   int ntiles;
@@ -89,13 +89,14 @@ template <typename T> struct ColArgs {
 
 // Host-side launch interface, specialised per precision in the
 // instantiation units.  L is the transform length along the pass axis.
+// ``var`` selects a tile-shape variant (0 = default; see Lsop::variants).
 template <typename T> struct Lsop {
   static bool supported(int L);
-  static cudaError_t row_fwd(int L, const RowFwdArgs<T>& a, cudaStream_t s);
-  static cudaError_t row_inv(int L, const RowInvArgs<T>& a, cudaStream_t s);
-  static cudaError_t col(int L, const ColArgs<T>& a, cudaStream_t s);
-  static int row_lines_per_cta(int L);
-  static cudaError_t prepare(int L);  // smem attributes, occupancy
+  static int variants(int L, int kind);  // kind 0 row_fwd, 1 row_inv, 2 col
+  static cudaError_t row_fwd(int L, const RowFwdArgs<T>& a, cudaStream_t s, int var = 0);
+  static cudaError_t row_inv(int L, const RowInvArgs<T>& a, cudaStream_t s, int var = 0);
+  static cudaError_t col(int L, const ColArgs<T>& a, cudaStream_t s, int var = 0);
+  static int row_lines_per_cta(int L, int var = 0);
 };
 
 }  // namespace fwi

@@ -65,6 +65,10 @@ struct fwi_ctx {
   // number of kernel nodes each replay launches
   struct GraphRec { cudaGraphExec_t exec; long long nodes; };
   std::map<std::tuple<const void*, int, int>, GraphRec> graphs;
+  // tile-shape variants of the operator passes (autotuned at creation)
+  int var_rf = 0, var_ri = 0, var_cz = 0, var_cy = 0;
+  int tuned = 0;
+  float tune_ms[4][4] = {};
   // instrumentation (launch counts always; event timing when profiling)
   long long launches = 0;
   bool capturing = false;
@@ -87,6 +91,7 @@ fwi_status fail(fwi_ctx* c, fwi_status s, const std::string& msg);
 fwi_status cuda_fail(fwi_ctx* c, cudaError_t e, const char* where);
 size_t workspace_bytes(const fwi_problem_desc* d, std::string* why);
 fwi_status setup_operator(fwi_ctx* c);
+fwi_status autotune(fwi_ctx* c);
 fwi_status forward_solve(fwi_ctx* c, const void* m, bool warm, fwi_solve_info* info);
 fwi_status adjoint_solve(fwi_ctx* c, const void* m, const void* src, bool conj_src,
                          fwi_solve_info* info);

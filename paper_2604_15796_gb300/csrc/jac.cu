@@ -31,17 +31,31 @@ inline int blocks_for(long long n, int threads, int cap) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// Tile (eb, jb) of grid index ty: all nbe^2 tiles, or (sym) only eb <= jb
+// enumerated column by column.
+__device__ inline void tile_of(int ty, int nbe, int sym, int& eb, int& jb) {
+  if (!sym) {
+    eb = ty % nbe;
+    jb = ty / nbe;
+    return;
+  }
+  jb = 0;
+  while ((jb + 1) * (jb + 2) / 2 <= ty) ++jb;
+  eb = ty - jb * (jb + 1) / 2;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 contract_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ a,
                 const cplx<T>* __restrict__ Q, cplx<T>* __restrict__ part, int NE,
-                long long N, int n_freq, long long chunk) {
+                long long N, int n_freq, long long chunk, int sym) {
   using V = cplx<T>;
   __shared__ V Xs[KC][TB + 1];
   __shared__ V Qs[KC][TB + 1];
   const int s = blockIdx.x;
   const int nbe = (NE + TB - 1) / TB;
-  const int eb = blockIdx.y % nbe, jb = blockIdx.y / nbe;
+  int eb, jb;
+  tile_of(blockIdx.y, nbe, sym, eb, jb);
   const int l = blockIdx.z;
   const int tid = threadIdx.x;
   const int te = tid & 15, tj = tid >> 4;
@@ -101,15 +115,23 @@ contract_kernel(const cplx<T>* __restrict__ X, const cplx<T>* __restrict__ a,
     }
 }
 
-// Y[l][e][j] = scale_l * sum_s part[s][l][e][j]  (FP64, fixed order)
+// Y[l][e][j] = scale_l * sum_s part[s][l][e][j]  (FP64, fixed order); with
+// sym, entries below the computed tiles (eb > jb) are read transposed.
 template <typename T>
 __global__ void contract_reduce_kernel(double2* Y, const cplx<T>* part, int split,
-                                       long long per_split, int NE2, const double* scale) {
+                                       long long per_split, int NE2, const double* scale,
+                                       int NE, int sym) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < per_split;
        i += (long long)gridDim.x * blockDim.x) {
+    long long src = i;
+    if (sym) {
+      const long long l = i / NE2;
+      const int e = (int)((i % NE2) / NE), j = (int)(i % NE);
+      if (e / TB > j / TB) src = l * NE2 + (long long)j * NE + e;
+    }
     double sx = 0.0, sy = 0.0;
     for (int s = 0; s < split; ++s) {
-      const cplx<T> v = part[(long long)s * per_split + i];
+      const cplx<T> v = part[(long long)s * per_split + src];
       sx += (double)v.x;
       sy += (double)v.y;
     }
@@ -329,27 +351,30 @@ template <typename T> struct Jac {
     return split;
   }
 
-  // Y = scale_l * contract(X, a, Q) (c128, [l][e][j])
+  // Y = scale_l * contract(X, a, Q) (c128, [l][e][j]); sym when Q == X
+  // (then Y_l is complex-symmetric and only tiles eb <= jb are computed).
   static fwi_status contract(fwi_ctx* c, const cplx<T>* X, const cplx<T>* a,
                              const cplx<T>* Q, double2* Y) {
     const int nbe = (c->n_elem + TB - 1) / TB;
     const int split = split_for(c);
+    const int sym = (X == Q) ? 1 : 0;
     long long chunk = (c->N + split - 1) / split;
     chunk = ((chunk + KC - 1) / KC) * KC;
-    dim3 grid(split, nbe * nbe, c->n_freq);
+    dim3 grid(split, sym ? nbe * (nbe + 1) / 2 : nbe * nbe, c->n_freq);
     const double fe = (double)c->n_freq * c->n_elem * c->N;
     {
       Prof p(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(cplx<T>),
              8.0 * fe * c->n_elem);
       contract_kernel<T><<<grid, 256, 0, c->stream>>>(X, a, Q, (cplx<T>*)c->jsplit, c->n_elem,
-                                                      c->N, c->n_freq, chunk);
+                                                      c->N, c->n_freq, chunk, sym);
     }
     FWI_CUDA(c, cudaGetLastError());
     const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
     {
       Prof p(c, KC_MISC);
       contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-          Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red);
+          Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red, c->n_elem,
+          sym);
     }
     FWI_CUDA(c, cudaGetLastError());
     return FWI_OK;
@@ -597,7 +622,8 @@ extern "C" fwi_status fwi_contract_pixels_noalloc(const void* X, const void* a, 
   cudaStream_t s = (cudaStream_t)cuda_stream;
   dim3 grid((unsigned)split, nbe * nbe, n_freq);
   contract_kernel<float><<<grid, 256, 0, s>>>((const float2*)X, (const float2*)a,
-                                              (const float2*)Q, part, n_elem, N, n_freq, chunk);
+                                              (const float2*)Q, part, n_elem, N, n_freq, chunk,
+                                              0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc launch");
   contract_reduce_static_kernel<<<blocks_for(per, 256, sms * 8), 256, 0, s>>>(

@@ -16,7 +16,12 @@
 // partial sums of the t-pass, so the x/r/p update fuses into the next
 // forward row pass.  The last update of each finished RHS is applied by a
 // final elementwise pass.
+#include <sys/stat.h>
+
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
 #include <vector>
 
 #include "ctx.cuh"
@@ -38,10 +43,10 @@ __device__ inline double2 zdiv(double2 a, double2 b) {
 __device__ inline double zabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 __device__ inline bool zfinite(double2 a) { return isfinite(a.x) && isfinite(a.y); }
 
-// Warp-cooperative fixed-order sum of one slot's tile partials.
-__device__ inline double2 warp_slot_sum(const double2* part, int ntiles, int lane) {
+// Warp-cooperative fixed-order sum of one slot's per-row partials.
+__device__ inline double2 warp_slot_sum(const double2* part, int nparts, int lane) {
   double2 s = make_double2(0.0, 0.0);
-  for (int i = lane; i < ntiles; i += 32) s = zadd(s, part[i]);
+  for (int i = lane; i < nparts; i += 32) s = zadd(s, part[i]);
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     s.x += __shfl_xor_sync(0xffffffffu, s.x, off);
@@ -52,14 +57,14 @@ __device__ inline double2 warp_slot_sum(const double2* part, int ntiles, int lan
 
 // S0: initial state from the INIT (slot 0 = ||b||^2) or R0 (slot 0 =
 // ||r0||^2, slot 1 = ||b||^2) partials.
-__global__ void s0_kernel(Scal* scal, const double2* partial, int ntiles, int nb,
+__global__ void s0_kernel(Scal* scal, const double2* partial, int nparts, int nb,
                           int from_r0, double tol2) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= nb) return;
-  const double2* p = partial + (long long)warp * NSLOT * ntiles;
-  const double r2 = warp_slot_sum(p, ntiles, lane).x;
-  const double b2 = from_r0 ? warp_slot_sum(p + ntiles, ntiles, lane).x : r2;
+  const double2* p = partial + (long long)warp * NSLOT * nparts;
+  const double r2 = warp_slot_sum(p, nparts, lane).x;
+  const double b2 = from_r0 ? warp_slot_sum(p + nparts, nparts, lane).x : r2;
   if (lane == 0) {
     Scal s;
     s.rho = make_double2(r2, 0.0);
@@ -78,13 +83,13 @@ __global__ void s0_kernel(Scal* scal, const double2* partial, int ntiles, int nb
 }
 
 // S1: alpha = rho / <rhat, v>.
-__global__ void s1_kernel(Scal* scal, const double2* partial, int ntiles,
+__global__ void s1_kernel(Scal* scal, const double2* partial, int nparts,
                           const int* active, const int* n_active) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= *n_active) return;
   const int rhs = active[warp];
-  const double2 rv = warp_slot_sum(partial + (long long)rhs * NSLOT * ntiles, ntiles, lane);
+  const double2 rv = warp_slot_sum(partial + (long long)rhs * NSLOT * nparts, nparts, lane);
   if (lane == 0) {
     Scal& s = scal[rhs];
     if (!zfinite(rv)) {
@@ -100,19 +105,19 @@ __global__ void s1_kernel(Scal* scal, const double2* partial, int ntiles,
 }
 
 // S2: omega, rho_new, ||r_new||^2, stopping test, beta.
-__global__ void s2_kernel(Scal* scal, const double2* partial, int ntiles,
+__global__ void s2_kernel(Scal* scal, const double2* partial, int nparts,
                           const int* active, const int* n_active, double tol2,
                           int max_it) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= *n_active) return;
   const int rhs = active[warp];
-  const double2* p = partial + (long long)rhs * NSLOT * ntiles;
-  const double2 ts = warp_slot_sum(p, ntiles, lane);
-  const double tt = warp_slot_sum(p + ntiles, ntiles, lane).x;
-  const double2 rt = warp_slot_sum(p + 2 * ntiles, ntiles, lane);
-  const double2 rs = warp_slot_sum(p + 3 * ntiles, ntiles, lane);
-  const double ss = warp_slot_sum(p + 4 * ntiles, ntiles, lane).x;
+  const double2* p = partial + (long long)rhs * NSLOT * nparts;
+  const double2 ts = warp_slot_sum(p, nparts, lane);
+  const double tt = warp_slot_sum(p + nparts, nparts, lane).x;
+  const double2 rt = warp_slot_sum(p + 2 * nparts, nparts, lane);
+  const double2 rs = warp_slot_sum(p + 3 * nparts, nparts, lane);
+  const double ss = warp_slot_sum(p + 4 * nparts, nparts, lane).x;
   if (lane != 0) return;
   Scal& s = scal[rhs];
   s.iters += 1;
@@ -247,13 +252,21 @@ template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int 
   r.plane = (cplx<T>*)c->plane1; r.tw = (const cplx<T>*)c->tw_x;
   r.active = c->active; r.n_active = c->n_active; r.nb = nb;
   r.scal = c->scal; r.partial = c->partial;
-  r.nx = c->nx; r.rows = c->rows; r.ntiles = c->ntiles; r.N = c->N;
+  r.nx = c->nx; r.rows = c->rows; r.N = c->N;
+  {
+    const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_rf);
+    r.ntiles = (c->rows + lpc - 1) / lpc;
+  }
   RowInvArgs<T>& q = b.ri;
   q.plane = (const cplx<T>*)c->plane1; q.m = (const cplx<T>*)c->mF;
   q.X = X; q.R = R; q.RH = RH; q.P = P; q.V = V; q.Tt = Tt;
   q.tw = (const cplx<T>*)c->tw_x;
   q.active = c->active; q.n_active = c->n_active; q.nb = nb;
-  q.partial = c->partial; q.nx = c->nx; q.rows = c->rows; q.ntiles = c->ntiles; q.N = c->N;
+  q.partial = c->partial; q.nx = c->nx; q.rows = c->rows; q.N = c->N;
+  {
+    const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_ri);
+    q.ntiles = (c->rows + lpc - 1) / lpc;
+  }
   const long long lyx = (long long)c->ly * c->lx;
   if (c->dim == 2) {
     ColArgs<T>& z = b.cz;
@@ -321,22 +334,22 @@ template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list, doub
   if (!use_list) z.active = nullptr;
   if (c->dim == 2) {
     Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
-    return Lsop<T>::col(c->lz, z, c->stream);
+    return Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
   }
   ColArgs<T> y = b.cy_fwd, w = b.cy_inv;
   if (!use_list) { y.active = nullptr; w.active = nullptr; }
   cudaError_t e;
   {
     Prof p(c, KC_COL_FWD, units * pass_bytes<T>(c, KC_COL_FWD));
-    e = Lsop<T>::col(c->ly, y, c->stream);
+    e = Lsop<T>::col(c->ly, y, c->stream, c->var_cy);
   }
   if (e == cudaSuccess) {
     Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
-    e = Lsop<T>::col(c->lz, z, c->stream);
+    e = Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
   }
   if (e == cudaSuccess) {
     Prof p(c, KC_COL_INV, units * pass_bytes<T>(c, KC_COL_INV));
-    e = Lsop<T>::col(c->ly, w, c->stream);
+    e = Lsop<T>::col(c->ly, w, c->stream, c->var_cy);
   }
   return e;
 }
@@ -350,7 +363,7 @@ template <typename T> cudaError_t row_fwd(const Batch<T>& b, int mode, bool use_
   const int k = mode == RF_INIT ? KC_ROW_FWD_INIT : mode == RF_ITER ? KC_ROW_FWD_ITER
               : mode == RF_S ? KC_ROW_FWD_S : KC_ROW_FWD_PLAIN;
   Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
-  return Lsop<T>::row_fwd(b.c->lx, r, b.c->stream);
+  return Lsop<T>::row_fwd(b.c->lx, r, b.c->stream, b.c->var_rf);
 }
 
 template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_list,
@@ -362,7 +375,7 @@ template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_
   if (!use_list) q.active = nullptr;
   const int k = mode == RI_V ? KC_ROW_INV_V : mode == RI_T ? KC_ROW_INV_T : KC_ROW_INV_OTHER;
   Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
-  return Lsop<T>::row_inv(b.c->lx, q, b.c->stream);
+  return Lsop<T>::row_inv(b.c->lx, q, b.c->stream, b.c->var_ri);
 }
 
 // Host copy of the active count (profiling mode only: synchronises).
@@ -385,7 +398,7 @@ template <typename T> cudaError_t iteration(const Batch<T>& b, double units) {
   if (e == cudaSuccess) e = row_inv(b, RI_V, true, units);
   if (e == cudaSuccess) {
     Prof p(c, KC_KRYLOV_SCALAR);
-    s1_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active, c->n_active);
+    s1_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, c->active, c->n_active);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = row_fwd(b, RF_S, true, units);
@@ -393,7 +406,7 @@ template <typename T> cudaError_t iteration(const Batch<T>& b, double units) {
   if (e == cudaSuccess) e = row_inv(b, RI_T, true, units);
   if (e == cudaSuccess) {
     Prof p(c, KC_KRYLOV_SCALAR);
-    s2_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, c->active,
+    s2_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, c->active,
                                         c->n_active, tol2, c->max_it);
     e = cudaGetLastError();
   }
@@ -421,13 +434,13 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
   if (!warm) {
     FWI_CUDA(c, row_fwd(b, RF_INIT, false, nb, bvec, conj_b));
     Prof p(c, KC_KRYLOV_SCALAR);
-    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 0, tol2);
+    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, nb, 0, tol2);
   } else {
     FWI_CUDA(c, row_fwd(b, RF_PLAIN, false, nb, X, 0));
     FWI_CUDA(c, columns(b, false, nb));
     FWI_CUDA(c, row_inv(b, RI_R0, false, nb, nullptr, nullptr, bvec, conj_b));
     Prof p(c, KC_KRYLOV_SCALAR);
-    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->ntiles, nb, 1, tol2);
+    s0_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, nb, 1, tol2);
   }
   FWI_CUDA(c, cudaGetLastError());
   {
@@ -577,7 +590,151 @@ fwi_status apply_op_t(fwi_ctx* c, int kind, const void* m, int freq, int n_rhs,
   return FWI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: times every tile-shape variant of the operator passes on the
+// context's full batch (scratch vectors) and keeps the fastest.  Variants
+// differ only in how many lines / columns a CTA holds; every one gives
+// bitwise-identical results.  Choices are cached in a text file keyed by
+// (architecture, precision, length, batch, pass).
+std::string tune_cache_path() {
+  const char* p = std::getenv("LIBFWI_TUNE_CACHE");
+  if (p && *p) return p;
+  const char* h = std::getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/libfwi/autotune.txt";
+}
+
+std::map<std::string, int> read_tune_cache() {
+  std::map<std::string, int> m;
+  FILE* f = std::fopen(tune_cache_path().c_str(), "r");
+  if (!f) return m;
+  char key[256];
+  int v = 0;
+  while (std::fscanf(f, "%255s %d", key, &v) == 2) m[key] = v;
+  std::fclose(f);
+  return m;
+}
+
+void append_tune_cache(const std::vector<std::pair<std::string, int>>& rows) {
+  const std::string path = tune_cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {
+    std::string dir = path.substr(0, slash);
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);  // parents, no shell
+  }
+  FILE* f = std::fopen(path.c_str(), "a");
+  if (!f) return;
+  for (auto& r : rows) std::fprintf(f, "%s %d\n", r.first.c_str(), r.second);
+  std::fclose(f);
+}
+
+template <typename T>
+fwi_status autotune_t(fwi_ctx* c) {
+  const char* env = std::getenv("LIBFWI_AUTOTUNE");
+  if (env && env[0] == '0') return FWI_OK;
+  const int nvr = Lsop<T>::variants(c->lx, 0);
+  const int nvc = Lsop<T>::variants(c->lz, 2);
+  const int nvy = c->dim == 3 ? Lsop<T>::variants(c->ly, 2) : 1;
+  if (nvr <= 1 && nvc <= 1 && nvy <= 1) return FWI_OK;
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  char base[160];
+  std::snprintf(base, sizeof(base), "sm%d%d|%s|d%d|%dx%dx%d|b%d|", major, minor,
+                sizeof(T) == 4 ? "c64" : "c128", c->dim, c->lx, c->ly, c->lz, c->batch);
+  const std::string kb(base);
+  const char* kinds[4] = {"row_fwd", "row_inv", "col_z", "col_y"};
+  std::map<std::string, int> cache = read_tune_cache();
+  int* vars[4] = {&c->var_rf, &c->var_ri, &c->var_cz, &c->var_cy};
+  const int nv[4] = {nvr, Lsop<T>::variants(c->lx, 1), nvc, nvy};
+  bool all_cached = true;
+  for (int k = 0; k < 4; ++k) {
+    auto it = cache.find(kb + kinds[k]);
+    if (nv[k] > 1 && it == cache.end()) all_cached = false;
+  }
+  if (all_cached) {
+    for (int k = 0; k < 4; ++k) {
+      auto it = cache.find(kb + kinds[k]);
+      if (it != cache.end() && it->second >= 0 && it->second < nv[k]) *vars[k] = it->second;
+    }
+    return FWI_OK;
+  }
+  // scratch: zero input vectors in kv[0], output into kv[1]
+  const long long nvec = c->N * (long long)c->batch;
+  FWI_CUDA(c, cudaMemsetAsync(c->kv[0], 0, sizeof(cplx<T>) * nvec, c->stream));
+  const bool saved_prof = c->profiling;
+  c->profiling = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FWI_CUDA(c, cudaEventCreate(&e0));
+  FWI_CUDA(c, cudaEventCreate(&e1));
+  auto time_it = [&](auto launch) -> float {
+    cudaError_t e = launch();  // warm-up (also sets up the launch grid)
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+    if (e != cudaSuccess) return -1.f;
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch();
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return e == cudaSuccess ? ms / 3.f : -1.f;
+  };
+  std::vector<std::pair<std::string, int>> rows;
+  Batch<T> b = make_batch<T>(c, (cplx<T>*)c->kv[2], 0, c->batch);
+  b.cz.freq_fixed = 0;
+  const cplx<T>* src = (const cplx<T>*)c->kv[0];
+  cplx<T>* dst = (cplx<T>*)c->kv[1];
+  for (int k = 0; k < 4; ++k) {
+    if (nv[k] <= 1) continue;
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v < nv[k]; ++v) {
+      float ms = -1.f;
+      if (k == 0) {
+        RowFwdArgs<T> r = b.rf;
+        r.mode = RF_PLAIN; r.in = src; r.use_m = 1; r.active = nullptr;
+        const int lpc = Lsop<T>::row_lines_per_cta(c->lx, v);
+        r.ntiles = (c->rows + lpc - 1) / lpc;
+        ms = time_it([&] { return Lsop<T>::row_fwd(c->lx, r, c->stream, v); });
+      } else if (k == 1) {
+        RowInvArgs<T> q = b.ri;
+        q.mode = RI_A; q.in = src; q.out = dst; q.active = nullptr;
+        const int lpc = Lsop<T>::row_lines_per_cta(c->lx, v);
+        q.ntiles = (c->rows + lpc - 1) / lpc;
+        ms = time_it([&] { return Lsop<T>::row_inv(c->lx, q, c->stream, v); });
+      } else if (k == 2) {
+        ColArgs<T> z = b.cz;
+        z.active = nullptr;
+        ms = time_it([&] { return Lsop<T>::col(c->lz, z, c->stream, v); });
+      } else {
+        ColArgs<T> y = b.cy_fwd;
+        y.active = nullptr;
+        ms = time_it([&] { return Lsop<T>::col(c->ly, y, c->stream, v); });
+      }
+      c->tune_ms[k][v] = ms;
+      if (ms > 0.f && ms < best) {
+        best = ms;
+        bestv = v;
+      }
+    }
+    *vars[k] = bestv;
+    rows.emplace_back(kb + kinds[k], bestv);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->profiling = saved_prof;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+  c->tuned = 1;
+  append_tune_cache(rows);
+  return FWI_OK;
+}
+
 }  // namespace
+
+fwi_status autotune(fwi_ctx* c) {
+  return c->fp64 ? autotune_t<double>(c) : autotune_t<float>(c);
+}
 
 fwi_status forward_solve(fwi_ctx* c, const void* m, bool warm, fwi_solve_info* info) {
   fwi_status st = set_contrast(c, m);

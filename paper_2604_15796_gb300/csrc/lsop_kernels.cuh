@@ -52,6 +52,28 @@ __device__ __forceinline__ void block_sum(A (&acc)[NV], double (&out)[NV]) {
   }
 }
 
+// Per-line fixed-order sums of NV per-thread values (threads t = 0..TL-1 of
+// each line, in order).  The result does not depend on how many lines a CTA
+// holds, so tile shapes can be tuned without changing any bit of the
+// partial inner products.  Thread t == 0 of each line receives the sums.
+template <int NTHREADS, int NV, typename A>
+__device__ __forceinline__ void line_sum(const A (&acc)[NV], int line, int t, int TL,
+                                         double (&out)[NV]) {
+  __shared__ double red[NTHREADS][NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = (double)acc[k];
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+      for (int u = 0; u < TL; ++u) s += red[line * TL + u][k];
+      out[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
 template <typename T> struct Coef { cplx<T> alpha, omega, beta; };
 
 template <typename T>
@@ -326,64 +348,108 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
       }
     }
     if (a.mode == RF_INIT) {
-      T accs[1] = {acc};
+      const T accs[1] = {acc};
       double tot[1];
-      block_sum<1>(accs, tot);
-      if (threadIdx.x == 0)
-        a.partial[((long long)rhs * NSLOT + 0) * a.ntiles + tile] = make_double2(tot[0], 0.0);
+      line_sum<LPC * P::TL, 1>(accs, line, t, P::TL, tot);
+      if (t == 0 && valid)
+        a.partial[((long long)rhs * NSLOT + 0) * a.rows + row] = make_double2(tot[0], 0.0);
     }
   }
 }
 
 // --------------------------------------------------------------------------
-// Row inverse pass with fused epilogues.  acc slots (complex, re/im pairs):
+// Row inverse pass with fused epilogues.  The epilogue operands of the
+// item (p and rhat, s and rhat, ...) are loaded before the FFT phases so
+// that their latency overlaps the transform.  acc slots (complex pairs):
 //   RI_V : 0 <rhat, v>
 //   RI_T : 0 <t, s>, 1 <t, t>, 2 <rhat, t>, 3 <rhat, s>, 4 <s, s>
 //   RI_R0: 0 <r, r>, 1 <b, b>
+template <class P> struct RowSlots {
+  static constexpr int N = PlanTraits<P>::CA * P::H1;  // output samples per thread
+};
+
 template <class P, typename T, int MODE>
-__device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs, int row,
-                                         const cplx<T>* v, T (&acc)[2 * NSLOT]) {
+__device__ __forceinline__ void ri_prefetch(const RowInvArgs<T>& a, int t, int rhs, int row,
+                                            cplx<T>* q0, cplx<T>* q1) {
   using V = cplx<T>;
   constexpr int GP = row_gp<P>();
   const V* __restrict__ in = a.in;
-  V* __restrict__ out = a.out;
   const V* __restrict__ mm = a.m;
   const V* __restrict__ Bv = a.B;
-  V* __restrict__ X = a.X;
+  const V* __restrict__ X = a.X;
+  const V* __restrict__ R = a.R;
+  const V* __restrict__ RH = a.RH;
+  const V* __restrict__ Pp = a.P;
+  const long long vb = (long long)rhs * a.N + (long long)row * a.nx;
+  const long long mb = (long long)row * a.nx;
+#pragma unroll
+  for (int i = 0; i < PlanTraits<P>::CA; ++i) {
+#pragma unroll
+    for (int m = 0; m < P::H1; ++m) {
+      const int j = i * P::H1 + m;
+      int n2, n1;
+      if (!slotA<P, GP>(t, i, m, n2, n1)) continue;
+      const int x = P::R2 * n1 + n2;
+      const long long idx = vb + x;
+      if (MODE == RI_A) {
+        q0[j] = in[idx];
+      } else if (MODE == RI_AH) {
+        q0[j] = in[idx];
+        q1[j] = mm[mb + x];
+      } else if (MODE == RI_V) {
+        q0[j] = Pp[idx];
+        q1[j] = RH[idx];
+      } else if (MODE == RI_T) {
+        q0[j] = R[idx];
+        q1[j] = RH[idx];
+      } else if (MODE == RI_R0) {
+        q0[j] = X[idx];
+        q1[j] = Bv[idx];
+      }
+    }
+  }
+}
+
+template <class P, typename T, int MODE>
+__device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs, int row,
+                                         const cplx<T>* v, const cplx<T>* q0,
+                                         const cplx<T>* q1, T (&acc)[2 * NSLOT]) {
+  using V = cplx<T>;
+  constexpr int GP = row_gp<P>();
+  V* __restrict__ out = a.out;
   V* __restrict__ R = a.R;
   V* __restrict__ RH = a.RH;
   V* __restrict__ Pp = a.P;
   V* __restrict__ Vv = a.V;
   V* __restrict__ Tt = a.Tt;
   const long long vb = (long long)rhs * a.N + (long long)row * a.nx;
-  const long long mb = (long long)row * a.nx;
 #pragma unroll
   for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-    for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+    for (int m = 0; m < P::H1; ++m) {
+      const int j = i * P::H1 + m;
       int n2, n1;
-      const bool ok = slotA<P, GP>(t, i, m, n2, n1);
-      if (!ok || n1 >= P::H1) continue;
-      const int x = P::R2 * n1 + n2;
-      const long long idx = vb + x;
+      if (!slotA<P, GP>(t, i, m, n2, n1)) continue;
+      const long long idx = vb + P::R2 * n1 + n2;
+      // phase-D output slot of sample n1 (< H1): same position as in phase A
       const V y = v[i * PlanTraits<P>::MA + m];
       if (MODE == RI_K) {
         out[idx] = y;
       } else if (MODE == RI_A) {
-        out[idx] = csub(in[idx], y);
+        out[idx] = csub(q0[j], y);
       } else if (MODE == RI_AH) {
-        out[idx] = csub(in[idx], cconj(cmul(mm[mb + x], y)));
+        out[idx] = csub(q0[j], cconj(cmul(q1[j], y)));
       } else if (MODE == RI_V) {
-        const V vv = csub(Pp[idx], y);
+        const V vv = csub(q0[j], y);
         Vv[idx] = vv;
-        const V rh = RH[idx];
+        const V rh = q1[j];
         acc[0] += rh.x * vv.x + rh.y * vv.y;
         acc[1] += rh.x * vv.y - rh.y * vv.x;
       } else if (MODE == RI_T) {
-        const V s = R[idx];
+        const V s = q0[j];
         const V tt = csub(s, y);
         Tt[idx] = tt;
-        const V rh = RH[idx];
+        const V rh = q1[j];
         acc[0] += tt.x * s.x + tt.y * s.y;    // <t, s>
         acc[1] += tt.x * s.y - tt.y * s.x;
         acc[2] += tt.x * tt.x + tt.y * tt.y;  // <t, t>
@@ -393,9 +459,9 @@ __device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs,
         acc[7] += rh.x * s.y - rh.y * s.x;
         acc[8] += s.x * s.x + s.y * s.y;      // <s, s>
       } else {  // RI_R0: r = b - (x - K m x)
-        V b = Bv[idx];
+        V b = q1[j];
         if (a.conj_b) b = cconj(b);
-        const V r = csub(b, csub(X[idx], y));
+        const V r = csub(b, csub(q0[j], y));
         R[idx] = r;
         RH[idx] = r;
         Pp[idx] = r;
@@ -406,20 +472,15 @@ __device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs,
   }
 }
 
-template <class P, typename T, int LPC>
-__global__ void __launch_bounds__(LPC * P::TL)
-row_inv_kernel(const RowInvArgs<T> a) {
+template <class P, typename T, int LPC, int MODE>
+__device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* sml, int line,
+                                              int t) {
   using V = cplx<T>;
   constexpr int GP = row_gp<P>();
-  extern __shared__ __align__(16) unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  constexpr int LSTR = P::span(1) + 1;
-  const int line = threadIdx.x / P::TL;
-  const int t = threadIdx.x - line * P::TL;
-  V* sml = sm + line * LSTR;
+  constexpr bool dots = MODE == RI_V || MODE == RI_T || MODE == RI_R0;
+  constexpr int NS = RowSlots<P>::N;
   const int nact = a.active ? *a.n_active : a.nb;
   const long long items = (long long)nact * a.ntiles;
-  const bool dots = a.mode == RI_V || a.mode == RI_T || a.mode == RI_R0;
   for (long long item = blockIdx.x; item < items; item += gridDim.x) {
     const int slot = (int)(item / a.ntiles);
     const int tile = (int)(item - (long long)slot * a.ntiles);
@@ -427,6 +488,7 @@ row_inv_kernel(const RowInvArgs<T> a) {
     const int row = tile * LPC + line;
     const bool valid = row < a.rows;
     V v[P::E];
+    V q0[NS], q1[NS];
     if (valid) {
       const V* __restrict__ in = a.plane + ((long long)rhs * a.rows + row) * P::L;
 #pragma unroll
@@ -438,6 +500,7 @@ row_inv_kernel(const RowInvArgs<T> a) {
             v[i * PlanTraits<P>::MB + kp] = in[k1 + P::R1 * k2];
         }
       }
+      ri_prefetch<P, T, MODE>(a, t, rhs, row, q0, q1);
     }
     __syncthreads();
     if (valid) ph_C<P, GP, T>(t, v, sml, 1, 1, a.tw);
@@ -447,25 +510,38 @@ row_inv_kernel(const RowInvArgs<T> a) {
     for (int k = 0; k < 2 * NSLOT; ++k) acc[k] = T(0);
     if (valid) {
       ph_D<P, GP, T>(t, v, sml, 1, 1);
-      switch (a.mode) {
-        case RI_K: ri_store<P, T, RI_K>(a, t, rhs, row, v, acc); break;
-        case RI_A: ri_store<P, T, RI_A>(a, t, rhs, row, v, acc); break;
-        case RI_AH: ri_store<P, T, RI_AH>(a, t, rhs, row, v, acc); break;
-        case RI_V: ri_store<P, T, RI_V>(a, t, rhs, row, v, acc); break;
-        case RI_T: ri_store<P, T, RI_T>(a, t, rhs, row, v, acc); break;
-        default: ri_store<P, T, RI_R0>(a, t, rhs, row, v, acc); break;
-      }
+      ri_store<P, T, MODE>(a, t, rhs, row, v, q0, q1, acc);
     }
     if (dots) {
       double tot[2 * NSLOT];
-      block_sum<2 * NSLOT>(acc, tot);
-      if (threadIdx.x == 0) {
-        double2* dst = a.partial + (long long)rhs * NSLOT * a.ntiles + tile;
+      line_sum<LPC * P::TL, 2 * NSLOT>(acc, line, t, P::TL, tot);
+      if (t == 0 && valid) {
+        double2* dst = a.partial + (long long)rhs * NSLOT * a.rows + row;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k)
-          dst[(long long)k * a.ntiles] = make_double2(tot[2 * k], tot[2 * k + 1]);
+          dst[(long long)k * a.rows] = make_double2(tot[2 * k], tot[2 * k + 1]);
       }
     }
+  }
+}
+
+template <class P, typename T, int LPC>
+__global__ void __launch_bounds__(LPC * P::TL)
+row_inv_kernel(const RowInvArgs<T> a) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  constexpr int LSTR = P::span(1) + 1;
+  const int line = threadIdx.x / P::TL;
+  const int t = threadIdx.x - line * P::TL;
+  V* sml = sm + line * LSTR;
+  switch (a.mode) {
+    case RI_K: row_inv_items<P, T, LPC, RI_K>(a, sml, line, t); break;
+    case RI_A: row_inv_items<P, T, LPC, RI_A>(a, sml, line, t); break;
+    case RI_AH: row_inv_items<P, T, LPC, RI_AH>(a, sml, line, t); break;
+    case RI_V: row_inv_items<P, T, LPC, RI_V>(a, sml, line, t); break;
+    case RI_T: row_inv_items<P, T, LPC, RI_T>(a, sml, line, t); break;
+    default: row_inv_items<P, T, LPC, RI_R0>(a, sml, line, t); break;
   }
 }
 
@@ -589,24 +665,36 @@ template <> struct PlanFor<1024> { using type = SPlan<1024, 32, 32, 2, 2>; };
 #define FWI_FOR_EACH_L(X) \
   X(16) X(32) X(64) X(128) X(192) X(256) X(320) X(384) X(512) X(640) X(768) X(1024)
 
-template <int L> constexpr int row_lpc() {
-  constexpr int tl = PlanFor<L>::type::TL;
-  return (128 / tl) > 0 ? 128 / tl : 1;
-}
+// Tile-shape variants (autotuned per context; results are identical for
+// every variant): row passes with 128 / 64 / 256 threads per CTA, column
+// passes with the default column-tile width or half of it.  Only the
+// lengths of the benchmark grids carry the extra variants.
+constexpr int kRowVariants = 3;
+constexpr int kColVariants = 2;
+template <int L> constexpr bool tuned_len() { return L == 256 || L == 320 || L == 512 || L == 1024; }
 
-template <int L, typename T> constexpr size_t row_smem() {
+template <int L, int VAR> constexpr int row_lpc_v() {
+  constexpr int tl = PlanFor<L>::type::TL;
+  constexpr int threads = (VAR == 1) ? 64 : (VAR == 2) ? 256 : 128;
+  return (threads / tl) > 0 ? threads / tl : 1;
+}
+template <int L> constexpr int row_lpc() { return row_lpc_v<L, 0>(); }
+
+template <int L, typename T, int VAR> constexpr size_t row_smem_v() {
   using P = typename PlanFor<L>::type;
-  return (size_t)row_lpc<L>() * (P::span(1) + 1) * sizeof(cplx<T>);
+  return (size_t)row_lpc_v<L, VAR>() * (P::span(1) + 1) * sizeof(cplx<T>);
 }
 
 // Columns per tile: 128-byte row segments for FP32 up to L = 512; eight
-// columns otherwise (at most 512 threads per tile).
-template <int L, typename T> constexpr int col_tc() {
-  return (sizeof(T) == 4 && L <= 512) ? 16 : 8;
+// columns otherwise (at most 512 threads per tile); variant 1 halves it.
+template <int L, typename T, int VAR> constexpr int col_tc_v() {
+  constexpr int base = (sizeof(T) == 4 && L <= 512) ? 16 : 8;
+  return VAR == 1 ? base / 2 : base;
 }
+template <int L, typename T> constexpr int col_tc() { return col_tc_v<L, T, 0>(); }
 
-template <int L, typename T> constexpr size_t col_smem() {
-  return (size_t)L * col_tc<L, T>() * sizeof(cplx<T>);
+template <int L, typename T, int VAR> constexpr size_t col_smem_v() {
+  return (size_t)L * col_tc_v<L, T, VAR>() * sizeof(cplx<T>);
 }
 
 // Persistent grid: resident CTAs per SM (occupancy) x SMs, cached per kernel
@@ -616,7 +704,7 @@ inline std::mutex& grid_mutex() {
   static std::mutex m;
   return m;
 }
-template <int L, typename T, int KIND> GridCache& gcache() {
+template <int L, typename T, int KIND, int VAR> GridCache& gcache() {
   static GridCache g;
   return g;
 }
@@ -640,6 +728,79 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
   return cudaSuccess;
 }
 
+template <int L, typename T, int VAR>
+cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s) {
+  using P = typename PlanFor<L>::type;
+  constexpr int lpc = row_lpc_v<L, VAR>();
+  auto k = row_fwd_kernel<P, T, lpc>;
+  GridCache& gc = gcache<L, T, 0, VAR>();
+  cudaError_t e = grid_for(k, lpc * P::TL, row_smem_v<L, T, VAR>(), gc);
+  if (e != cudaSuccess) return e;
+  k<<<gc.blocks.load(), lpc * P::TL, row_smem_v<L, T, VAR>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int L, typename T, int VAR>
+cudaError_t launch_row_inv(const RowInvArgs<T>& a, cudaStream_t s) {
+  using P = typename PlanFor<L>::type;
+  constexpr int lpc = row_lpc_v<L, VAR>();
+  auto k = row_inv_kernel<P, T, lpc>;
+  GridCache& gc = gcache<L, T, 1, VAR>();
+  cudaError_t e = grid_for(k, lpc * P::TL, row_smem_v<L, T, VAR>(), gc);
+  if (e != cudaSuccess) return e;
+  k<<<gc.blocks.load(), lpc * P::TL, row_smem_v<L, T, VAR>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int L, typename T, int VAR>
+cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
+  using P = typename PlanFor<L>::type;
+  constexpr int tc = col_tc_v<L, T, VAR>();
+  auto k = col_kernel<P, T, tc>;
+  GridCache& gc = gcache<L, T, 2, VAR>();
+  cudaError_t e = grid_for(k, tc * P::TL, col_smem_v<L, T, VAR>(), gc);
+  if (e != cudaSuccess) return e;
+  k<<<gc.blocks.load(), tc * P::TL, col_smem_v<L, T, VAR>(), s>>>(a);
+  return cudaGetLastError();
+}
+
+// Variant dispatch: tuned lengths of the FP32 path carry every variant, all
+// other (length, precision) pairs only the default.
+template <int L, typename T> constexpr bool has_variants() {
+  return tuned_len<L>() && sizeof(T) == 4;
+}
+
+template <int L, typename T>
+cudaError_t row_fwd_v(int var, const RowFwdArgs<T>& a, cudaStream_t s) {
+  if constexpr (has_variants<L, T>()) {
+    if (var == 1) return launch_row_fwd<L, T, 1>(a, s);
+    if (var == 2) return launch_row_fwd<L, T, 2>(a, s);
+  }
+  return launch_row_fwd<L, T, 0>(a, s);
+}
+template <int L, typename T>
+cudaError_t row_inv_v(int var, const RowInvArgs<T>& a, cudaStream_t s) {
+  if constexpr (has_variants<L, T>()) {
+    if (var == 1) return launch_row_inv<L, T, 1>(a, s);
+    if (var == 2) return launch_row_inv<L, T, 2>(a, s);
+  }
+  return launch_row_inv<L, T, 0>(a, s);
+}
+template <int L, typename T>
+cudaError_t col_v(int var, const ColArgs<T>& a, cudaStream_t s) {
+  if constexpr (has_variants<L, T>()) {
+    if (var == 1) return launch_col<L, T, 1>(a, s);
+  }
+  return launch_col<L, T, 0>(a, s);
+}
+template <int L, typename T> int row_lpc_of(int var) {
+  if constexpr (has_variants<L, T>()) {
+    if (var == 1) return row_lpc_v<L, 1>();
+    if (var == 2) return row_lpc_v<L, 2>();
+  }
+  return row_lpc_v<L, 0>();
+}
+
 // Definition of Lsop<T> for one precision; used by the instantiation units.
 #define FWI_DEFINE_LSOP(TYPE)                                                         \
   template <> bool Lsop<TYPE>::supported(int L) {                                     \
@@ -649,92 +810,42 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
       default: return false;                                                          \
     }                                                                                 \
   }                                                                                   \
-  template <> int Lsop<TYPE>::row_lines_per_cta(int L) {                              \
+  template <> int Lsop<TYPE>::variants(int L, int kind) {                             \
+    const bool t = (sizeof(TYPE) == 4) &&                                             \
+                   (L == 256 || L == 320 || L == 512 || L == 1024);                   \
+    return t ? (kind == 2 ? kColVariants : kRowVariants) : 1;                         \
+  }                                                                                   \
+  template <> int Lsop<TYPE>::row_lines_per_cta(int L, int var) {                     \
     switch (L) {                                                                      \
       FWI_FOR_EACH_L(FWI_LPC_CASE)                                                    \
       default: return 0;                                                              \
     }                                                                                 \
   }                                                                                   \
   template <> cudaError_t Lsop<TYPE>::row_fwd(int L, const RowFwdArgs<TYPE>& a,       \
-                                              cudaStream_t s) {                       \
+                                              cudaStream_t s, int var) {              \
     switch (L) {                                                                      \
       FWI_FOR_EACH_L(FWI_ROWFWD_CASE)                                                 \
       default: return cudaErrorInvalidValue;                                          \
     }                                                                                 \
   }                                                                                   \
   template <> cudaError_t Lsop<TYPE>::row_inv(int L, const RowInvArgs<TYPE>& a,       \
-                                              cudaStream_t s) {                       \
+                                              cudaStream_t s, int var) {              \
     switch (L) {                                                                      \
       FWI_FOR_EACH_L(FWI_ROWINV_CASE)                                                 \
       default: return cudaErrorInvalidValue;                                          \
     }                                                                                 \
   }                                                                                   \
   template <> cudaError_t Lsop<TYPE>::col(int L, const ColArgs<TYPE>& a,              \
-                                          cudaStream_t s) {                           \
+                                          cudaStream_t s, int var) {                  \
     switch (L) {                                                                      \
       FWI_FOR_EACH_L(FWI_COL_CASE)                                                    \
       default: return cudaErrorInvalidValue;                                          \
     }                                                                                 \
-  }                                                                                   \
-  template <> cudaError_t Lsop<TYPE>::prepare(int L) {                                \
-    switch (L) {                                                                      \
-      FWI_FOR_EACH_L(FWI_PREP_CASE)                                                   \
-      default: return cudaErrorInvalidValue;                                          \
-    }                                                                                 \
   }
 
-#define FWI_LPC_CASE(LL) case LL: return row_lpc<LL>();
-
-#define FWI_ROWFWD_CASE(LL)                                                          \
-  case LL: {                                                                         \
-    using P = PlanFor<LL>::type;                                                     \
-    constexpr int lpc = row_lpc<LL>();                                               \
-    auto k = row_fwd_kernel<P, FWI_T, lpc>;                                          \
-    GridCache& gc = gcache<LL, FWI_T, 0>();                                          \
-    cudaError_t e = grid_for(k, lpc * P::TL, row_smem<LL, FWI_T>(), gc);             \
-    if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks.load(), lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                 \
-    return cudaGetLastError();                                                       \
-  }
-
-#define FWI_ROWINV_CASE(LL)                                                          \
-  case LL: {                                                                         \
-    using P = PlanFor<LL>::type;                                                     \
-    constexpr int lpc = row_lpc<LL>();                                               \
-    auto k = row_inv_kernel<P, FWI_T, lpc>;                                          \
-    GridCache& gc = gcache<LL, FWI_T, 1>();                                          \
-    cudaError_t e = grid_for(k, lpc * P::TL, row_smem<LL, FWI_T>(), gc);             \
-    if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks.load(), lpc * P::TL, row_smem<LL, FWI_T>(), s>>>(a);                 \
-    return cudaGetLastError();                                                       \
-  }
-
-#define FWI_COL_CASE(LL)                                                             \
-  case LL: {                                                                         \
-    using P = PlanFor<LL>::type;                                                     \
-    constexpr int tc = col_tc<LL, FWI_T>();                                              \
-    auto k = col_kernel<P, FWI_T, tc>;                                               \
-    GridCache& gc = gcache<LL, FWI_T, 2>();                                          \
-    cudaError_t e = grid_for(k, tc * P::TL, col_smem<LL, FWI_T>(), gc);              \
-    if (e != cudaSuccess) return e;                                                  \
-    k<<<gc.blocks.load(), tc * P::TL, col_smem<LL, FWI_T>(), s>>>(a);                 \
-    return cudaGetLastError();                                                       \
-  }
-
-#define FWI_PREP_CASE(LL)                                                            \
-  case LL: {                                                                         \
-    using P = PlanFor<LL>::type;                                                     \
-    constexpr int lpc = row_lpc<LL>();                                               \
-    constexpr int tc = col_tc<LL, FWI_T>();                                              \
-    cudaError_t e = grid_for(row_fwd_kernel<P, FWI_T, lpc>, lpc * P::TL,             \
-                             row_smem<LL, FWI_T>(), gcache<LL, FWI_T, 0>());         \
-    if (e == cudaSuccess)                                                            \
-      e = grid_for(row_inv_kernel<P, FWI_T, lpc>, lpc * P::TL,                       \
-                   row_smem<LL, FWI_T>(), gcache<LL, FWI_T, 1>());                   \
-    if (e == cudaSuccess)                                                            \
-      e = grid_for(col_kernel<P, FWI_T, tc>, tc * P::TL, col_smem<LL, FWI_T>(),      \
-                   gcache<LL, FWI_T, 2>());                                          \
-    return e;                                                                        \
-  }
+#define FWI_LPC_CASE(LL) case LL: return row_lpc_of<LL, FWI_T>(var);
+#define FWI_ROWFWD_CASE(LL) case LL: return row_fwd_v<LL, FWI_T>(var, a, s);
+#define FWI_ROWINV_CASE(LL) case LL: return row_inv_v<LL, FWI_T>(var, a, s);
+#define FWI_COL_CASE(LL) case LL: return col_v<LL, FWI_T>(var, a, s);
 
 }  // namespace fwi

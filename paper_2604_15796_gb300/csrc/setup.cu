@@ -245,12 +245,6 @@ fwi_status setup_t(fwi_ctx* c) {
   FWI_CUDA(c, upload_twiddles<T>(c->lx, &c->tw_x, c->stream));
   FWI_CUDA(c, upload_twiddles<T>(c->lz, &c->tw_z, c->stream));
   if (c->dim == 3) FWI_CUDA(c, upload_twiddles<T>(c->ly, &c->tw_y, c->stream));
-  FWI_CUDA(c, Lsop<T>::prepare(c->lx));
-  FWI_CUDA(c, Lsop<T>::prepare(c->lz));
-  if (c->dim == 3) FWI_CUDA(c, Lsop<T>::prepare(c->ly));
-  FWI_CUDA(c, Lsop<double>::prepare(c->lx));
-  FWI_CUDA(c, Lsop<double>::prepare(c->lz));
-  if (c->dim == 3) FWI_CUDA(c, Lsop<double>::prepare(c->ly));
   fwi_status st = compute_spectra<T>(c);
   if (st != FWI_OK) return st;
   // incident fields

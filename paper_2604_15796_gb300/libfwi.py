@@ -59,6 +59,11 @@ class fwi_stats(Structure):
                 ("kernels", fwi_kernel_stat * FWI_MAX_KERNEL_STATS)]
 
 
+class fwi_tuning(Structure):
+    _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
+                ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4)]
+
+
 class fwi_admm_params(Structure):
     _fields_ = [("lambda_", c_double), ("rho", c_double), ("gamma", c_double),
                 ("dual_step", c_double), ("n_cg", c_int), ("m_ref", c_void_p)]
@@ -104,6 +109,8 @@ EXPORTS = {
                                 POINTER(fwi_request_result)]),
     "fwi_server_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_size_t)]),
     "fwi_server_destroy": (c_int, [c_void_p]),
+    "fwi_get_tuning": (c_int, [c_void_p, POINTER(fwi_tuning)]),
+    "fwi_set_tuning": (c_int, [c_void_p, POINTER(fwi_tuning)]),
     "fwi_set_profiling": (c_int, [c_void_p, c_int]),
     "fwi_get_stats": (c_int, [c_void_p, POINTER(fwi_stats)]),
     "fwi_reset_stats": (c_int, [c_void_p]),
@@ -157,6 +164,8 @@ fwi_server_submit = _bind("fwi_server_submit")
 fwi_server_wait = _bind("fwi_server_wait")
 fwi_server_stats = _bind("fwi_server_stats")
 fwi_server_destroy = _bind("fwi_server_destroy")
+fwi_get_tuning = _bind("fwi_get_tuning")
+fwi_set_tuning = _bind("fwi_set_tuning")
 fwi_set_profiling = _bind("fwi_set_profiling")
 fwi_get_stats = _bind("fwi_get_stats")
 fwi_reset_stats = _bind("fwi_reset_stats")
@@ -325,6 +334,19 @@ class Context:
             st = fwi_apply_AH(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
         self._check(st)
         return out
+
+    def tuning(self):
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        return {"row_fwd": t.row_fwd_variant, "row_inv": t.row_inv_variant,
+                "col": t.col_variant, "col_y": t.col_y_variant, "tuned": t.tuned,
+                "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)]}
+
+    def set_tuning(self, row_fwd=0, row_inv=0, col=0, col_y=0):
+        t = fwi_tuning()
+        t.row_fwd_variant, t.row_inv_variant, t.col_variant, t.col_y_variant = (
+            row_fwd, row_inv, col, col_y)
+        self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def set_profiling(self, on):
         self._check(fwi_set_profiling(self.handle, int(bool(on))))

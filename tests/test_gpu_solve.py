@@ -126,6 +126,31 @@ def test_batched_launches_match_single_launch(lib):
     assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
 
 
+@pytest.mark.parametrize("shape", [(256, 256), (16, 512), (8, 16, 160)])
+def test_tile_variants_give_identical_results(lib, shape):
+    """Every tile-shape variant the autotuner may pick gives bitwise the same
+    fields (per-row fixed-order partial sums)."""
+    import itertools
+    import torch
+    w = small_workload(shape, n_elem=3, freqs=(2.5e6,))
+    m_gpu = to_gpu(contrast(w), torch.complex128)
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs)
+    ref = None
+    ncy = 2 if len(shape) == 3 else 1
+    for rf, ri, cz, cy in itertools.product(range(3), range(3), range(2), range(ncy)):
+        try:
+            ctx.set_tuning(rf, ri, cz, cy)
+        except lib.FwiError:
+            continue  # this length has no such variant
+        f = ctx.empty_fields()
+        ctx.forward(m_gpu, fields=f)
+        got = to_np(f)
+        if ref is None:
+            ref = got
+        assert np.array_equal(got, ref), (rf, ri, cz, cy)
+    ctx.close()
+
+
 def test_adjoint_solves(lib):
     import torch
     w = small_workload((32, 32), n_elem=4, freqs=(2e6, 3e6))
