@@ -477,6 +477,8 @@ def run_serving(args):
 
     def waiter(k, rid):
         sos, r = srv.wait(rid)
+        w = work[k][0]
+        r = dict(r, grid="x".join(map(str, reversed(w.shape))), rhs=int(w.n_rhs))
         with lock:
             results[k] = r
 
@@ -512,6 +514,8 @@ def run_serving(args):
                            "mean": float(lat.mean()), "max": float(lat.max())},
             "queue_ms_mean": float(np.mean([r["queue_ms"] for r in results])),
             "requests_per_s": len(work) / wall, "failed_requests": bad,
+            "requests": [{k: r[k] for k in ("grid", "rhs", "status", "queue_ms", "run_ms",
+                                              "latency_ms")} for r in results],
             "clocks": clk.summary()}
 
 
