@@ -22,56 +22,60 @@
 
 namespace fwi {
 
-// --------------------------------------------------------------------------
-// Block-wide reduction of NV per-thread values; thread 0 receives the
-// totals in fixed order (deterministic).  All threads must call it.
-template <int NV, typename A>
-__device__ __forceinline__ void block_sum(A (&acc)[NV], double (&out)[NV]) {
-  __shared__ double red[32][NV];
+// Per-line fixed-order sums of NV per-thread values over the TL threads of
+// each line.  The result does not depend on how many lines a CTA holds, so
+// tile shapes can be tuned without changing any bit of the partial inner
+// products.  Power-of-two lines up to a warp reduce with a shuffle
+// butterfly inside their aligned lane segment, 64-thread lines add the two
+// warp results, other lengths use a shared-memory tree.  Every thread of
+// the CTA must call it; thread t == 0 of each line receives the sums.
+template <int TL, int NTHREADS, int NV, typename A>
+__device__ __forceinline__ void line_sum(const A (&acc)[NV], int line, int t,
+                                         double (&out)[NV]) {
   double d[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) d[k] = (double)acc[k];
+  if constexpr ((TL & (TL - 1)) == 0 && TL <= 32) {
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1)
+    for (int off = TL / 2; off > 0; off >>= 1)
 #pragma unroll
-    for (int k = 0; k < NV; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], off);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0)
+      for (int k = 0; k < NV; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], off);
 #pragma unroll
-    for (int k = 0; k < NV; ++k) red[warp][k] = d[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < NV; ++k) out[k] = d[k];
+  } else if constexpr (TL == 64) {
+    __shared__ double red[NTHREADS / 32][NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += red[w][k];
-      out[k] = s;
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) d[k] += __shfl_xor_sync(0xffffffffu, d[k], off);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) red[warp][k] = d[k];
+    __syncthreads();
+    if (t == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) out[k] = red[2 * line][k] + red[2 * line + 1][k];
+    __syncthreads();
+  } else {
+    constexpr int P2 = (TL <= 32) ? 32 : 64;
+    __shared__ double red[NTHREADS][NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = d[k];
+    __syncthreads();
+#pragma unroll
+    for (int s = P2 / 2; s >= 1; s >>= 1) {
+      if (t < s && t + s < TL)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
+      __syncthreads();
     }
-  }
-}
-
-// Per-line fixed-order sums of NV per-thread values (threads t = 0..TL-1 of
-// each line, in order).  The result does not depend on how many lines a CTA
-// holds, so tile shapes can be tuned without changing any bit of the
-// partial inner products.  Thread t == 0 of each line receives the sums.
-template <int NTHREADS, int NV, typename A>
-__device__ __forceinline__ void line_sum(const A (&acc)[NV], int line, int t, int TL,
-                                         double (&out)[NV]) {
-  __shared__ double red[NTHREADS][NV];
+    if (t == 0)
 #pragma unroll
-  for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = (double)acc[k];
-  __syncthreads();
-  if (t == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-      for (int u = 0; u < TL; ++u) s += red[line * TL + u][k];
-      out[k] = s;
-    }
+      for (int k = 0; k < NV; ++k) out[k] = red[threadIdx.x][k];
+    __syncthreads();
   }
-  __syncthreads();
+  (void)line;
 }
 
 template <typename T> struct Coef { cplx<T> alpha, omega, beta; };
@@ -350,7 +354,7 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
     if (a.mode == RF_INIT) {
       const T accs[1] = {acc};
       double tot[1];
-      line_sum<LPC * P::TL, 1>(accs, line, t, P::TL, tot);
+      line_sum<P::TL, LPC * P::TL, 1>(accs, line, t, tot);
       if (t == 0 && valid)
         a.partial[((long long)rhs * NSLOT + 0) * a.rows + row] = make_double2(tot[0], 0.0);
     }
@@ -364,8 +368,15 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
 //   RI_V : 0 <rhat, v>
 //   RI_T : 0 <t, s>, 1 <t, t>, 2 <rhat, t>, 3 <rhat, s>, 4 <s, s>
 //   RI_R0: 0 <r, r>, 1 <b, b>
+// Phase-A slots m whose sample n1 lies in the cropped half n1 < H1: for a
+// split phase A (n1 = 2m + s) these are m < H1/2, otherwise m < H1.
+template <class P> constexpr int out_m() {
+  if constexpr (PlanTraits<P>::split) return (P::S1 == 2) ? P::H1 / 2 : P::H1;
+  else return P::H1;
+}
 template <class P> struct RowSlots {
-  static constexpr int N = PlanTraits<P>::CA * P::H1;  // output samples per thread
+  static constexpr int M = out_m<P>();
+  static constexpr int N = PlanTraits<P>::CA * M;  // output samples per thread
 };
 
 template <class P, typename T, int MODE>
@@ -385,10 +396,10 @@ __device__ __forceinline__ void ri_prefetch(const RowInvArgs<T>& a, int t, int r
 #pragma unroll
   for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-    for (int m = 0; m < P::H1; ++m) {
-      const int j = i * P::H1 + m;
+    for (int m = 0; m < RowSlots<P>::M; ++m) {
+      const int j = i * RowSlots<P>::M + m;
       int n2, n1;
-      if (!slotA<P, GP>(t, i, m, n2, n1)) continue;
+      if (!slotA<P, GP>(t, i, m, n2, n1) || n1 >= P::H1) continue;
       const int x = P::R2 * n1 + n2;
       const long long idx = vb + x;
       if (MODE == RI_A) {
@@ -426,10 +437,10 @@ __device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs,
 #pragma unroll
   for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-    for (int m = 0; m < P::H1; ++m) {
-      const int j = i * P::H1 + m;
+    for (int m = 0; m < RowSlots<P>::M; ++m) {
+      const int j = i * RowSlots<P>::M + m;
       int n2, n1;
-      if (!slotA<P, GP>(t, i, m, n2, n1)) continue;
+      if (!slotA<P, GP>(t, i, m, n2, n1) || n1 >= P::H1) continue;
       const long long idx = vb + P::R2 * n1 + n2;
       // phase-D output slot of sample n1 (< H1): same position as in phase A
       const V y = v[i * PlanTraits<P>::MA + m];
@@ -514,7 +525,7 @@ __device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* s
     }
     if (dots) {
       double tot[2 * NSLOT];
-      line_sum<LPC * P::TL, 2 * NSLOT>(acc, line, t, P::TL, tot);
+      line_sum<P::TL, LPC * P::TL, 2 * NSLOT>(acc, line, t, tot);
       if (t == 0 && valid) {
         double2* dst = a.partial + (long long)rhs * NSLOT * a.rows + row;
 #pragma unroll
