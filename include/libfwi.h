@@ -317,6 +317,11 @@ typedef struct fwi_tuning {
   int col_y_variant;    /* 3-D y passes */
   int tuned;            /* 1 if chosen by timing */
   float ms[4][4];       /* measured ms per pass kind and variant (0: not timed) */
+  int jac_tensor_cores; /* 1 (default): FP32 pixel contractions of the data
+                           projection, J a and J^H b on the tensor cores
+                           (tcgen05, 3xTF32 products, FP32 accumulation);
+                           0: CUDA-core FP32 kernels.  FP64 contexts and odd
+                           pixel counts always use the CUDA-core kernels. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

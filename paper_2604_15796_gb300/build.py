@@ -15,7 +15,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "lib", "libfwi.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 
-UNITS = ["lsop_f32.cu", "lsop_f64.cu", "setup.cu", "krylov.cu", "jac.cu", "admm.cu",
+UNITS = ["lsop_f32.cu", "lsop_f64.cu", "setup.cu", "krylov.cu", "jac.cu", "jac_tc.cu", "admm.cu",
          "api.cu", "serve.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

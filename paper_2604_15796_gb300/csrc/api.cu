@@ -39,7 +39,7 @@ struct Layout {
   int dim, nx, ny, nz, lx, ly, lz, rows, n_elem, n_freq, n_rhs, batch, ntiles, split;
   long long N;
   size_t csz;
-  size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec;
+  size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec, b_tc;
   size_t total;
 };
 
@@ -90,8 +90,9 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.b_zpart = (size_t)L.n_freq * nbe * L.N * L.csz;
   L.b_vec = (size_t)L.N * L.csz * 2 + (size_t)8 * L.N * 16 + (size_t)3 * L.dim * L.N * 16 +
             sizeof(double) * (L.n_freq + 256 + 512 + 16);
+  L.b_tc = (d->precision == FWI_FP64) ? 0 : tc_bops_bytes(L.n_elem, L.n_freq);
   L.total = L.b_ghat + 4 * L.b_field + 5 * L.b_kv + L.b_plane1 + L.b_plane2 + L.b_small +
-            L.b_jsplit + L.b_zpart + L.b_vec;
+            L.b_jsplit + L.b_zpart + L.b_vec + L.b_tc + 256;
   return true;
 }
 
@@ -118,7 +119,7 @@ static void release(fwi_ctx* c) {
   void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
-                  c->jsplit, c->zpart, c->aF, c->red};
+                  c->jsplit, c->zpart, c->aF, c->red, c->tc_bops, c->tc_err};
   // stream-ordered frees: no device-wide synchronisation, so a context can be
   // retired while other contexts' work runs
   for (void* p : bufs) if (p) cudaFreeAsync(p, c->stream);
@@ -128,6 +129,7 @@ static void release(fwi_ctx* c) {
   if (c->h_n_active) cudaFreeHost(c->h_n_active);
   if (c->h_scal) cudaFreeHost(c->h_scal);
   if (c->h_red) cudaFreeHost(c->h_red);
+  if (c->h_tc_err) cudaFreeHost(c->h_tc_err);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -214,9 +216,14 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   alloc((void**)&c->vD[0], (size_t)L.dim * L.N * 16);
   c->red_n = L.n_freq + 256 + 512 + 16;
   alloc((void**)&c->red, sizeof(double) * c->red_n);
+  alloc(&c->tc_bops, L.b_tc);
+  alloc((void**)&c->tc_err, 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_n_active, 64);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_scal, sizeof(Scal) * L.batch);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_red, sizeof(double) * c->red_n);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_tc_err, sizeof(int));
+  if (e == cudaSuccess) *c->h_tc_err = 0;
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
   if (e != cudaSuccess) {
@@ -278,8 +285,10 @@ fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields, int warm_start
   if (fields) st2 = copy_field(ctx, fields, ctx->fields, nf, 0);
   if (st2 == FWI_OK) st2 = project_data(ctx, m, data);
   if (st2 == FWI_OK) {
+    tc_err_fetch(ctx);
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_forward");
+    st2 = tc_err_check(ctx);
   }
   return st2 != FWI_OK ? st2 : st;
 }
@@ -321,9 +330,11 @@ fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs, void* gr
   if (st != FWI_OK) worst = st;
   st = assemble_gradient(ctx, grad);
   if (st != FWI_OK) return st;
+  tc_err_fetch(ctx);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_gradient");
-  return worst;
+  st = tc_err_check(ctx);
+  return st != FWI_OK ? st : worst;
 }
 
 fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void* grad,
@@ -335,9 +346,10 @@ fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void*
   ctx->err.clear();
   fwi_status st = admm_step(ctx, m, g, u, grad, p, sos_out);
   if (st != FWI_OK) return st;
+  tc_err_fetch(ctx);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_admm_tv_step");
-  return FWI_OK;
+  return tc_err_check(ctx);
 }
 
 fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u) {
@@ -394,6 +406,7 @@ fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
   out->col_variant = ctx->var_cz;
   out->col_y_variant = ctx->var_cy;
   out->tuned = ctx->tuned;
+  out->jac_tensor_cores = ctx->use_tc ? 1 : 0;
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
   return FWI_OK;
@@ -409,6 +422,9 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
                       in->col_y_variant};
   for (int k = 0; k < 4; ++k)
     if (req[k] < 0 || req[k] >= lims[k]) return fail(ctx, FWI_ERR_INVALID_ARG, "variant out of range");
+  if (in->jac_tensor_cores != 0 && in->jac_tensor_cores != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "jac_tensor_cores must be 0 or 1");
+  ctx->use_tc = in->jac_tensor_cores == 1;
   ctx->var_rf = req[0];
   ctx->var_ri = req[1];
   ctx->var_cz = req[2];

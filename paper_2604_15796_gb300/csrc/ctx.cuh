@@ -57,6 +57,10 @@ struct fwi_ctx {
   void* aF = nullptr;               // [N] field-precision vector
   double2* vN[8] = {};              // [N] c128 ADMM / CG vectors
   double2* vD[3] = {};              // [dim][N] c128 ADMM vectors
+  void* tc_bops = nullptr;          // tensor-core J^H: B operand stages (FP32 only)
+  int* tc_err = nullptr;            // error word of the tensor-core kernels
+  int* h_tc_err = nullptr;          // pinned host mirror
+  bool use_tc = true;               // tensor-core pixel contractions (FP32 fields)
   double* red = nullptr;            // reduction scratch (doubles)
   double* h_red = nullptr;          // pinned host mirror
   int red_n = 0;
@@ -109,6 +113,14 @@ fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u);
 fwi_status admm_step(fwi_ctx* c, void* m, void* g, void* u, const void* grad,
                      const fwi_admm_params* p, double* sos);
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m);
+// tensor-core pixel contractions (jac_tc.cu)
+bool tc_usable(const fwi_ctx* c);
+size_t tc_bops_bytes(int n_elem, int n_freq);
+int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const float2* Q,
+                         float2* part);
+int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart);
+void tc_err_fetch(fwi_ctx* c);
+fwi_status tc_err_check(fwi_ctx* c);
 }  // namespace fwi
 
 #define FWI_CUDA(c, call)                                          \

@@ -10,10 +10,14 @@
 //             materialised (adjoint sources conj(s_e) = sum_j R_j conj(r_ej))
 //             or fused with z[n] += sum_e conj(X_l[e][n]) W_l[e][n]  (J^H b)
 //
-// Both are register-tiled CUDA-core kernels (64 x 64 complex output tiles,
-// 4 x 4 per thread, operands staged through shared memory).  Partial sums
-// across pixel chunks / transmit blocks are combined in FP64 in fixed order.
+// With FP32 fields the contraction and the fused J^H run on the tensor
+// cores (jac_tc.cu); the kernels here are the FP64 path, the materialised
+// mix, and the fallback for odd pixel counts: register-tiled CUDA-core
+// kernels (64 x 64 complex output tiles, 4 x 4 per thread, operands staged
+// through shared memory).  Partial sums across pixel chunks / transmit
+// blocks are combined in FP64 in fixed order.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.cuh"
@@ -355,6 +359,19 @@ template <typename T> struct Jac {
   // (then Y_l is complex-symmetric and only tiles eb <= jb are computed).
   static fwi_status contract(fwi_ctx* c, const cplx<T>* X, const cplx<T>* a,
                              const cplx<T>* Q, double2* Y) {
+    const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc_usable(c)) {
+        const int split = tc_contract_partials(c, X, a, Q, (float2*)c->jsplit);
+        if (split < 0) return FWI_ERR_CUDA;
+        Prof p(c, KC_MISC);
+        contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+            Y, (const cplx<T>*)c->jsplit, split, per, c->n_elem * c->n_elem, c->red, c->n_elem,
+            0);
+        FWI_CUDA(c, cudaGetLastError());
+        return FWI_OK;
+      }
+    }
     const int nbe = (c->n_elem + TB - 1) / TB;
     const int split = split_for(c);
     const int sym = (X == Q) ? 1 : 0;
@@ -369,7 +386,6 @@ template <typename T> struct Jac {
                                                       c->N, c->n_freq, chunk, sym);
     }
     FWI_CUDA(c, cudaGetLastError());
-    const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
     {
       Prof p(c, KC_MISC);
       contract_reduce_kernel<T><<<blocks_for(per, 256, c->n_sm * 8), 256, 0, c->stream>>>(
@@ -498,6 +514,17 @@ fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {
 template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2* y, double2* z) {
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc_usable(c)) {
+      const int np = tc_jh_partials(c, y, (const float2*)c->fields, (float2*)c->zpart);
+      if (np < 0) return FWI_ERR_CUDA;
+      Prof p(c, KC_MISC);
+      sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+          z, (const cplx<T>*)c->zpart, np, c->N, 0);
+      FWI_CUDA(c, cudaGetLastError());
+      return FWI_OK;
+    }
+  }
   const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
   {
     Prof p(c, KC_MISC);

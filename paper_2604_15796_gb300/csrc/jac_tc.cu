@@ -1,0 +1,625 @@
+// Tensor-core (tcgen05, TF32) versions of the two FP32 pixel contractions
+// of the data equation and the implicit Jacobian (Eq. 4, 15-17; Sec. IV-B,
+// IV-C):
+//
+//  contract : Y_l[e][j] = sum_n X_l[e][n] (a[n] Q_l[j][n])       (data, J a)
+//  J^H      : z_l[n]    = s_l sum_e conj(X_l[e][n]) W_l[e][n],
+//             W_l[e][n] = sum_j B_l[e][j] conj(X_l[j][n])           (J^H b)
+//
+// Both are complex GEMMs with one dimension of 128 array elements per tile
+// and the pixels as the long dimension (K for the contraction, M for J^H).
+// A complex product is four real products; in the 128 x 256 accumulator
+// [Re | Im] they are two MMAs per k-step,
+//     D += Ar [Br; Bi]^T   and   D += Ai [-Bi; Br]^T,
+// with the B rows kept once as the stack [-Bi | Br | Bi].  Each real
+// operand is split into TF32 hi + lo parts and a b is taken as
+// ah bh + ah bl + al bh (3xTF32), which keeps the products at FP32
+// accuracy; accumulation is FP32 in TMEM and partial sums over CTAs are
+// combined in FP64 by the callers' reduction kernels.
+//
+// Pipelines: four producer warps stream raw FP32 tiles with cp.async (three
+// stages ahead), split them into the TF32 operand planes of a shared-memory
+// stage and signal an mbarrier; one warp issues the MMAs and releases the
+// stage with tcgen05.commit.  Every wait is bounded (tc.cuh).
+#include <mutex>
+#include <string>
+
+#include "ctx.cuh"
+#include "prof.cuh"
+#include "tc.cuh"
+
+namespace fwi {
+
+namespace {
+
+using tc::smem_addr;
+
+constexpr int ROWS = 128;             // MMA M, rows of an operand tile
+constexpr int KS = 8;                 // complex values per k-step (TF32 K = 8)
+constexpr int PLANE = ROWS * 32;      // one 128-row operand block of a k-step
+constexpr int BROWS = 3 * ROWS;       // B stack [-Bi | Br | Bi]
+constexpr int BPLANE = BROWS * 32;
+constexpr uint32_t LBO_A = 16 * ROWS, LBO_B = 16 * BROWS, SBO = 128;
+constexpr uint32_t IDESC = tc::idesc_tf32(128, 256, false);
+constexpr int NTHREADS = 160;         // 4 producer warps + 1 MMA warp
+
+// Operand planes inside a conversion stage: A = {Ar hi, Ar lo, Ai hi, Ai lo}
+// (one 128-row block each), then B hi and B lo (384 rows each).
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_base, uint32_t b_base,
+                                           uint32_t first) {
+  using namespace tc;
+  const uint64_t ar_h = sdesc(a_base + 0 * PLANE, LBO_A, SBO);
+  const uint64_t ar_l = sdesc(a_base + 1 * PLANE, LBO_A, SBO);
+  const uint64_t ai_h = sdesc(a_base + 2 * PLANE, LBO_A, SBO);
+  const uint64_t ai_l = sdesc(a_base + 3 * PLANE, LBO_A, SBO);
+  // [Br; Bi] starts at row 128 of the stack, [-Bi; Br] at row 0
+  const uint64_t b1_h = sdesc(b_base + 16 * ROWS, LBO_B, SBO);
+  const uint64_t b1_l = sdesc(b_base + BPLANE + 16 * ROWS, LBO_B, SBO);
+  const uint64_t b2_h = sdesc(b_base, LBO_B, SBO);
+  const uint64_t b2_l = sdesc(b_base + BPLANE, LBO_B, SBO);
+  mma_tf32(tmem, ar_h, b1_h, IDESC, first ? 0u : 1u);
+  mma_tf32(tmem, ar_h, b1_l, IDESC, 1u);
+  mma_tf32(tmem, ar_l, b1_h, IDESC, 1u);
+  mma_tf32(tmem, ai_h, b2_h, IDESC, 1u);
+  mma_tf32(tmem, ai_h, b2_l, IDESC, 1u);
+  mma_tf32(tmem, ai_l, b2_h, IDESC, 1u);
+}
+
+// Store 4 consecutive-k values of operand row `row` (hi and lo planes).
+__device__ __forceinline__ void put_a(uint32_t plane_hi, uint32_t plane_lo, int half, int row,
+                                      const float (&v)[4]) {
+  float h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tc::split_tf32(v[i], h[i], l[i]);
+  const uint32_t off = (uint32_t)(half * 16 * ROWS + 16 * row);
+  tc::sts128(plane_hi + off, h[0], h[1], h[2], h[3]);
+  tc::sts128(plane_lo + off, l[0], l[1], l[2], l[3]);
+}
+
+// B row `row`: re and im parts into the [-Bi | Br | Bi] stack.
+__device__ __forceinline__ void put_b(uint32_t bhi, uint32_t blo, int half, int row,
+                                      const float (&re)[4], const float (&im)[4]) {
+  float rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    tc::split_tf32(re[i], rh[i], rl[i]);
+    tc::split_tf32(im[i], ih[i], il[i]);
+  }
+  const uint32_t o = (uint32_t)(half * 16 * BROWS + 16 * row);
+  tc::sts128(bhi + o, -ih[0], -ih[1], -ih[2], -ih[3]);
+  tc::sts128(bhi + o + 16 * ROWS, rh[0], rh[1], rh[2], rh[3]);
+  tc::sts128(bhi + o + 32 * ROWS, ih[0], ih[1], ih[2], ih[3]);
+  tc::sts128(blo + o, -il[0], -il[1], -il[2], -il[3]);
+  tc::sts128(blo + o + 16 * ROWS, rl[0], rl[1], rl[2], rl[3]);
+  tc::sts128(blo + o + 32 * ROWS, il[0], il[1], il[2], il[3]);
+}
+
+__device__ __forceinline__ float4 lds128(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ float2 lds64(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Contraction: one CTA per (pixel chunk s, tile pair (eb, jb), frequency l);
+// accumulator D[e][j] (128 x [128 Re | 128 Im]) over its pixel chunk,
+// written as FP32 partials part[s][l][e][j].
+constexpr int C_CONV = 3, C_RAW = 3;
+constexpr int C_RAWROW = 80;  // 8 complex (64 bytes) + 16 bytes of padding
+constexpr int C_RAW_X = 0, C_RAW_Q = ROWS * C_RAWROW, C_RAW_A = 2 * ROWS * C_RAWROW;
+constexpr int C_RAW_BYTES = 2 * ROWS * C_RAWROW + 64;
+constexpr int C_CONV_BYTES = 4 * PLANE + 2 * BPLANE;
+constexpr int C_SMEM = C_CONV * C_CONV_BYTES + C_RAW * C_RAW_BYTES;
+
+struct ContractArgs {
+  const float2* X;
+  const float2* Q;
+  const float2* a;  // may be NULL
+  float2* part;
+  int* err;
+  long long N, chunk;
+  int NE, n_freq;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = blockIdx.x, l = blockIdx.z;
+  const int nbe = (p.NE + ROWS - 1) / ROWS;
+  const int eb = blockIdx.y % nbe, jb = blockIdx.y / nbe;
+  const long long n_begin = (long long)s * p.chunk;
+  const long long n_end = (n_begin + p.chunk < p.N) ? n_begin + p.chunk : p.N;
+  const int nch = (n_begin < p.N) ? (int)((n_end - n_begin + KS - 1) / KS) : 0;
+  const float2* Xl = p.X + (long long)l * p.NE * p.N;
+  const float2* Ql = p.Q + (long long)l * p.NE * p.N;
+  const bool same_rows = (p.X == p.Q) && (eb == jb);
+  const bool has_a = p.a != nullptr;
+
+  if (tid == 0) {
+    for (int i = 0; i < C_CONV; ++i) {
+      mbar_init(smem_addr(&bar_full[i]), 128);
+      mbar_init(smem_addr(&bar_empty[i]), 1);
+    }
+    mbar_init(smem_addr(&bar_done), 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 256);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t sbase = smem_addr(smem);
+  const uint32_t raw0 = sbase + C_CONV * C_CONV_BYTES;
+
+  if (warp < 4) {
+    const int r = tid;
+    const int e = eb * ROWS + r, j = jb * ROWS + r;
+    const bool ev = e < p.NE, jv = j < p.NE;
+    const float2* xrow = Xl + (long long)(ev ? e : 0) * p.N;
+    const float2* qrow = Ql + (long long)(jv ? j : 0) * p.N;
+    auto issue = [&](int g) {
+      if (g < nch) {
+        const long long n0 = n_begin + (long long)g * KS;
+        const uint32_t rb = raw0 + (uint32_t)((g % C_RAW) * C_RAW_BYTES);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const long long n = n0 + 2 * q;
+          const bool ok = n < n_end;
+          cp_async16(rb + C_RAW_X + r * C_RAWROW + 16 * q, (ok && ev) ? xrow + n : Xl,
+                     (ok && ev) ? 16u : 0u);
+          if (!same_rows)
+            cp_async16(rb + C_RAW_Q + r * C_RAWROW + 16 * q, (ok && jv) ? qrow + n : Ql,
+                       (ok && jv) ? 16u : 0u);
+        }
+        if (has_a && r < 4) {
+          const long long n = n0 + 2 * r;
+          const bool ok = n < n_end;
+          cp_async16(rb + C_RAW_A + 16 * r, ok ? p.a + n : p.a, ok ? 16u : 0u);
+        }
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int g = 0; g < C_RAW - 1; ++g) issue(g);
+    for (int g = 0; g < nch; ++g) {
+      cp_async_wait<C_RAW - 2>();
+      bar_sync(1, 128);  // chunk g visible to all; everyone done with chunk g-1
+      issue(g + C_RAW - 1);
+      const int cs = g % C_CONV;
+      mbar_wait(smem_addr(&bar_empty[cs]), ((g / C_CONV) & 1) ^ 1, &abort_flag, p.err,
+                kErrWaitEmpty);
+      const uint32_t rb = raw0 + (uint32_t)((g % C_RAW) * C_RAW_BYTES);
+      const uint32_t cb = sbase + (uint32_t)(cs * C_CONV_BYTES);
+      const uint32_t bhi = cb + 4 * PLANE, blo = bhi + BPLANE;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        float2 x[4], q[4];
+        {
+          const float4 u0 = lds128(rb + C_RAW_X + r * C_RAWROW + 32 * half);
+          const float4 u1 = lds128(rb + C_RAW_X + r * C_RAWROW + 32 * half + 16);
+          x[0] = make_float2(u0.x, u0.y); x[1] = make_float2(u0.z, u0.w);
+          x[2] = make_float2(u1.x, u1.y); x[3] = make_float2(u1.z, u1.w);
+        }
+        if (same_rows) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) q[i] = x[i];
+        } else {
+          const float4 u0 = lds128(rb + C_RAW_Q + r * C_RAWROW + 32 * half);
+          const float4 u1 = lds128(rb + C_RAW_Q + r * C_RAWROW + 32 * half + 16);
+          q[0] = make_float2(u0.x, u0.y); q[1] = make_float2(u0.z, u0.w);
+          q[2] = make_float2(u1.x, u1.y); q[3] = make_float2(u1.z, u1.w);
+        }
+        if (has_a) {
+          const float4 u0 = lds128(rb + C_RAW_A + 32 * half);
+          const float4 u1 = lds128(rb + C_RAW_A + 32 * half + 16);
+          const float2 av[4] = {make_float2(u0.x, u0.y), make_float2(u0.z, u0.w),
+                                make_float2(u1.x, u1.y), make_float2(u1.z, u1.w)};
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            q[i] = make_float2(q[i].x * av[i].x - q[i].y * av[i].y,
+                               q[i].x * av[i].y + q[i].y * av[i].x);
+        }
+        const float xr[4] = {x[0].x, x[1].x, x[2].x, x[3].x};
+        const float xi[4] = {x[0].y, x[1].y, x[2].y, x[3].y};
+        const float qr[4] = {q[0].x, q[1].x, q[2].x, q[3].x};
+        const float qi[4] = {q[0].y, q[1].y, q[2].y, q[3].y};
+        put_a(cb + 0 * PLANE, cb + 1 * PLANE, half, r, xr);
+        put_a(cb + 2 * PLANE, cb + 3 * PLANE, half, r, xi);
+        put_b(bhi, blo, half, r, qr, qi);
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_addr(&bar_full[cs]));
+    }
+    cp_async_wait<0>();
+    // epilogue: TMEM lane r = row e; columns j (Re) and 128 + j (Im)
+    const bool ok = mbar_wait(smem_addr(&bar_done), 0, &abort_flag, p.err, kErrWaitDone);
+    fence_after_sync();
+    float2* out = p.part + (((long long)s * p.n_freq + l) * p.NE + (ev ? e : 0)) * p.NE;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+    for (int jc = 0; jc < ROWS / 32; ++jc) {
+      uint32_t re[32], im[32];
+      tmem_ld32(lane_addr + 32 * jc, re);
+      tmem_ld32(lane_addr + ROWS + 32 * jc, im);
+      tmem_wait_ld();
+      if (ev) {
+        const bool zero = (nch == 0) || !ok;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int jj = jb * ROWS + 32 * jc + i;
+          if (jj < p.NE)
+            out[jj] = zero ? make_float2(0.f, 0.f)
+                           : make_float2(__uint_as_float(re[i]), __uint_as_float(im[i]));
+        }
+      }
+    }
+  } else {
+    for (int g = 0; g < nch; ++g) {
+      const int cs = g % C_CONV;
+      const bool ok = mbar_wait(smem_addr(&bar_full[cs]), (g / C_CONV) & 1, &abort_flag,
+                                p.err, kErrWaitFull);
+      fence_after_sync();
+      if (lane == 0 && ok) {
+        const uint32_t cb = sbase + (uint32_t)(cs * C_CONV_BYTES);
+        issue_kstep(tmem, cb, cb + 4 * PLANE, g == 0);
+        commit(smem_addr(&bar_empty[cs]));
+      }
+      __syncwarp();
+    }
+    if (lane == 0) commit(smem_addr(&bar_done));
+    __syncwarp();
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 256);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// J^H: persistent CTAs over units (frequency l, element tile eb, block of
+// M_TILES x 128 pixels).  Per unit and pixel tile the accumulator holds
+// W[n][e] (128 pixels x [128 Re | 128 Im]); the epilogue forms
+// s_l sum_e conj(X[e][n]) W[e][n] into zpart[l][eb][n].
+constexpr int M_TILES = 2;
+constexpr int M_CONV = 3, M_RAW = 3;
+constexpr int M_RAW_TILE = KS * ROWS * 8;               // [8 j][128 n] complex
+constexpr int M_RAW_BYTES = M_TILES * M_RAW_TILE;
+constexpr int M_A_BYTES = M_TILES * 4 * PLANE;
+constexpr int M_B_BYTES = 2 * BPLANE;                    // one k-step of B hi + lo
+constexpr int M_CONV_BYTES = M_A_BYTES + M_B_BYTES;
+constexpr int M_SMEM = M_CONV * M_CONV_BYTES + M_RAW * M_RAW_BYTES;
+
+struct JhArgs {
+  const float2* X;     // [n_freq][NE][N]
+  const float* bops;   // [n_freq][nbe][nks] k-step blocks of the B stack (hi, lo)
+  const double* scale; // [n_freq]
+  float2* zpart;       // [n_freq][nbe][N]
+  int* err;
+  long long N;
+  int NE, n_freq, nbe, nks, npb, units;
+};
+
+__global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
+  using namespace tc;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar_full[M_CONV], bar_empty[M_CONV], bar_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int my_units = (blockIdx.x < p.units)
+                           ? (p.units - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
+                           : 0;
+  const int nchunks = my_units * p.nks;
+
+  if (tid == 0) {
+    for (int i = 0; i < M_CONV; ++i) {
+      mbar_init(smem_addr(&bar_full[i]), 129);  // 128 producers + expect_tx
+      mbar_init(smem_addr(&bar_empty[i]), 1);
+    }
+    mbar_init(smem_addr(&bar_done), 1);
+    abort_flag = 0;
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 256 * M_TILES);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  const uint32_t sbase = smem_addr(smem);
+  const uint32_t raw0 = sbase + M_CONV * M_CONV_BYTES;
+
+  // unit index -> (l, eb, pixel block)
+  auto unit_of = [&](int k, int& l, int& eb, int& pb) {
+    const int u = (int)blockIdx.x + k * (int)gridDim.x;
+    pb = u % p.npb;
+    eb = (u / p.npb) % p.nbe;
+    l = u / (p.npb * p.nbe);
+  };
+
+  if (warp < 4) {
+    const int r = tid;
+    auto issue = [&](int g) {
+      if (g < nchunks) {
+        int l, eb, pb;
+        unit_of(g / p.nks, l, eb, pb);
+        const int ks = g % p.nks;
+        const uint32_t rb = raw0 + (uint32_t)((g % M_RAW) * M_RAW_BYTES);
+        const float2* Xl = p.X + (long long)l * p.NE * p.N;
+#pragma unroll
+        for (int k = 0; k < (M_TILES * KS * ROWS / 2) / 128; ++k) {
+          const int i = r + 128 * k;
+          const int t = i / (KS * ROWS / 2), jj = (i / (ROWS / 2)) % KS, pr = i % (ROWS / 2);
+          const int jrow = ks * KS + jj;
+          const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + 2 * pr;
+          const bool ok = (jrow < p.NE) && (n < p.N);
+          cp_async16(rb + (uint32_t)(t * M_RAW_TILE + jj * ROWS * 8 + 16 * pr),
+                     ok ? Xl + (long long)jrow * p.N + n : p.X, ok ? 16u : 0u);
+        }
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int g = 0; g < M_RAW - 1; ++g) issue(g);
+    for (int g = 0; g < nchunks; ++g) {
+      cp_async_wait<M_RAW - 2>();
+      bar_sync(1, 128);
+      issue(g + M_RAW - 1);
+      const int kunit = g / p.nks, ks = g % p.nks;
+      int l, eb, pb;
+      unit_of(kunit, l, eb, pb);
+      const int cs = g % M_CONV;
+      mbar_wait(smem_addr(&bar_empty[cs]), ((g / M_CONV) & 1) ^ 1, &abort_flag, p.err,
+                kErrWaitEmpty);
+      const uint32_t cb = sbase + (uint32_t)(cs * M_CONV_BYTES);
+      if (r == 0) {
+        const uint32_t fb = smem_addr(&bar_full[cs]);
+        mbar_arrive_expect_tx(fb, M_B_BYTES);
+        const float* src =
+            p.bops + ((((long long)l * p.nbe + eb) * p.nks + ks) * (long long)(M_B_BYTES / 4));
+        bulk_g2s(cb + M_A_BYTES, src, M_B_BYTES, fb);
+      }
+      const uint32_t rb = raw0 + (uint32_t)((g % M_RAW) * M_RAW_BYTES);
+#pragma unroll
+      for (int t = 0; t < M_TILES; ++t) {
+        const uint32_t ab = cb + (uint32_t)(t * 4 * PLANE);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float re[4], im[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float2 v = lds64(rb + (uint32_t)(t * M_RAW_TILE + (4 * half + i) * ROWS * 8 + 8 * r));
+            re[i] = v.x;
+            im[i] = -v.y;  // A = conj(X)^T
+          }
+          put_a(ab + 0 * PLANE, ab + 1 * PLANE, half, r, re);
+          put_a(ab + 2 * PLANE, ab + 3 * PLANE, half, r, im);
+        }
+      }
+      fence_proxy_async();
+      mbar_arrive(smem_addr(&bar_full[cs]));
+      if (ks == p.nks - 1) {
+        // epilogue of this unit: TMEM lane r = pixel, columns e (Re), 128 + e (Im)
+        const bool ok = mbar_wait(smem_addr(&bar_done), kunit & 1, &abort_flag, p.err,
+                                  kErrWaitDone);
+        fence_after_sync();
+        const float2* Xl = p.X + (long long)l * p.NE * p.N;
+        const float sc = (float)p.scale[l];
+        const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll 1
+        for (int t = 0; t < M_TILES; ++t) {
+          const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + r;
+          const bool nv = n < p.N;
+          float zx = 0.f, zy = 0.f;
+#pragma unroll 1
+          for (int ec = 0; ec < ROWS / 32; ++ec) {
+            uint32_t wr[32], wi[32];
+            tmem_ld32(lane_addr + (uint32_t)(t * 256 + 32 * ec), wr);
+            tmem_ld32(lane_addr + (uint32_t)(t * 256 + ROWS + 32 * ec), wi);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int e = eb * ROWS + 32 * ec + i;
+              if (nv && e < p.NE) {
+                const float2 x = __ldg(Xl + (long long)e * p.N + n);
+                const float a = __uint_as_float(wr[i]), b = __uint_as_float(wi[i]);
+                zx += x.x * a + x.y * b;
+                zy += x.x * b - x.y * a;
+              }
+            }
+          }
+          if (nv)
+            p.zpart[((long long)l * p.nbe + eb) * p.N + n] =
+                ok ? make_float2(zx * sc, zy * sc) : make_float2(0.f, 0.f);
+        }
+        fence_before_sync();  // TMEM reads precede the next unit's MMAs
+      }
+    }
+    cp_async_wait<0>();
+  } else {
+    for (int g = 0; g < nchunks; ++g) {
+      const int cs = g % M_CONV, ks = g % p.nks;
+      const bool ok = mbar_wait(smem_addr(&bar_full[cs]), (g / M_CONV) & 1, &abort_flag,
+                                p.err, kErrWaitFull);
+      fence_after_sync();
+      if (lane == 0 && ok) {
+        const uint32_t cb = sbase + (uint32_t)(cs * M_CONV_BYTES);
+#pragma unroll
+        for (int t = 0; t < M_TILES; ++t)
+          issue_kstep(tmem + (uint32_t)(t * 256), cb + (uint32_t)(t * 4 * PLANE),
+                      cb + M_A_BYTES, ks == 0);
+        commit(smem_addr(&bar_empty[cs]));
+        if (ks == p.nks - 1) commit(smem_addr(&bar_done));
+      }
+      __syncwarp();
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after_sync();
+    tmem_dealloc(tmem, 256 * M_TILES);
+  }
+}
+
+// B operand of J^H: per (l, eb, k-step) the stack [-Bi | Br | Bi] of
+// B = y_l[e][j] (e in tile eb, j in the k-step) as TF32 hi and lo planes,
+// laid out exactly as one shared-memory stage.
+__global__ void tc_jh_bops_kernel(const double2* __restrict__ y, float* __restrict__ bops,
+                                  int NE, int nbe, int nks, long long nseg) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nseg;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long blk = idx / (2 * 2 * BROWS);
+    const int rem = (int)(idx % (2 * 2 * BROWS));
+    const int hl = rem / (2 * BROWS), half = (rem / BROWS) % 2, row = rem % BROWS;
+    const int ks = (int)(blk % nks), eb = (int)((blk / nks) % nbe);
+    const long long l = blk / ((long long)nks * nbe);
+    const int e = eb * ROWS + row % ROWS, part = row / ROWS;
+    float v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int j = ks * KS + 4 * half + k;
+      double x = 0.0;
+      if (e < NE && j < NE) {
+        const double2 b = y[(l * NE + e) * NE + j];
+        x = part == 0 ? -b.y : (part == 1 ? b.x : b.y);
+      }
+      const float hi = tc::to_tf32((float)x);
+      v[k] = hl == 0 ? hi : tc::to_tf32((float)(x - (double)hi));
+    }
+    float4* dst = (float4*)(bops + blk * (M_B_BYTES / 4) + hl * (BPLANE / 4) +
+                            half * (16 * BROWS / 4) + 4 * row);
+    *dst = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+int blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+std::once_flag g_attr_once;
+cudaError_t g_attr_err = cudaSuccess;
+
+cudaError_t set_attrs() {
+  std::call_once(g_attr_once, [] {
+    g_attr_err = cudaFuncSetAttribute(tc_contract_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
+  });
+  return g_attr_err;
+}
+
+}  // namespace
+
+bool tc_usable(const fwi_ctx* c) {
+  return !c->fp64 && c->use_tc && (c->N % 2 == 0) && c->tc_bops != nullptr;
+}
+
+size_t tc_bops_bytes(int n_elem, int n_freq) {
+  const size_t nbe = (size_t)(n_elem + ROWS - 1) / ROWS;
+  const size_t nks = (size_t)(n_elem + KS - 1) / KS;
+  return (size_t)n_freq * nbe * nks * M_B_BYTES;
+}
+
+int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const float2* Q,
+                         float2* part) {
+  cudaError_t e = set_attrs();
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "tc_contract attributes");
+    return -1;
+  }
+  const int nbe = (c->n_elem + ROWS - 1) / ROWS;
+  const int tiles = nbe * nbe * c->n_freq;
+  int split = c->n_sm / tiles;
+  if (split > c->jsplit_n) split = c->jsplit_n;
+  if (split < 1) split = 1;
+  long long chunk = (c->N + split - 1) / split;
+  chunk = ((chunk + KS - 1) / KS) * KS;
+  split = (int)((c->N + chunk - 1) / chunk);
+  ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq};
+  dim3 grid(split, nbe * nbe, c->n_freq);
+  const double fe = (double)c->n_freq * c->n_elem * c->N;
+  {
+    Prof pf(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(float2),
+            8.0 * fe * c->n_elem);
+    tc_contract_kernel<<<grid, NTHREADS, C_SMEM, c->stream>>>(args);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "tc_contract_kernel");
+    return -1;
+  }
+  return split;
+}
+
+int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart) {
+  cudaError_t e = set_attrs();
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "tc_jh attributes");
+    return -1;
+  }
+  const int nbe = (c->n_elem + ROWS - 1) / ROWS;
+  const int nks = (c->n_elem + KS - 1) / KS;
+  const long long nseg = (long long)c->n_freq * nbe * nks * 2 * 2 * BROWS;
+  {
+    Prof pf(c, KC_MISC);
+    tc_jh_bops_kernel<<<blocks_for(nseg, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        y, (float*)c->tc_bops, c->n_elem, nbe, nks, nseg);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "tc_jh_bops_kernel");
+    return -1;
+  }
+  const int npb = (int)((c->N + M_TILES * ROWS - 1) / (M_TILES * ROWS));
+  const int units = c->n_freq * nbe * npb;
+  const int grid = units < c->n_sm ? units : c->n_sm;
+  JhArgs args{X, (const float*)c->tc_bops, c->red, zpart, c->tc_err, c->N,
+              c->n_elem, c->n_freq, nbe, nks, npb, units};
+  {
+    const double fe = (double)c->n_freq * c->n_elem * c->N;
+    Prof pf(c, KC_MIX_JH, 2.0 * fe * sizeof(float2), 8.0 * fe * c->n_elem + 8.0 * fe);
+    tc_jh_kernel<<<grid, NTHREADS, M_SMEM, c->stream>>>(args);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(c, e, "tc_jh_kernel");
+    return -1;
+  }
+  return c->n_freq * nbe;
+}
+
+// The error word is read back with the callers' final synchronisation:
+// tc_err_fetch enqueues the copy, tc_err_check inspects it after the sync.
+void tc_err_fetch(fwi_ctx* c) {
+  if (c->tc_err && c->h_tc_err)
+    cudaMemcpyAsync(c->h_tc_err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+}
+
+fwi_status tc_err_check(fwi_ctx* c) {
+  if (!c->h_tc_err || *c->h_tc_err == 0) return FWI_OK;
+  const int code = *c->h_tc_err;
+  *c->h_tc_err = 0;
+  cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
+  return fail(c, FWI_ERR_CUDA,
+              std::string("tensor-core contraction: pipeline wait timed out (code ") +
+                  std::to_string(code) + ")");
+}
+
+}  // namespace fwi

@@ -61,7 +61,8 @@ class fwi_stats(Structure):
 
 class fwi_tuning(Structure):
     _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
-                ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4)]
+                ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
+                ("jac_tensor_cores", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -340,12 +341,28 @@ class Context:
         self._check(fwi_get_tuning(self.handle, byref(t)))
         return {"row_fwd": t.row_fwd_variant, "row_inv": t.row_inv_variant,
                 "col": t.col_variant, "col_y": t.col_y_variant, "tuned": t.tuned,
-                "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)]}
+                "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)],
+                "jac_tensor_cores": t.jac_tensor_cores}
 
-    def set_tuning(self, row_fwd=0, row_inv=0, col=0, col_y=0):
+    def set_tuning(self, row_fwd=None, row_inv=None, col=None, col_y=None,
+                   jac_tensor_cores=None):
+        """Force tile variants (0 when not given) and, optionally, switch the
+        tensor-core pixel contractions on (1) or off (0); None keeps the
+        current setting."""
         t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
         t.row_fwd_variant, t.row_inv_variant, t.col_variant, t.col_y_variant = (
-            row_fwd, row_inv, col, col_y)
+            row_fwd or 0, row_inv or 0, col or 0, col_y or 0)
+        if jac_tensor_cores is not None:
+            t.jac_tensor_cores = int(jac_tensor_cores)
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_jac_tensor_cores(self, on):
+        """Switch the FP32 pixel contractions between tensor cores (True) and
+        CUDA cores (False), keeping the tile variants."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.jac_tensor_cores = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def set_profiling(self, on):
