@@ -56,7 +56,7 @@ def describe(w):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "jac.cu"):
+    for f in ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "jac.cu", "jac_tc.cu", "tc.cuh"):
         with open(os.path.join(ROOT, "paper_2604_15796_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -210,6 +210,9 @@ def run_ours(args, rank, world, samples):
     with torch.cuda.stream(stream):
         ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6, stream=stream,
                              max_batch=args.max_batch)
+        if args.cuda_core_jacobian:
+            ctx.set_jac_tensor_cores(False)
+        tuning = ctx.tuning()
         c128 = torch.complex128
         sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
         m_true = ctx.contrast_from_sos(sos_true)
@@ -340,7 +343,9 @@ def run_ours(args, rank, world, samples):
     tot_ms = sum(k["ms"] for k in kst.values())
     op_classes = [k for k in kst if k.startswith(("row_", "col_"))]
     dominant = max(kst, key=lambda k: kst[k]["ms"])
-    roof = roofline(dominant, kst[dominant], peaks, peak_kind, w.name, clk.summary())
+    tensor = bool(tuning.get("jac_tensor_cores"))
+    roof = roofline(dominant, kst[dominant], peaks, peak_kind, w.name, tensor)
+    rates = {k: kernel_rates(k, v, peaks, tensor) for k, v in kst.items() if v["launches"]}
     share = {k: round(v["ms"] / tot_ms, 4) for k, v in sorted(kst.items(),
                                                              key=lambda kv: -kv[1]["ms"])}
     op_ms = sum(kst[k]["ms"] for k in op_classes)
@@ -354,7 +359,9 @@ def run_ours(args, rank, world, samples):
         "config": {"workload": describe(w), "l2": "inputs larger than L2 (fields "
                    f"{w.n_rhs * w.n * 8 / 1e6:.0f} MB per array)",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "krylov_tol": 1e-6, "admm": {k: v for k, v in params.items()}},
+                   "krylov_tol": 1e-6, "admm": {k: v for k, v in params.items()},
+                   "jacobian": "tensor cores (tcgen05, 3xTF32)" if tensor
+                   else "CUDA cores (FP32 FMA)"},
         "gradient_evals_per_s": args.steps * world / (ms / 1e3),
         "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
                            "fwd_mean": float(its[:, 2].mean()),
@@ -365,6 +372,7 @@ def run_ours(args, rank, world, samples):
                             "frac_of_hbm": (op_bytes / (op_ms * 1e6)) / peaks["hbm_gbs"]
                             if op_ms else None},
         "kernel_time_share": share,
+        "kernel_rates": rates,
         "gpu_launches": int(launches1 - launches0),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -374,23 +382,74 @@ def run_ours(args, rank, world, samples):
     return line
 
 
-def roofline(name, k, peaks, peak_kind, wname, clocks):
+TENSOR_CLASSES = ("contract_pixels", "mix_jac_adjoint", "mix_adjoint_sources")
+
+
+def peak_table(peaks, peak_kind):
+    """Denominators: measured HBM copy bandwidth; FP32 FMA peak from the SM
+    count and clock; the TF32 tensor peak from the measured bf16 GEMM peak
+    and the nominal tf32/bf16 ratio (1/2), divided by the three TF32
+    products of one FP32 product (3xTF32)."""
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+    return {
+        "hbm": (peaks["hbm_gbs"], "GB/s", f"{peak_kind} hbm_gbs"),
+        "alu": (152 * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
+                f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"),
+        "tensor": (peaks["bf16_tflops"] * 0.5 / 3.0, "TFLOP/s",
+                   f"{peak_kind} bf16_tflops {peaks['bf16_tflops']:.0f} x 1/2 (tf32/bf16 nominal)"
+                   " / 3 (3xTF32 products per FP32 product)"),
+    }
+
+
+def bound_of(name, k, tensor):
+    """The resource that limits a kernel class (from its ncu counters): the
+    pixel contractions run on the tensor cores (or FP32 FMA without them),
+    the column FFT passes are instruction-issue bound, the row passes and
+    vector kernels stream HBM."""
+    if name in TENSOR_CLASSES:
+        return "tensor" if tensor else "alu"
+    if name.startswith("col_") and k["flops"] > 0:
+        return "alu"
+    if k["bytes"] > 0:
+        return "hbm"
+    return "alu" if k["flops"] > 0 else None
+
+
+def kernel_rates(name, k, peaks, tensor):
+    tab = peak_table(peaks, "measured")
+    avg_ms = k["ms"] / k["launches"]
+    out = {"ms_per_launch": round(avg_ms, 4), "launches": k["launches"]}
+    if k["bytes"] > 0:
+        gbs = k["bytes"] / k["launches"] / (avg_ms * 1e6)
+        out["gbs"] = round(gbs, 1)
+        out["hbm_frac"] = round(gbs / tab["hbm"][0], 3)
+    if k["flops"] > 0:
+        tf = k["flops"] / k["launches"] / (avg_ms * 1e9)
+        out["tflops"] = round(tf, 2)
+        b = bound_of(name, k, tensor)
+        if b in ("alu", "tensor"):
+            out[b + "_frac"] = round(tf / tab[b][0], 3)
+    return out
+
+
+def roofline(name, k, peaks, peak_kind, wname, tensor):
     avg_ms = k["ms"] / k["launches"]
     rec = recorded_traffic(name, wname)
-    if k["bytes"] > 0 and (name.startswith(("row_", "col_", "gradient")) or k["flops"] == 0):
+    bound = bound_of(name, k, tensor) or "hbm"
+    peak, unit, src = peak_table(peaks, peak_kind)[bound]
+    if bound == "hbm":
         achieved = k["bytes"] / k["launches"] / (avg_ms * 1e6)
-        peak = peaks["hbm_gbs"]
-        out = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-               "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs"}
     else:
         achieved = k["flops"] / k["launches"] / (avg_ms * 1e9)
-        mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x clock
-        out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-               "frac": achieved / peak,
-               "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
+    out = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "peak_source": src}
+    if bound != "hbm" and k["bytes"] > 0:
+        gbs = k["bytes"] / k["launches"] / (avg_ms * 1e6)
+        out["hbm_gbs_at_algorithmic_bytes"] = gbs
+        out["hbm_frac"] = gbs / peaks["hbm_gbs"]
     out.update({"kernel": name, "launches": k["launches"], "avg_launch_ms": avg_ms,
                 "algorithmic_bytes_per_launch": k["bytes"] / k["launches"],
+                "algorithmic_flops_per_launch": k["flops"] / k["launches"],
                 "traffic": None})
     if rec is not None:
         bpl, units = rec
@@ -531,6 +590,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--cuda-core-jacobian", action="store_true",
+                    help="run the pixel contractions on CUDA cores instead of tensor cores")
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--check-samples", type=int, default=2)

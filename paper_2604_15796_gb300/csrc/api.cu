@@ -1,6 +1,7 @@
 // C entry points of libfwi (include/libfwi.h): argument checks, context
 // creation and workspace accounting, and the composition of the hot-path
 // steps into the calls of the paper's problem statement (Sec. II-III).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -65,6 +66,15 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.n_rhs = d->n_elem * d->n_freq;
   L.batch = (d->max_batch > 0 && d->max_batch < L.n_rhs) ? d->max_batch : L.n_rhs;
   L.N = (long long)L.nx * L.ny * L.nz;
+  {
+    // the FFT passes index their work items (batch x lines or column tiles)
+    // with 32-bit arithmetic
+    const long long per = std::max({(long long)L.ny * L.nz, (long long)L.lx * L.ly,
+                                    (long long)L.nz * L.lx});
+    const long long cap = 0x7fffffffLL / per;
+    if (cap < 1) return bad("grid too large");
+    if (L.batch > cap) L.batch = (int)cap;
+  }
   L.rows = L.ny * L.nz;
   L.csz = (d->precision == FWI_FP64) ? 16 : 8;
   const int lpc = (d->precision == FWI_FP64) ? Lsop<double>::row_lines_per_cta(L.lx)

@@ -119,6 +119,7 @@ size_t tc_bops_bytes(int n_elem, int n_freq);
 int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const float2* Q,
                          float2* part);
 int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart);
+int tc_adjoint_sources(fwi_ctx* c, const float2* B, const float2* Q, float2* out);
 void tc_err_fetch(fwi_ctx* c);
 fwi_status tc_err_check(fwi_ctx* c);
 }  // namespace fwi

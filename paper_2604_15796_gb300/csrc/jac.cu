@@ -455,6 +455,13 @@ fwi_status residual_misfit(fwi_ctx* c, const void* d_obs, double* misfit) {
 template <typename T> static fwi_status adjoint_sources_t(fwi_ctx* c, void* out) {
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc_usable(c)) {
+      if (tc_adjoint_sources(c, (const float2*)c->dF, (const float2*)c->p0, (float2*)out) < 0)
+        return FWI_ERR_CUDA;
+      return FWI_OK;
+    }
+  }
   dim3 grid((unsigned)((c->N + TB - 1) / TB), (c->n_elem + TB - 1) / TB, c->n_freq);
   const double fe = (double)c->n_freq * c->n_elem * c->N;
   Prof p(c, KC_MIX_SOURCES, 2.0 * fe * sizeof(cplx<T>), 8.0 * fe * c->n_elem);

@@ -111,12 +111,20 @@ __device__ __forceinline__ float2 lds64(uint32_t addr) {
 // Contraction: one CTA per (pixel chunk s, tile pair (eb, jb), frequency l);
 // accumulator D[e][j] (128 x [128 Re | 128 Im]) over its pixel chunk,
 // written as FP32 partials part[s][l][e][j].
-constexpr int C_CONV = 3, C_RAW = 3;
+// Raw stages: 128 rows of X (and of Q unless the two share rows) plus the
+// 8 weights a[n]; SHARED (X == Q, one element tile) keeps 10 stages in
+// flight, the general case 5, which fills the shared memory left by the
+// three conversion stages.
+constexpr int C_CONV = 3;
 constexpr int C_RAWROW = 80;  // 8 complex (64 bytes) + 16 bytes of padding
-constexpr int C_RAW_X = 0, C_RAW_Q = ROWS * C_RAWROW, C_RAW_A = 2 * ROWS * C_RAWROW;
-constexpr int C_RAW_BYTES = 2 * ROWS * C_RAWROW + 64;
 constexpr int C_CONV_BYTES = 4 * PLANE + 2 * BPLANE;
-constexpr int C_SMEM = C_CONV * C_CONV_BYTES + C_RAW * C_RAW_BYTES;
+template <bool SHARED> struct CRaw {
+  static constexpr int N = SHARED ? 10 : 5;
+  static constexpr int X = 0, Q = ROWS * C_RAWROW;
+  static constexpr int A = (SHARED ? 1 : 2) * ROWS * C_RAWROW;
+  static constexpr int BYTES = A + 64;
+  static constexpr int SMEM = C_CONV * C_CONV_BYTES + N * BYTES;
+};
 
 struct ContractArgs {
   const float2* X;
@@ -128,8 +136,12 @@ struct ContractArgs {
   int NE, n_freq;
 };
 
+template <bool SHARED>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p) {
   using namespace tc;
+  using RW = CRaw<SHARED>;
+  constexpr int C_RAW = RW::N, C_RAW_BYTES = RW::BYTES;
+  constexpr int C_RAW_X = RW::X, C_RAW_Q = RW::Q, C_RAW_A = RW::A;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done;
   __shared__ uint32_t tmem_base;
@@ -143,7 +155,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
   const int nch = (n_begin < p.N) ? (int)((n_end - n_begin + KS - 1) / KS) : 0;
   const float2* Xl = p.X + (long long)l * p.NE * p.N;
   const float2* Ql = p.Q + (long long)l * p.NE * p.N;
-  const bool same_rows = (p.X == p.Q) && (eb == jb);
+  constexpr bool same_rows = SHARED;
   const bool has_a = p.a != nullptr;
 
   if (tid == 0) {
@@ -307,12 +319,17 @@ struct JhArgs {
   const float2* X;     // [n_freq][NE][N]
   const float* bops;   // [n_freq][nbe][nks] k-step blocks of the B stack (hi, lo)
   const double* scale; // [n_freq]
-  float2* zpart;       // [n_freq][nbe][N]
+  float2* zpart;       // FUSED: [n_freq][nbe][N]; else W itself, [n_freq][NE][N]
   int* err;
   long long N;
   int NE, n_freq, nbe, nks, npb, units;
+  int conj_x;          // A = conj(X)^T (J^H) or X^T (adjoint sources)
 };
 
+// FUSED: z_l[n] = s_l sum_e conj(X[e][n]) W[e][n] (J^H b); otherwise the
+// mix W_l[e][n] = s_l sum_j B[e][j] X'[j][n] itself is written (adjoint
+// sources conj(s_e) = k^2 dV sum_j p0_j conj(r_ej)).
+template <bool FUSED>
 __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -403,7 +420,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
           for (int i = 0; i < 4; ++i) {
             const float2 v = lds64(rb + (uint32_t)(t * M_RAW_TILE + (4 * half + i) * ROWS * 8 + 8 * r));
             re[i] = v.x;
-            im[i] = -v.y;  // A = conj(X)^T
+            im[i] = p.conj_x ? -v.y : v.y;
           }
           put_a(ab + 0 * PLANE, ab + 1 * PLANE, half, r, re);
           put_a(ab + 2 * PLANE, ab + 3 * PLANE, half, r, im);
@@ -419,8 +436,30 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
         const float2* Xl = p.X + (long long)l * p.NE * p.N;
         const float sc = (float)p.scale[l];
         const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+        if constexpr (!FUSED) {
 #pragma unroll 1
-        for (int t = 0; t < M_TILES; ++t) {
+          for (int t = 0; t < M_TILES; ++t) {
+            const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + r;
+            const bool nv = n < p.N;
+#pragma unroll 1
+            for (int ec = 0; ec < ROWS / 32; ++ec) {
+              uint32_t wr[32], wi[32];
+              tmem_ld32(lane_addr + (uint32_t)(t * 256 + 32 * ec), wr);
+              tmem_ld32(lane_addr + (uint32_t)(t * 256 + ROWS + 32 * ec), wi);
+              tmem_wait_ld();
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                const int e = eb * ROWS + 32 * ec + i;
+                if (nv && e < p.NE)
+                  p.zpart[((long long)l * p.NE + e) * p.N + n] =
+                      ok ? make_float2(__uint_as_float(wr[i]) * sc, __uint_as_float(wi[i]) * sc)
+                         : make_float2(0.f, 0.f);
+              }
+            }
+          }
+        }
+#pragma unroll 1
+        for (int t = 0; t < (FUSED ? M_TILES : 0); ++t) {
           const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + r;
           const bool nv = n < p.N;
           float zx = 0.f, zy = 0.f;
@@ -478,7 +517,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
 // B operand of J^H: per (l, eb, k-step) the stack [-Bi | Br | Bi] of
 // B = y_l[e][j] (e in tile eb, j in the k-step) as TF32 hi and lo planes,
 // laid out exactly as one shared-memory stage.
-__global__ void tc_jh_bops_kernel(const double2* __restrict__ y, float* __restrict__ bops,
+template <typename V>
+__global__ void tc_jh_bops_kernel(const V* __restrict__ y, float* __restrict__ bops,
                                   int NE, int nbe, int nks, long long nseg) {
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < nseg;
        idx += (long long)gridDim.x * blockDim.x) {
@@ -494,8 +534,8 @@ __global__ void tc_jh_bops_kernel(const double2* __restrict__ y, float* __restri
       const int j = ks * KS + 4 * half + k;
       double x = 0.0;
       if (e < NE && j < NE) {
-        const double2 b = y[(l * NE + e) * NE + j];
-        x = part == 0 ? -b.y : (part == 1 ? b.x : b.y);
+        const V b = y[(l * NE + e) * NE + j];
+        x = part == 0 ? -(double)b.y : (part == 1 ? (double)b.x : (double)b.y);
       }
       const float hi = tc::to_tf32((float)x);
       v[k] = hl == 0 ? hi : tc::to_tf32((float)(x - (double)hi));
@@ -516,14 +556,28 @@ cudaError_t g_attr_err = cudaSuccess;
 
 cudaError_t set_attrs() {
   std::call_once(g_attr_once, [] {
-    g_attr_err = cudaFuncSetAttribute(tc_contract_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, C_SMEM);
+    g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      CRaw<true>::SMEM);
     if (g_attr_err == cudaSuccess)
-      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel,
+      g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        CRaw<false>::SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
   });
   return g_attr_err;
 }
+
+// Shared launcher of the two mixes; B is [n_freq][NE][NE] (double2 for
+// J^H, float2 for the adjoint sources).
+template <bool FUSED, typename V>
+int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int kclass,
+           double bytes, double flops);
 
 }  // namespace
 
@@ -558,7 +612,10 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   {
     Prof pf(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(float2),
             8.0 * fe * c->n_elem);
-    tc_contract_kernel<<<grid, NTHREADS, C_SMEM, c->stream>>>(args);
+    if (X == Q && nbe == 1)
+      tc_contract_kernel<true><<<grid, NTHREADS, CRaw<true>::SMEM, c->stream>>>(args);
+    else
+      tc_contract_kernel<false><<<grid, NTHREADS, CRaw<false>::SMEM, c->stream>>>(args);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -568,10 +625,14 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   return split;
 }
 
-int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart) {
+namespace {
+
+template <bool FUSED, typename V>
+int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int kclass,
+           double bytes, double flops) {
   cudaError_t e = set_attrs();
   if (e != cudaSuccess) {
-    cuda_fail(c, e, "tc_jh attributes");
+    cuda_fail(c, e, "tc_mix attributes");
     return -1;
   }
   const int nbe = (c->n_elem + ROWS - 1) / ROWS;
@@ -579,8 +640,8 @@ int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart)
   const long long nseg = (long long)c->n_freq * nbe * nks * 2 * 2 * BROWS;
   {
     Prof pf(c, KC_MISC);
-    tc_jh_bops_kernel<<<blocks_for(nseg, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-        y, (float*)c->tc_bops, c->n_elem, nbe, nks, nseg);
+    tc_jh_bops_kernel<V><<<blocks_for(nseg, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        B, (float*)c->tc_bops, c->n_elem, nbe, nks, nseg);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -590,12 +651,11 @@ int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart)
   const int npb = (int)((c->N + M_TILES * ROWS - 1) / (M_TILES * ROWS));
   const int units = c->n_freq * nbe * npb;
   const int grid = units < c->n_sm ? units : c->n_sm;
-  JhArgs args{X, (const float*)c->tc_bops, c->red, zpart, c->tc_err, c->N,
-              c->n_elem, c->n_freq, nbe, nks, npb, units};
+  JhArgs args{X, (const float*)c->tc_bops, c->red, out, c->tc_err, c->N,
+              c->n_elem, c->n_freq, nbe, nks, npb, units, conj_x};
   {
-    const double fe = (double)c->n_freq * c->n_elem * c->N;
-    Prof pf(c, KC_MIX_JH, 2.0 * fe * sizeof(float2), 8.0 * fe * c->n_elem + 8.0 * fe);
-    tc_jh_kernel<<<grid, NTHREADS, M_SMEM, c->stream>>>(args);
+    Prof pf(c, kclass, bytes, flops);
+    tc_jh_kernel<FUSED><<<grid, NTHREADS, M_SMEM, c->stream>>>(args);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -603,6 +663,20 @@ int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart)
     return -1;
   }
   return c->n_freq * nbe;
+}
+
+}  // namespace
+
+int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart) {
+  const double fe = (double)c->n_freq * c->n_elem * c->N;
+  return tc_mix<true>(c, y, X, 1, zpart, KC_MIX_JH, 2.0 * fe * sizeof(float2),
+                      8.0 * fe * c->n_elem + 8.0 * fe);
+}
+
+int tc_adjoint_sources(fwi_ctx* c, const float2* B, const float2* Q, float2* out) {
+  const double fe = (double)c->n_freq * c->n_elem * c->N;
+  return tc_mix<false>(c, B, Q, 0, out, KC_MIX_SOURCES, 2.0 * fe * sizeof(float2),
+                       8.0 * fe * c->n_elem);
 }
 
 // The error word is read back with the callers' final synchronisation:

@@ -321,6 +321,21 @@ template <typename T> double pass_bytes(const fwi_ctx* c, int kind) {
   }
 }
 
+// Nominal FFT flops of one column pass for one right-hand side: 5 L log2 L
+// per complex L-point transform (forward and inverse along the column for
+// the convolution, one transform for the 3-D y passes) plus 6 flops per
+// spectrum multiply.
+template <typename T> double pass_flops(const fwi_ctx* c, int kind) {
+  auto fft = [](double L) { return 5.0 * L * std::log2(L); };
+  const double lx = c->lx, ly = c->ly, lz = c->lz;
+  switch (kind) {
+    case KC_COL_CONV: return lx * ly * (2.0 * fft(lz) + 6.0 * lz);
+    case KC_COL_FWD:
+    case KC_COL_INV: return lx * (double)c->nz * fft(ly);
+    default: return 0.0;
+  }
+}
+
 // Ghat reads of one convolution launch (once per frequency).
 template <typename T> double ghat_bytes(const fwi_ctx* c) {
   return (double)c->n_freq * c->lx * c->ly * c->lz * sizeof(cplx<T>);
@@ -333,22 +348,26 @@ template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list, doub
   ColArgs<T> z = b.cz;
   if (!use_list) z.active = nullptr;
   if (c->dim == 2) {
-    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
+    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c),
+           units * pass_flops<T>(c, KC_COL_CONV));
     return Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
   }
   ColArgs<T> y = b.cy_fwd, w = b.cy_inv;
   if (!use_list) { y.active = nullptr; w.active = nullptr; }
   cudaError_t e;
   {
-    Prof p(c, KC_COL_FWD, units * pass_bytes<T>(c, KC_COL_FWD));
+    Prof p(c, KC_COL_FWD, units * pass_bytes<T>(c, KC_COL_FWD),
+           units * pass_flops<T>(c, KC_COL_FWD));
     e = Lsop<T>::col(c->ly, y, c->stream, c->var_cy);
   }
   if (e == cudaSuccess) {
-    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c));
+    Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c),
+           units * pass_flops<T>(c, KC_COL_CONV));
     e = Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
   }
   if (e == cudaSuccess) {
-    Prof p(c, KC_COL_INV, units * pass_bytes<T>(c, KC_COL_INV));
+    Prof p(c, KC_COL_INV, units * pass_bytes<T>(c, KC_COL_INV),
+           units * pass_flops<T>(c, KC_COL_INV));
     e = Lsop<T>::col(c->ly, w, c->stream, c->var_cy);
   }
   return e;

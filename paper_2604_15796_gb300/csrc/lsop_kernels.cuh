@@ -22,20 +22,64 @@
 
 namespace fwi {
 
+// FP64 sum of NV (a power of two, <= 32) values over the 32 lanes of a
+// warp, reduce-scatter style: at each of the first log2(NV) levels a lane
+// keeps half of its values and adds the partner's copy of that half, so a
+// lane performs NV - 1 + (5 - log2 NV) additions instead of 5 NV.  (FP64
+// issues at a small fraction of the FP32 rate on this part.)  The pairing
+// is fixed, so the result is deterministic.  On return every lane holds
+// all NV sums in out[].
+template <int NV>
+__device__ __forceinline__ void warp_sum_scatter(double (&d)[NV], double (&out)[NV]) {
+  static_assert(NV >= 1 && NV <= 32 && (NV & (NV - 1)) == 0, "NV must be a power of two");
+  const int lane = threadIdx.x & 31;
+  int off = 16;
+#pragma unroll
+  for (int h = NV / 2; h >= 1; h >>= 1, off >>= 1) {
+    const bool hi = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const double keep = hi ? d[i + h] : d[i];
+      const double send = hi ? d[i] : d[i + h];
+      d[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+  for (; off >= 1; off >>= 1) d[0] += __shfl_xor_sync(0xffffffffu, d[0], off);
+  // value k now sits in lanes k * (32 / NV) ... (k + 1) * (32 / NV) - 1
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = __shfl_sync(0xffffffffu, d[0], k * (32 / NV));
+}
+
 // Per-line fixed-order sums of NV per-thread values over the TL threads of
 // each line.  The result does not depend on how many lines a CTA holds, so
 // tile shapes can be tuned without changing any bit of the partial inner
-// products.  Power-of-two lines up to a warp reduce with a shuffle
-// butterfly inside their aligned lane segment, 64-thread lines add the two
-// warp results, other lengths use a shared-memory tree.  Every thread of
-// the CTA must call it; thread t == 0 of each line receives the sums.
+// products.  32-thread lines use the warp reduce-scatter above (NV a power
+// of two), 64-thread lines add the two warp results, shorter power-of-two
+// lines reduce with a shuffle butterfly inside their aligned lane segment,
+// other lengths use a shared-memory tree.  Every thread of the CTA must
+// call it; thread t == 0 of each line receives the sums.
 template <int TL, int NTHREADS, int NV, typename A>
 __device__ __forceinline__ void line_sum(const A (&acc)[NV], int line, int t,
                                          double (&out)[NV]) {
   double d[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) d[k] = (double)acc[k];
-  if constexpr ((TL & (TL - 1)) == 0 && TL <= 32) {
+  if constexpr (TL == 32 && (NV & (NV - 1)) == 0) {
+    warp_sum_scatter<NV>(d, out);
+  } else if constexpr (TL == 64 && (NV & (NV - 1)) == 0) {
+    __shared__ double red[NTHREADS / 32][NV];
+    double w[NV];
+    warp_sum_scatter<NV>(d, w);
+    const int warp = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) red[warp][k] = w[k];
+    __syncthreads();
+    if (t == 0)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) out[k] = red[2 * line][k] + red[2 * line + 1][k];
+    __syncthreads();
+  } else if constexpr ((TL & (TL - 1)) == 0 && TL <= 32) {
 #pragma unroll
     for (int off = TL / 2; off > 0; off >>= 1)
 #pragma unroll
@@ -317,10 +361,13 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
   const int t = threadIdx.x - line * P::TL;
   V* sml = sm + line * LSTR;
   const int nact = a.active ? *a.n_active : a.nb;
-  const long long items = (long long)nact * a.ntiles;
-  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
-    const int slot = (int)(item / a.ntiles);
-    const int tile = (int)(item - (long long)slot * a.ntiles);
+  // 32-bit item arithmetic: the context caps the batch so that every item
+  // count fits (fwi_create)
+  const unsigned ntiles = (unsigned)a.ntiles;
+  const unsigned items = (unsigned)nact * ntiles;
+  for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
+    const int slot = (int)(item / ntiles);
+    const int tile = (int)(item - (unsigned)slot * ntiles);
     const int rhs = a.active ? a.active[slot] : slot;
     const int row = tile * LPC + line;
     const bool valid = row < a.rows;
@@ -491,10 +538,13 @@ __device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* s
   constexpr bool dots = MODE == RI_V || MODE == RI_T || MODE == RI_R0;
   constexpr int NS = RowSlots<P>::N;
   const int nact = a.active ? *a.n_active : a.nb;
-  const long long items = (long long)nact * a.ntiles;
-  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
-    const int slot = (int)(item / a.ntiles);
-    const int tile = (int)(item - (long long)slot * a.ntiles);
+  // 32-bit item arithmetic: the context caps the batch so that every item
+  // count fits (fwi_create)
+  const unsigned ntiles = (unsigned)a.ntiles;
+  const unsigned items = (unsigned)nact * ntiles;
+  for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
+    const int slot = (int)(item / ntiles);
+    const int tile = (int)(item - (unsigned)slot * ntiles);
     const int rhs = a.active ? a.active[slot] : slot;
     const int row = tile * LPC + line;
     const bool valid = row < a.rows;
@@ -524,13 +574,41 @@ __device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* s
       ri_store<P, T, MODE>(a, t, rhs, row, v, q0, q1, acc);
     }
     if (dots) {
-      double tot[2 * NSLOT];
-      line_sum<P::TL, LPC * P::TL, 2 * NSLOT>(acc, line, t, tot);
+      // only the live accumulators enter the FP64 line sum
+      constexpr int NV = MODE == RI_T ? 8 : 2;
+      T live[NV];
+      if constexpr (MODE == RI_T) {
+        const int src[8] = {0, 1, 2, 4, 5, 6, 7, 8};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) live[k] = acc[src[k]];
+      } else if constexpr (MODE == RI_V) {
+        live[0] = acc[0];
+        live[1] = acc[1];
+      } else {
+        live[0] = acc[0];
+        live[1] = acc[2];
+      }
+      double tot[NV];
+      line_sum<P::TL, LPC * P::TL, NV>(live, line, t, tot);
       if (t == 0 && valid) {
+        double full[2 * NSLOT];
+#pragma unroll
+        for (int k = 0; k < 2 * NSLOT; ++k) full[k] = 0.0;
+        if constexpr (MODE == RI_T) {
+          const int dst_k[8] = {0, 1, 2, 4, 5, 6, 7, 8};
+#pragma unroll
+          for (int k = 0; k < 8; ++k) full[dst_k[k]] = tot[k];
+        } else if constexpr (MODE == RI_V) {
+          full[0] = tot[0];
+          full[1] = tot[1];
+        } else {
+          full[0] = tot[0];
+          full[2] = tot[1];
+        }
         double2* dst = a.partial + (long long)rhs * NSLOT * a.rows + row;
 #pragma unroll
         for (int k = 0; k < NSLOT; ++k)
-          dst[(long long)k * a.rows] = make_double2(tot[2 * k], tot[2 * k + 1]);
+          dst[(long long)k * a.rows] = make_double2(full[2 * k], full[2 * k + 1]);
       }
     }
   }
@@ -571,16 +649,16 @@ col_kernel(const ColArgs<T> a) {
   const int c = threadIdx.x % TC;
   const int t = threadIdx.x / TC;
   V* smc = sm + c;
-  const int ntile = a.ncols / TC;
-  const long long per_rhs = (long long)a.nplanes * ntile;
+  const unsigned ntile = (unsigned)(a.ncols / TC);
+  const unsigned per_rhs = (unsigned)a.nplanes * ntile;
   const int nact = a.active ? *a.n_active : a.nb;
-  const long long items = (long long)nact * per_rhs;
+  const unsigned items = (unsigned)nact * per_rhs;  // < 2^31 (fwi_create caps the batch)
   const long long ls = a.line_stride;
-  for (long long item = blockIdx.x; item < items; item += gridDim.x) {
+  for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
     const int slot = (int)(item / per_rhs);
-    const long long rem = item - (long long)slot * per_rhs;
-    const int plane = (int)(rem / ntile);
-    const int tile = (int)(rem - (long long)plane * ntile);
+    const unsigned rem = item - (unsigned)slot * per_rhs;
+    const int plane = (a.nplanes == 1) ? 0 : (int)(rem / ntile);
+    const int tile = (int)(rem - (unsigned)plane * ntile);
     const int rhs = a.active ? a.active[slot] : slot;
     const int j = tile * TC + c;
     const V* __restrict__ in = a.in + rhs * a.in_rhs_stride + plane * a.in_plane_stride + j;

@@ -1,12 +1,16 @@
 """Time the Lippmann-Schwinger operator passes (row FFT, column convolution,
-inverse row FFT) on a synthetic batch, for kernel tuning and ncu captures.
+inverse row FFT) or the Jacobian contractions on a synthetic batch, for
+kernel tuning and ncu captures.
 
     python -m paper_2604_15796_gb300.profile_op --grid 256 --rhs 256 --reps 3
+    python -m paper_2604_15796_gb300.profile_op --jac --grid 256 --rhs 128 --nfreq 2
 
-Creates a context with ``rhs`` array elements at one frequency (so that one
-operator application processes ``rhs`` right-hand sides), applies
-A = I - K diag(m) ``reps`` times and prints the per-pass device times
-measured with CUDA events (profiling mode) as JSON.
+Operator mode: a context with ``rhs`` array elements at one frequency (one
+operator application processes ``rhs`` right-hand sides) applies
+A = I - K diag(m) ``reps`` times.  Jacobian mode (--jac): ``rhs`` elements at
+``nfreq`` frequencies; one forward solve, then ``reps`` products J a and
+J^H b.  Prints the per-kernel-class device times measured with CUDA events
+(profiling mode) as JSON.
 """
 import argparse
 import json
@@ -25,18 +29,41 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--freq", type=float, default=3e6)
     ap.add_argument("--fp64", action="store_true")
+    ap.add_argument("--jac", action="store_true")
+    ap.add_argument("--nfreq", type=int, default=2)
+    ap.add_argument("--cuda-core-jacobian", action="store_true")
     args = ap.parse_args()
     nz = args.depth or args.grid
     shape = (nz, args.grid)
     h = 0.1e-3
+    freqs = np.linspace(0.5e6, args.freq, args.nfreq) if args.jac else np.array([args.freq])
     w = phantoms.tissue_phantom(shape, h, args.rhs, min(0.2e-3, args.grid * h / args.rhs),
-                                np.array([args.freq]), 5, inclusions=[1520.0, 1580.0])
+                                freqs, 5, inclusions=[1520.0, 1580.0])
     prec = libfwi.FWI_FP64 if args.fp64 else libfwi.FWI_MIXED
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, precision=prec,
                              stream=stream)
         m = ctx.contrast_from_sos(torch.from_numpy(np.ascontiguousarray(w.sos)).cuda())
+        if args.jac:
+            if args.cuda_core_jacobian:
+                ctx.set_jac_tensor_cores(False)
+            ctx.forward(m)
+            a = torch.from_numpy(phantoms.complex_normal(shape, 3)).cuda()
+            y = ctx.jac_forward(a)
+            ctx.jac_adjoint(y)  # warm-up
+            torch.cuda.synchronize()
+            ctx.reset_stats()
+            ctx.set_profiling(True)
+            for _ in range(args.reps):
+                y = ctx.jac_forward(a)
+                ctx.jac_adjoint(y)
+            torch.cuda.synchronize()
+            _, ks = ctx.stats()
+            ctx.set_profiling(False)
+            ctx.close()
+            report(shape, args.rhs * args.nfreq, ks)
+            return
         dt = torch.complex128 if args.fp64 else torch.complex64
         v = torch.from_numpy(phantoms.complex_normal((args.rhs,) + shape, 3)).to(
             device="cuda", dtype=dt)
@@ -50,13 +77,18 @@ def main():
         _, ks = ctx.stats()
         ctx.set_profiling(False)
         ctx.close()
+    report(shape, args.rhs, ks)
+
+
+def report(shape, rhs, ks):
     out = {}
     for name, k in ks.items():
         if k["launches"]:
             ms = k["ms"] / k["launches"]
             out[name] = {"ms_per_launch": ms,
-                         "gbs": k["bytes"] / k["launches"] / (ms * 1e6) if k["bytes"] else None}
-    print(json.dumps({"grid": list(shape), "rhs": args.rhs, "passes": out}))
+                         "gbs": k["bytes"] / k["launches"] / (ms * 1e6) if k["bytes"] else None,
+                         "tflops": k["flops"] / k["launches"] / (ms * 1e9) if k["flops"] else None}
+    print(json.dumps({"grid": list(shape), "rhs": rhs, "passes": out}))
 
 
 if __name__ == "__main__":

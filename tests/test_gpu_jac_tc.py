@@ -87,3 +87,32 @@ def test_tensor_core_products_are_deterministic(lib):
     r2 = (to_np(ctx.jac_forward(a)), to_np(ctx.jac_adjoint(b)))
     ctx.close()
     assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+
+
+@pytest.mark.parametrize("shape,n_elem,freqs", [((32, 32), 6, (1.5e6, 3.0e6)),
+                                                ((16, 128), 136, (2.0e6,))])
+def test_gradient_with_tensor_core_mixes(lib, shape, n_elem, freqs):
+    """Data projection, adjoint sources (materialised mix) and gradient: the
+    tensor-core and CUDA-core paths agree, and both match the oracle."""
+    import torch
+    w = _workload(shape, n_elem, freqs)
+    prob = oracle_problem(w)
+    m_true = contrast(w)
+    m0 = 0.5 * m_true
+    _, d_obs = inverse.forward_model(m_true, prob, "bicgstab", tol=1e-12)
+    d32 = d_obs.astype(np.complex64)
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs)
+    m_gpu = to_gpu(m0, torch.complex128)
+    out = {}
+    for tc in (True, False):
+        ctx.set_jac_tensor_cores(tc)
+        grad = torch.empty(w.shape, dtype=torch.complex128, device="cuda")
+        mis, _, _ = ctx.gradient(m_gpu, to_gpu(d32, torch.complex64), grad)
+        out[tc] = (to_np(grad), mis)
+    ctx.close()
+    assert rel_l2(out[True][0], out[False][0]) < 1e-5
+    # the data agree to ~1e-6 (FP32 rounding); the misfit of a partly fitted
+    # model amplifies that by |d| / |F(m) - d|
+    assert abs(out[True][1] - out[False][1]) <= 1e-4 * out[False][1]
+    ref = inverse.gradient(m0, d32.astype(np.complex128), prob, "bicgstab", tol=1e-12)
+    assert rel_l2(out[True][0], ref["grad"]) < 1e-3
