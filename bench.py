@@ -212,6 +212,8 @@ def run_ours(args, rank, world, samples):
                              max_batch=args.max_batch)
         if args.cuda_core_jacobian:
             ctx.set_jac_tensor_cores(False)
+        if args.one_chain:
+            ctx.set_overlap(False)
         tuning = ctx.tuning()
         c128 = torch.complex128
         sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
@@ -361,7 +363,8 @@ def run_ours(args, rank, world, samples):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "krylov_tol": 1e-6, "admm": {k: v for k, v in params.items()},
                    "jacobian": "tensor cores (tcgen05, 3xTF32)" if tensor
-                   else "CUDA cores (FP32 FMA)"},
+                   else "CUDA cores (FP32 FMA)",
+                   "krylov_chains": 2 if tuning.get("overlap_halves") else 1},
         "gradient_evals_per_s": args.steps * world / (ms / 1e3),
         "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
                            "fwd_mean": float(its[:, 2].mean()),
@@ -590,6 +593,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
+    ap.add_argument("--one-chain", action="store_true",
+                    help="iterate each batch as one chain (no two-stream overlap)")
     ap.add_argument("--cuda-core-jacobian", action="store_true",
                     help="run the pixel contractions on CUDA cores instead of tensor cores")
     ap.add_argument("--requests", type=int, default=16)

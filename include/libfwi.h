@@ -322,6 +322,12 @@ typedef struct fwi_tuning {
                            (tcgen05, 3xTF32 products, FP32 accumulation);
                            0: CUDA-core FP32 kernels.  FP64 contexts and odd
                            pixel counts always use the CUDA-core kernels. */
+  int overlap_halves;   /* 1 (default): batches of >= 32 right-hand sides
+                           iterate as two independent halves on two streams
+                           of one CUDA graph, so that the passes of one half
+                           fill the SMs the other half's passes leave idle;
+                           results are bitwise the same as with 0 (one
+                           chain). */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

@@ -142,6 +142,9 @@ static void release(fwi_ctx* c) {
   if (c->h_tc_err) cudaFreeHost(c->h_tc_err);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->stream2) cudaStreamDestroy(c->stream2);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
   delete c;
   cudaSetDevice(cur);
@@ -236,6 +239,9 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   if (e == cudaSuccess) *c->h_tc_err = 0;
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     fwi_status st = (e == cudaErrorMemoryAllocation) ? FWI_ERR_NOMEM : FWI_ERR_CUDA;
     fail(nullptr, st, std::string("workspace allocation: ") + cudaGetErrorString(e));
@@ -417,6 +423,7 @@ fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
   out->col_y_variant = ctx->var_cy;
   out->tuned = ctx->tuned;
   out->jac_tensor_cores = ctx->use_tc ? 1 : 0;
+  out->overlap_halves = ctx->overlap ? 1 : 0;
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
   return FWI_OK;
@@ -434,7 +441,10 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
     if (req[k] < 0 || req[k] >= lims[k]) return fail(ctx, FWI_ERR_INVALID_ARG, "variant out of range");
   if (in->jac_tensor_cores != 0 && in->jac_tensor_cores != 1)
     return fail(ctx, FWI_ERR_INVALID_ARG, "jac_tensor_cores must be 0 or 1");
+  if (in->overlap_halves != 0 && in->overlap_halves != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "overlap_halves must be 0 or 1");
   ctx->use_tc = in->jac_tensor_cores == 1;
+  ctx->overlap = in->overlap_halves == 1;
   ctx->var_rf = req[0];
   ctx->var_ri = req[1];
   ctx->var_cz = req[2];

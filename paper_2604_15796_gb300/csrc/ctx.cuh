@@ -27,6 +27,9 @@ struct fwi_ctx {
   // ---- device ----
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;  // created when the caller passes NULL
+  cudaStream_t stream2 = nullptr;     // second chain of the Krylov iteration graph
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool overlap = true;                // iterate large batches as two chains
   int device = 0, n_sm = 0;
   // workspace (field precision unless noted)
   void* ghat = nullptr;             // [n_freq][lz][ly][lx], scaled k^2/(lx ly lz)
@@ -65,10 +68,10 @@ struct fwi_ctx {
   double* h_red = nullptr;          // pinned host mirror
   int red_n = 0;
   bool fields_valid = false;
-  // graphs keyed by (solution pointer, batch start, batch size), with the
-  // number of kernel nodes each replay launches
+  // graphs keyed by (solution pointer, batch start, batch size, chains),
+  // with the number of kernel nodes each replay launches
   struct GraphRec { cudaGraphExec_t exec; long long nodes; };
-  std::map<std::tuple<const void*, int, int>, GraphRec> graphs;
+  std::map<std::tuple<const void*, int, int, int>, GraphRec> graphs;
   // tile-shape variants of the operator passes (autotuned at creation)
   int var_rf = 0, var_ri = 0, var_cz = 0, var_cy = 0;
   int tuned = 0;

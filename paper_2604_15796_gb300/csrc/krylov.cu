@@ -228,41 +228,61 @@ inline int blocks_for(long long n, int threads, int cap) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// Argument bundles for one batch.
+// Argument bundles for one batch, or for one half of a batch: the views
+// of the per-RHS state (Krylov vectors, planes, scalars, partial sums,
+// active list) start at slot `off` of the context's batch buffers, the
+// half's active count lives in n_active[half], and its work goes to
+// stream `st`.
 template <typename T> struct Batch {
   fwi_ctx* c;
   int rhs0, nb;
   cplx<T>* X;
+  cudaStream_t st;
+  Scal* scal;
+  double2* partial;
+  int* active;
+  int* n_active;
   RowFwdArgs<T> rf;
   RowInvArgs<T> ri;
   ColArgs<T> cz, cy_fwd, cy_inv;
 };
 
-template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb) {
+template <typename T>
+Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int half = 0,
+                    cudaStream_t st = nullptr) {
   Batch<T> b{};
   b.c = c; b.rhs0 = rhs0; b.nb = nb; b.X = X;
-  cplx<T>* R = (cplx<T>*)c->kv[0];
-  cplx<T>* RH = (cplx<T>*)c->kv[1];
-  cplx<T>* P = (cplx<T>*)c->kv[2];
-  cplx<T>* V = (cplx<T>*)c->kv[3];
-  cplx<T>* Tt = (cplx<T>*)c->kv[4];
+  b.st = st ? st : c->stream;
+  b.scal = c->scal + off;
+  b.partial = c->partial + (long long)off * NSLOT * c->rows;
+  b.active = c->active + off;
+  b.n_active = c->n_active + half;
+  const long long vo = (long long)off * c->N;
+  cplx<T>* R = (cplx<T>*)c->kv[0] + vo;
+  cplx<T>* RH = (cplx<T>*)c->kv[1] + vo;
+  cplx<T>* P = (cplx<T>*)c->kv[2] + vo;
+  cplx<T>* V = (cplx<T>*)c->kv[3] + vo;
+  cplx<T>* Tt = (cplx<T>*)c->kv[4] + vo;
+  cplx<T>* plane1 = (cplx<T>*)c->plane1 + (long long)off * c->rows * c->lx;
+  cplx<T>* plane2 = c->plane2 ? (cplx<T>*)c->plane2 + (long long)off * c->nz * c->ly * c->lx
+                              : nullptr;
   RowFwdArgs<T>& r = b.rf;
   r.m = (const cplx<T>*)c->mF; r.use_m = 1;
   r.X = X; r.R = R; r.RH = RH; r.P = P; r.V = V; r.Tt = Tt;
-  r.plane = (cplx<T>*)c->plane1; r.tw = (const cplx<T>*)c->tw_x;
-  r.active = c->active; r.n_active = c->n_active; r.nb = nb;
-  r.scal = c->scal; r.partial = c->partial;
+  r.plane = plane1; r.tw = (const cplx<T>*)c->tw_x;
+  r.active = b.active; r.n_active = b.n_active; r.nb = nb;
+  r.scal = b.scal; r.partial = b.partial;
   r.nx = c->nx; r.rows = c->rows; r.N = c->N;
   {
     const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_rf);
     r.ntiles = (c->rows + lpc - 1) / lpc;
   }
   RowInvArgs<T>& q = b.ri;
-  q.plane = (const cplx<T>*)c->plane1; q.m = (const cplx<T>*)c->mF;
+  q.plane = plane1; q.m = (const cplx<T>*)c->mF;
   q.X = X; q.R = R; q.RH = RH; q.P = P; q.V = V; q.Tt = Tt;
   q.tw = (const cplx<T>*)c->tw_x;
-  q.active = c->active; q.n_active = c->n_active; q.nb = nb;
-  q.partial = c->partial; q.nx = c->nx; q.rows = c->rows; q.N = c->N;
+  q.active = b.active; q.n_active = b.n_active; q.nb = nb;
+  q.partial = b.partial; q.nx = c->nx; q.rows = c->rows; q.N = c->N;
   {
     const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_ri);
     q.ntiles = (c->rows + lpc - 1) / lpc;
@@ -270,12 +290,12 @@ template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int 
   const long long lyx = (long long)c->ly * c->lx;
   if (c->dim == 2) {
     ColArgs<T>& z = b.cz;
-    z.mode = C_CONV; z.in = (const cplx<T>*)c->plane1; z.out = (cplx<T>*)c->plane1;
+    z.mode = C_CONV; z.in = plane1; z.out = plane1;
     z.in_rhs_stride = z.out_rhs_stride = (long long)c->rows * c->lx;
     z.line_stride = c->lx; z.ncols = c->lx; z.nplanes = 1;
   } else {
     ColArgs<T>& y = b.cy_fwd;
-    y.mode = C_FWD; y.in = (const cplx<T>*)c->plane1; y.out = (cplx<T>*)c->plane2;
+    y.mode = C_FWD; y.in = plane1; y.out = plane2;
     y.in_rhs_stride = (long long)c->rows * c->lx;
     y.out_rhs_stride = (long long)c->nz * lyx;
     y.in_plane_stride = (long long)c->ny * c->lx; y.out_plane_stride = lyx;
@@ -283,16 +303,16 @@ template <typename T> Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int 
     y.tw = (const cplx<T>*)c->tw_y;
     ColArgs<T>& w = b.cy_inv;
     w = y;
-    w.mode = C_INV; w.in = (const cplx<T>*)c->plane2; w.out = (cplx<T>*)c->plane1;
+    w.mode = C_INV; w.in = plane2; w.out = plane1;
     w.in_rhs_stride = y.out_rhs_stride; w.out_rhs_stride = y.in_rhs_stride;
     w.in_plane_stride = lyx; w.out_plane_stride = (long long)c->ny * c->lx;
     ColArgs<T>& z = b.cz;
-    z.mode = C_CONV; z.in = (const cplx<T>*)c->plane2; z.out = (cplx<T>*)c->plane2;
+    z.mode = C_CONV; z.in = plane2; z.out = plane2;
     z.in_rhs_stride = z.out_rhs_stride = (long long)c->nz * lyx;
     z.line_stride = lyx; z.ncols = (int)lyx; z.nplanes = 1;
   }
   for (ColArgs<T>* a : {&b.cz, &b.cy_fwd, &b.cy_inv}) {
-    a->active = c->active; a->n_active = c->n_active; a->nb = nb;
+    a->active = b.active; a->n_active = b.n_active; a->nb = nb;
     a->rhs0 = rhs0; a->n_elem = c->n_elem; a->freq_fixed = -1;
   }
   b.cz.tw = (const cplx<T>*)c->tw_z;
@@ -350,7 +370,7 @@ template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list, doub
   if (c->dim == 2) {
     Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c),
            units * pass_flops<T>(c, KC_COL_CONV));
-    return Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
+    return Lsop<T>::col(c->lz, z, b.st, c->var_cz);
   }
   ColArgs<T> y = b.cy_fwd, w = b.cy_inv;
   if (!use_list) { y.active = nullptr; w.active = nullptr; }
@@ -358,17 +378,17 @@ template <typename T> cudaError_t columns(const Batch<T>& b, bool use_list, doub
   {
     Prof p(c, KC_COL_FWD, units * pass_bytes<T>(c, KC_COL_FWD),
            units * pass_flops<T>(c, KC_COL_FWD));
-    e = Lsop<T>::col(c->ly, y, c->stream, c->var_cy);
+    e = Lsop<T>::col(c->ly, y, b.st, c->var_cy);
   }
   if (e == cudaSuccess) {
     Prof p(c, KC_COL_CONV, units * pass_bytes<T>(c, KC_COL_CONV) + ghat_bytes<T>(c),
            units * pass_flops<T>(c, KC_COL_CONV));
-    e = Lsop<T>::col(c->lz, z, c->stream, c->var_cz);
+    e = Lsop<T>::col(c->lz, z, b.st, c->var_cz);
   }
   if (e == cudaSuccess) {
     Prof p(c, KC_COL_INV, units * pass_bytes<T>(c, KC_COL_INV),
            units * pass_flops<T>(c, KC_COL_INV));
-    e = Lsop<T>::col(c->ly, w, c->stream, c->var_cy);
+    e = Lsop<T>::col(c->ly, w, b.st, c->var_cy);
   }
   return e;
 }
@@ -382,7 +402,7 @@ template <typename T> cudaError_t row_fwd(const Batch<T>& b, int mode, bool use_
   const int k = mode == RF_INIT ? KC_ROW_FWD_INIT : mode == RF_ITER ? KC_ROW_FWD_ITER
               : mode == RF_S ? KC_ROW_FWD_S : KC_ROW_FWD_PLAIN;
   Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
-  return Lsop<T>::row_fwd(b.c->lx, r, b.c->stream, b.c->var_rf);
+  return Lsop<T>::row_fwd(b.c->lx, r, b.st, b.c->var_rf);
 }
 
 template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_list,
@@ -394,13 +414,13 @@ template <typename T> cudaError_t row_inv(const Batch<T>& b, int mode, bool use_
   if (!use_list) q.active = nullptr;
   const int k = mode == RI_V ? KC_ROW_INV_V : mode == RI_T ? KC_ROW_INV_T : KC_ROW_INV_OTHER;
   Prof p(b.c, k, units * pass_bytes<T>(b.c, k));
-  return Lsop<T>::row_inv(b.c->lx, q, b.c->stream, b.c->var_ri);
+  return Lsop<T>::row_inv(b.c->lx, q, b.st, b.c->var_ri);
 }
 
 // Host copy of the active count (profiling mode only: synchronises).
-inline int read_active(fwi_ctx* c) {
-  if (cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int), cudaMemcpyDeviceToHost,
-                      c->stream) != cudaSuccess)
+inline int read_active(fwi_ctx* c, const int* n_active = nullptr) {
+  if (cudaMemcpyAsync(c->h_n_active, n_active ? n_active : c->n_active, sizeof(int),
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
     return 0;
   cudaStreamSynchronize(c->stream);
   return *c->h_n_active;
@@ -409,15 +429,19 @@ inline int read_active(fwi_ctx* c) {
 // One BiCGSTAB iteration body (from the column pass of the first
 // operator application to the fused update of the next iteration).
 // `units`: active right-hand sides (byte accounting in profiling mode).
-template <typename T> cudaError_t iteration(const Batch<T>& b, double units) {
+// `after_col`: if given, recorded on the batch's stream after the first
+// column pass (used to start a second chain one pass behind).
+template <typename T>
+cudaError_t iteration(const Batch<T>& b, double units, cudaEvent_t after_col = nullptr) {
   fwi_ctx* c = b.c;
   const int wb = blocks_for((long long)b.nb * 32, 256, 1 << 30);
   const double tol2 = c->tol * c->tol;
   cudaError_t e = columns(b, true, units);
+  if (e == cudaSuccess && after_col) e = cudaEventRecord(after_col, b.st);
   if (e == cudaSuccess) e = row_inv(b, RI_V, true, units);
   if (e == cudaSuccess) {
     Prof p(c, KC_KRYLOV_SCALAR);
-    s1_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, c->active, c->n_active);
+    s1_kernel<<<wb, 256, 0, b.st>>>(b.scal, b.partial, c->rows, b.active, b.n_active);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = row_fwd(b, RF_S, true, units);
@@ -425,23 +449,26 @@ template <typename T> cudaError_t iteration(const Batch<T>& b, double units) {
   if (e == cudaSuccess) e = row_inv(b, RI_T, true, units);
   if (e == cudaSuccess) {
     Prof p(c, KC_KRYLOV_SCALAR);
-    s2_kernel<<<wb, 256, 0, c->stream>>>(c->scal, c->partial, c->rows, c->active,
-                                        c->n_active, tol2, c->max_it);
+    s2_kernel<<<wb, 256, 0, b.st>>>(b.scal, b.partial, c->rows, b.active, b.n_active, tol2,
+                                   c->max_it);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
     Prof p(c, KC_KRYLOV_SCALAR);
-    compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, b.nb, c->active, c->n_active);
+    compact_kernel<<<1, 1024, 0, b.st>>>(b.scal, b.nb, b.active, b.n_active);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    const double u2 = (c->profiling && !c->capturing) ? (double)read_active(c) : units;
+    const double u2 =
+        (c->profiling && !c->capturing) ? (double)read_active(c, b.n_active) : units;
     e = row_fwd(b, RF_ITER, true, u2);
   }
   return e;
 }
 
 constexpr int kGraphIters = 4;
+// Smallest half-batch for which the iterations run as two chains.
+constexpr int kMinHalf = 16;
 
 template <typename T>
 fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, bool warm,
@@ -449,7 +476,20 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
   Batch<T> b = make_batch<T>(c, X, rhs0, nb);
   const double tol2 = c->tol * c->tol;
   const int wb = blocks_for((long long)nb * 32, 256, 1 << 30);
-  // ---- initial residual and first search direction ----
+  // With a large enough batch the iterations run as two independent halves
+  // on two streams of one graph, so that each chain's passes can start on
+  // SMs the other chain's passes leave idle.  The halves share no
+  // data, so every right-hand side follows exactly the same arithmetic as
+  // in one chain.  Profiling mode times each launch and keeps one chain.
+  const bool two = c->overlap && !c->profiling && c->stream2 != nullptr && nb >= 2 * kMinHalf;
+  const int h0 = two ? nb / 2 : nb;
+  const int nchains = two ? 2 : 1;
+  Batch<T> hb[2] = {b, b};
+  if (two) {
+    hb[0] = make_batch<T>(c, X, rhs0, h0, 0, 0);
+    hb[1] = make_batch<T>(c, X + (long long)h0 * c->N, rhs0 + h0, nb - h0, h0, 1);
+  }
+  // ---- initial residual and first search direction (whole batch) ----
   if (!warm) {
     FWI_CUDA(c, row_fwd(b, RF_INIT, false, nb, bvec, conj_b));
     Prof p(c, KC_KRYLOV_SCALAR);
@@ -463,13 +503,17 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
   }
   FWI_CUDA(c, cudaGetLastError());
   {
-    Prof p(c, KC_KRYLOV_SCALAR);
-    compact_kernel<<<1, 1024, 0, c->stream>>>(c->scal, nb, c->active, c->n_active);
+    Prof p(c, KC_KRYLOV_SCALAR, 0.0, 0.0, nchains);
+    for (int k = 0; k < nchains; ++k)
+      compact_kernel<<<1, 1024, 0, c->stream>>>(hb[k].scal, hb[k].nb, hb[k].active,
+                                                hb[k].n_active);
   }
   FWI_CUDA(c, cudaGetLastError());
   if (warm) {
-    const double u = c->profiling ? (double)read_active(c) : nb;
-    FWI_CUDA(c, row_fwd(b, RF_START, true, u));
+    for (int k = 0; k < nchains; ++k) {
+      const double u = c->profiling ? (double)read_active(c, hb[k].n_active) : hb[k].nb;
+      FWI_CUDA(c, row_fwd(hb[k], RF_START, true, u));
+    }
   }
   const int max_replays = (c->max_it + kGraphIters - 1) / kGraphIters + 1;
   if (c->profiling) {
@@ -482,8 +526,8 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
       prof_flush(c);
     }
   } else {
-    // ---- iterations: graph of kGraphIters bodies, replayed ----
-    auto key = std::make_tuple((const void*)X, rhs0, nb);
+    // ---- iterations: graph of kGraphIters bodies (per chain), replayed ----
+    auto key = std::make_tuple((const void*)X, rhs0, nb, nchains);
     fwi_ctx::GraphRec rec{nullptr, 0};
     auto it = c->graphs.find(key);
     if (it != c->graphs.end()) {
@@ -494,10 +538,30 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
       c->capturing = true;
       c->capture_nodes = 0;
       cudaError_t e = cudaSuccess;
-      for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = iteration(b, nb);
+      if (two) {
+        // both chains launch full persistent grids: a pass of one chain fills
+        // the SMs that the other chain's pass leaves idle in its tail
+        Batch<T> b0 = hb[0], b1 = hb[1];
+        b1.st = c->stream2;
+        // chain B starts when chain A's first column pass is done, so that
+        // the chains run one pass apart and their passes interleave
+        e = cudaEventRecord(c->ev_fork, c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0);
+        for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) {
+          e = iteration(b0, b0.nb);
+          if (e == cudaSuccess) e = iteration(b1, b1.nb);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->stream2);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+      } else {
+        for (int k = 0; k < kGraphIters && e == cudaSuccess; ++k) e = iteration(b, nb);
+      }
       c->capturing = false;
       cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
-      if (e != cudaSuccess) return cuda_fail(c, e, "capturing the Krylov iteration");
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(c, e, "capturing the Krylov iteration");
+      }
       FWI_CUDA(c, e2);
       e = cudaGraphInstantiate(&rec.exec, g, 0);
       cudaGraphDestroy(g);
@@ -506,10 +570,12 @@ fwi_status solve_batch(fwi_ctx* c, const cplx<T>* bvec, int conj_b, cplx<T>* X, 
       c->graphs[key] = rec;
     }
     for (int rep = 0; rep < max_replays; ++rep) {
-      FWI_CUDA(c, cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int),
+      FWI_CUDA(c, cudaMemcpyAsync(c->h_n_active, c->n_active, sizeof(int) * nchains,
                                   cudaMemcpyDeviceToHost, c->stream));
       FWI_CUDA(c, cudaStreamSynchronize(c->stream));
-      if (*c->h_n_active == 0) break;
+      int act = 0;
+      for (int k = 0; k < nchains; ++k) act += c->h_n_active[k];
+      if (act == 0) break;
       if (c->cancel.load()) return fail(c, FWI_ERR_CANCELLED, "solve cancelled");
       FWI_CUDA(c, cudaGraphLaunch(rec.exec, c->stream));
       c->launches += rec.nodes;

@@ -62,7 +62,7 @@ class fwi_stats(Structure):
 class fwi_tuning(Structure):
     _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
                 ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
-                ("jac_tensor_cores", c_int)]
+                ("jac_tensor_cores", c_int), ("overlap_halves", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -342,19 +342,29 @@ class Context:
         return {"row_fwd": t.row_fwd_variant, "row_inv": t.row_inv_variant,
                 "col": t.col_variant, "col_y": t.col_y_variant, "tuned": t.tuned,
                 "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)],
-                "jac_tensor_cores": t.jac_tensor_cores}
+                "jac_tensor_cores": t.jac_tensor_cores, "overlap_halves": t.overlap_halves}
 
     def set_tuning(self, row_fwd=None, row_inv=None, col=None, col_y=None,
-                   jac_tensor_cores=None):
+                   jac_tensor_cores=None, overlap_halves=None):
         """Force tile variants (0 when not given) and, optionally, switch the
-        tensor-core pixel contractions on (1) or off (0); None keeps the
-        current setting."""
+        tensor-core pixel contractions or the two-chain iteration on (1) or
+        off (0); None keeps the current setting."""
         t = fwi_tuning()
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.row_fwd_variant, t.row_inv_variant, t.col_variant, t.col_y_variant = (
             row_fwd or 0, row_inv or 0, col or 0, col_y or 0)
         if jac_tensor_cores is not None:
             t.jac_tensor_cores = int(jac_tensor_cores)
+        if overlap_halves is not None:
+            t.overlap_halves = int(overlap_halves)
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_overlap(self, on):
+        """Iterate large batches as two chains (True) or one (False), keeping
+        the tile variants."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.overlap_halves = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def set_jac_tensor_cores(self, on):
