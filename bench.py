@@ -521,6 +521,7 @@ def run_serving(args):
     srv = libfwi.Server(max_active=args.max_active)
     # capacity on a burst of 4 requests
     burst = [build(sp) for sp in specs[:4]]
+    print("serving: burst requests built", file=sys.stderr, flush=True)
     t0 = time.perf_counter()
     ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, s0, d, **prm)
            for w, s0, d, prm in burst]
@@ -532,6 +533,7 @@ def run_serving(args):
     rate = 0.8 * cap
     rng = np.random.default_rng(77)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.requests))
+    print(f"serving: burst capacity {cap:.3f} req/s", file=sys.stderr, flush=True)
     work = [build(sp) for sp in specs[4:4 + args.requests]]
     results = [None] * len(work)
     lock = threading.Lock()
@@ -543,6 +545,8 @@ def run_serving(args):
         r = dict(r, grid="x".join(map(str, reversed(w.shape))), rhs=int(w.n_rhs))
         with lock:
             results[k] = r
+        print(f"serving: request {k} {r['grid']} rhs={r['rhs']} status={r['status']} "
+              f"latency {r['latency_ms'] / 1e3:.1f} s", file=sys.stderr, flush=True)
 
     threads = []
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
@@ -568,7 +572,7 @@ def run_serving(args):
             "config": {"workload": f"serving stream: {len(work)} reconstruction requests, "
                                    "Poisson arrivals at 80% of burst capacity, grids "
                                    "{128^2,256^2,384^2,512^2,96^3}, 64-192 elements, 2-12 "
-                                   "frequencies in 0.3-5 MHz, 5 ADMM-TV iterations each",
+                                   "frequencies in 0.3-min(5 MHz, c0/(3.85 h)), 5 ADMM-TV iterations each",
                        "max_active": args.max_active, "arrival_rate_hz": rate,
                        "burst_capacity_req_per_s": cap},
             "latency_ms": {"p50": float(np.percentile(lat, 50)),
@@ -597,7 +601,7 @@ def main():
                     help="iterate each batch as one chain (no two-stream overlap)")
     ap.add_argument("--cuda-core-jacobian", action="store_true",
                     help="run the pixel contractions on CUDA cores instead of tensor cores")
-    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--check-samples", type=int, default=2)
     ap.add_argument("--ref-step-s", type=float, default=2.0)

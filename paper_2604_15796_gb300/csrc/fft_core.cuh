@@ -229,6 +229,50 @@ template <int R, bool INV, typename T> struct Dft {
   }
 };
 
+// R-point DFT whose inputs x[R/2 .. R) are zero (a zero-padded half):
+// X[2k] = DFT_{R/2}(x)[k], X[2k+1] = DFT_{R/2}(w_R^n x[n])[k].
+template <int R, bool INV, typename T> struct DftHalfIn {
+  static_assert(R % 2 == 0, "even size");
+  static FWI_HD void run(cplx<T>* x) {
+    constexpr int H = R / 2;
+    cplx<T> a[H], b[H];
+    SFor<H>::run([&](auto nc) {
+      constexpr int n = decltype(nc)::value;
+      a[n] = x[n];
+      b[n] = twiddle_ct<n, R, INV>(x[n]);
+    });
+    Dft<H, INV, T>::run(a);
+    Dft<H, INV, T>::run(b);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      x[2 * k] = a[k];
+      x[2 * k + 1] = b[k];
+    }
+  }
+};
+
+// R-point DFT of which only the outputs x[0 .. R/2) are wanted (a cropped
+// half): x[n] = DFT_{R/2}(X_even)[n] + w_R^n DFT_{R/2}(X_odd)[n].  The
+// entries x[R/2 .. R) are left undefined.
+template <int R, bool INV, typename T> struct DftHalfOut {
+  static_assert(R % 2 == 0, "even size");
+  static FWI_HD void run(cplx<T>* x) {
+    constexpr int H = R / 2;
+    cplx<T> a[H], b[H];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      a[k] = x[2 * k];
+      b[k] = x[2 * k + 1];
+    }
+    Dft<H, INV, T>::run(a);
+    Dft<H, INV, T>::run(b);
+    SFor<H>::run([&](auto nc) {
+      constexpr int n = decltype(nc)::value;
+      x[n] = cadd(a[n], twiddle_ct<n, R, INV>(b[n]));
+    });
+  }
+};
+
 // ---------------------------------------------------------------------------
 // Line plan: L = R1 * R2 handled by TL threads.  Thread t owns columns
 // n2 = t + i*TL (i < C1) in phases A/D and rows k1 = t + i*TL (i < C3) in
@@ -342,28 +386,55 @@ template <typename V> __device__ __forceinline__ V shfl_pair(V a) {
   return o;
 }
 
+// Twiddle applied only on lane h = 1 of a pair, without selects:
+// z * (h w + (1 - h)) with w = w_R^J (conjugated for INV) and hf = h,
+// hc = 1 - h exactly 0 or 1, so lane 0 gets z and lane 1 gets z w exactly
+// as the plain product.
+template <int J, int R, bool INV, typename V, typename S>
+__device__ __forceinline__ V lane_twiddle(V z, S hf, S hc) {
+  constexpr int q = tw_quarter(J, R);
+  if constexpr (q == 0) {
+    return z;
+  } else {
+    // exact quarter turns; otherwise the compile-time cosine / sine
+    constexpr double wr = q == 2 ? -1.0 : (q == 1 || q == 3) ? 0.0 : tw_re(J, R);
+    constexpr double wf = q == 1 ? -1.0 : q == 3 ? 1.0 : q == 2 ? 0.0 : tw_im(J, R);
+    constexpr double wi = INV ? -wf : wf;
+    const S a = hf * S(wr) + hc;  // h wr + (1 - h)
+    const S b = hf * S(wi);       // h wi
+    V o;
+    o.x = z.x * a - z.y * b;
+    o.y = z.x * b + z.y * a;
+    return o;
+  }
+}
+
+// Lane h = 0 holds E, lane 1 holds O (the DFT_Q of the even / odd samples):
+// lane 1 sends w^k O, lane 0 sends E, and each lane forms
+// (1 - 2h) v + received, i.e. E + w^k O on lane 0 and E - w^k O on lane 1.
 template <int Q, bool INV, typename T>
 __device__ __forceinline__ void split_dft(cplx<T>* u, int h) {
   Dft<Q, INV, T>::run(u);
+  const T hf = T(h), hc = T(1 - h), sg = T(1 - 2 * h);
   SFor<Q>::run([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    const cplx<T> o = shfl_pair(u[k]);
-    const cplx<T> u0 = h ? o : u[k];
-    const cplx<T> u1 = twiddle_ct<k, 2 * Q, INV>(h ? u[k] : o);
-    u[k] = h ? csub(u0, u1) : cadd(u0, u1);
+    const cplx<T> v = lane_twiddle<k, 2 * Q, INV>(u[k], hf, hc);
+    const cplx<T> o = shfl_pair(v);
+    u[k] = mk<T>(sg * v.x + o.x, sg * v.y + o.y);
   });
 }
 
+// Lane 0 holds X[k], lane 1 holds X[k + Q]: lane 0 forms X[k] + X[k + Q],
+// lane 1 (X[k] - X[k + Q]) w^k, then each lane's inverse DFT_Q.
 template <int Q, bool INV, typename T>
 __device__ __forceinline__ void split_idft(cplx<T>* u, int h) {
+  const T hf = T(h), hc = T(1 - h), sg = T(1 - 2 * h);
   SFor<Q>::run([&](auto kc) {
     constexpr int k = decltype(kc)::value;
-    const cplx<T> o = shfl_pair(u[k]);
-    const cplx<T> xa = h ? o : u[k];  // X[k]
-    const cplx<T> xb = h ? u[k] : o;  // X[k + Q]
-    cplx<T> z = h ? csub(xa, xb) : cadd(xa, xb);
-    if (h) z = twiddle_ct<k, 2 * Q, INV>(z);
-    u[k] = z;
+    const cplx<T> own = u[k];
+    const cplx<T> o = shfl_pair(own);
+    const cplx<T> z = mk<T>(sg * own.x + o.x, sg * own.y + o.y);
+    u[k] = lane_twiddle<k, 2 * Q, INV>(z, hf, hc);
   });
   Dft<Q, INV, T>::run(u);
 }

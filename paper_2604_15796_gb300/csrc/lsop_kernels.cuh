@@ -203,13 +203,16 @@ __device__ __forceinline__ bool slotB(int t, int i, int kp, int& k1, int& k2) {
   }
 }
 
-template <class P, int GP, typename T>
+// HALF_IN: the line's samples n1 >= R1/2 are zero (zero-padded rows and
+// columns of the doubled lattice), so single-thread first DFTs skip them.
+template <class P, int GP, typename T, bool HALF_IN = false>
 __device__ __forceinline__ void ph_A(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                                      const cplx<T>* tw) {
   if constexpr (PlanTraits<P>::split) {
     int n2, s;
     decode<P::S1, GP>(t, n2, s);
-    if constexpr (P::S1 == 1) Dft<P::R1, false, T>::run(v);
+    if constexpr (P::S1 == 1 && HALF_IN) DftHalfIn<P::R1, false, T>::run(v);
+    else if constexpr (P::S1 == 1) Dft<P::R1, false, T>::run(v);
     else split_dft<P::Q1, false, T>(v, s);
 #pragma unroll
     for (int kp = 0; kp < P::Q1; ++kp) {
@@ -270,7 +273,8 @@ __device__ __forceinline__ void ph_D(int t, cplx<T>* v, const cplx<T>* sm, int s
       const int k1 = (P::S1 == 1) ? kp : kp + P::Q1 * s;
       v[kp] = sm[(n2 * (P::R1 + pad) + k1) * sj];
     }
-    if constexpr (P::S1 == 1) Dft<P::R1, true, T>::run(v);
+    // every caller keeps only the samples n1 < R1/2 (cropped output)
+    if constexpr (P::S1 == 1) DftHalfOut<P::R1, true, T>::run(v);
     else split_idft<P::Q1, true, T>(v, s);
   } else {
     phaseD_load<P, T>(t, v, sm, sj, pad);
@@ -383,7 +387,8 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
       }
     }
     __syncthreads();  // shared memory of the previous item fully consumed
-    if (valid) ph_A<P, GP, T>(t, v, sml, 1, 1, a.tw);
+    // (the half-input DFT measured slower in this pass than the full one)
+    if (valid) ph_A<P, GP, T, false>(t, v, sml, 1, 1, a.tw);
     __syncthreads();
     if (valid) {
       ph_B<P, GP, T>(t, v, sml, 1, 1);
@@ -690,7 +695,8 @@ col_kernel(const ColArgs<T> a) {
     }
     __syncthreads();
     if (a.mode != C_INV) {
-      ph_A<P, GP, T>(t, v, smc, TC, 0, a.tw);
+      if (a.full) ph_A<P, GP, T, false>(t, v, smc, TC, 0, a.tw);
+      else ph_A<P, GP, T, true>(t, v, smc, TC, 0, a.tw);
       __syncthreads();
       ph_B<P, GP, T>(t, v, smc, TC, 0);
       if (a.mode == C_FWD) {

@@ -194,8 +194,10 @@ def complex_normal(shape, seed):
 def serving_requests(n_req=256, seed=1004, rate_hz=1.0):
     """Request stream: Poisson arrival times and, per request, a grid drawn
     from {128^2, 256^2, 384^2, 512^2, 96^3}, N_E ~ U{64..192}, N_F ~ U{2..12}
-    frequencies in [0.3, 5] MHz.  The pixel size keeps the aperture inside
-    the grid width."""
+    frequencies in [0.3, f_max] MHz.  The pixel size keeps the aperture
+    inside the grid width; f_max = min(5 MHz, c0 / (3.85 h)) keeps at least
+    3.85 pixels per wavelength (the coarsest sampling of the paper's own
+    configurations; coarser grids do not resolve the wave field)."""
     rng = np.random.default_rng(seed)
     grids = [(128, 128), (256, 256), (384, 384), (512, 512), (96, 96, 96)]
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=n_req))
@@ -204,10 +206,11 @@ def serving_requests(n_req=256, seed=1004, rate_hz=1.0):
         shape = grids[int(rng.integers(0, len(grids)))]
         n_elem = int(rng.integers(64, 193))
         n_freq = int(rng.integers(2, 13))
-        freqs = np.sort(rng.uniform(0.3e6, 5.0e6, size=n_freq))
         pitch = 0.2e-3
         width_needed = n_elem * pitch
         h = max(0.05e-3, width_needed / shape[-1])
+        f_max = min(5.0e6, 1540.0 / (3.85 * h))
+        freqs = np.sort(rng.uniform(0.3e6, f_max, size=n_freq))
         reqs.append(dict(arrival=float(t[i]), shape=shape, h=h,
                          n_elem=n_elem, pitch=pitch, freqs=freqs,
                          seed=seed * 1000 + i))
