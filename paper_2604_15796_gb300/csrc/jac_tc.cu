@@ -134,6 +134,7 @@ struct ContractArgs {
   int* err;
   long long N, chunk;
   int NE, n_freq;
+  int sub_ks;       // k-steps per accumulation sub-chunk
 };
 
 template <bool SHARED>
@@ -179,6 +180,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
     const int r = tid;
     const int e = eb * ROWS + r, j = jb * ROWS + r;
     const bool ev = e < p.NE, jv = j < p.NE;
+    // this thread's row of the CTA's partial; TMEM lane r = row e, columns
+    // j (Re) and 128 + j (Im)
+    float2* out = p.part + (((long long)s * p.n_freq + l) * p.NE + (ev ? e : 0)) * p.NE;
+    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
     const float2* xrow = Xl + (long long)(ev ? e : 0) * p.N;
     const float2* qrow = Ql + (long long)(jv ? j : 0) * p.N;
     auto issue = [&](int g) {
@@ -253,29 +258,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
       }
       fence_proxy_async();
       mbar_arrive(smem_addr(&bar_full[cs]));
+      if ((g + 1) % p.sub_ks == 0 || g == nch - 1) {
+        // end of an accumulation sub-chunk: add the accumulator into this
+        // CTA's FP32 partial (the first sub-chunk writes it), fixed order
+        const int sub = g / p.sub_ks;
+        const bool ok = mbar_wait(smem_addr(&bar_done), sub & 1, &abort_flag, p.err,
+                                  kErrWaitDone);
+        fence_after_sync();
+#pragma unroll 1
+        for (int jc = 0; jc < ROWS / 32; ++jc) {
+          uint32_t re[32], im[32];
+          tmem_ld32(lane_addr + 32 * jc, re);
+          tmem_ld32(lane_addr + ROWS + 32 * jc, im);
+          tmem_wait_ld();
+          if (ev) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int jj = jb * ROWS + 32 * jc + i;
+              if (jj < p.NE) {
+                float2 v = ok ? make_float2(__uint_as_float(re[i]), __uint_as_float(im[i]))
+                              : make_float2(0.f, 0.f);
+                if (sub > 0) {
+                  const float2 o = out[jj];
+                  v.x += o.x;
+                  v.y += o.y;
+                }
+                out[jj] = v;
+              }
+            }
+          }
+        }
+        fence_before_sync();  // TMEM reads precede the next sub-chunk's MMAs
+      }
     }
     cp_async_wait<0>();
-    // epilogue: TMEM lane r = row e; columns j (Re) and 128 + j (Im)
-    const bool ok = mbar_wait(smem_addr(&bar_done), 0, &abort_flag, p.err, kErrWaitDone);
-    fence_after_sync();
-    float2* out = p.part + (((long long)s * p.n_freq + l) * p.NE + (ev ? e : 0)) * p.NE;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
+    if (nch == 0 && ev) {
 #pragma unroll 1
-    for (int jc = 0; jc < ROWS / 32; ++jc) {
-      uint32_t re[32], im[32];
-      tmem_ld32(lane_addr + 32 * jc, re);
-      tmem_ld32(lane_addr + ROWS + 32 * jc, im);
-      tmem_wait_ld();
-      if (ev) {
-        const bool zero = (nch == 0) || !ok;
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int jj = jb * ROWS + 32 * jc + i;
-          if (jj < p.NE)
-            out[jj] = zero ? make_float2(0.f, 0.f)
-                           : make_float2(__uint_as_float(re[i]), __uint_as_float(im[i]));
-        }
-      }
+      for (int jj = jb * ROWS; jj < jb * ROWS + ROWS && jj < p.NE; ++jj)
+        out[jj] = make_float2(0.f, 0.f);
     }
   } else {
     for (int g = 0; g < nch; ++g) {
@@ -285,13 +305,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
       fence_after_sync();
       if (lane == 0 && ok) {
         const uint32_t cb = sbase + (uint32_t)(cs * C_CONV_BYTES);
-        issue_kstep(tmem, cb, cb + 4 * PLANE, g == 0);
+        issue_kstep(tmem, cb, cb + 4 * PLANE, g % p.sub_ks == 0);
         commit(smem_addr(&bar_empty[cs]));
       }
+      if (lane == 0 && ((g + 1) % p.sub_ks == 0 || g == nch - 1))
+        commit(smem_addr(&bar_done));
       __syncwarp();
     }
-    if (lane == 0) commit(smem_addr(&bar_done));
-    __syncwarp();
   }
   fence_before_sync();
   __syncthreads();
@@ -606,7 +626,12 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   long long chunk = (c->N + split - 1) / split;
   chunk = ((chunk + KS - 1) / KS) * KS;
   split = (int)((c->N + chunk - 1) / chunk);
-  ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq};
+  // Balanced sub-chunks of at most 2048 pixels bound the FP32 accumulation
+  // chain in TMEM; the partial of a CTA collects its sub-chunks in order.
+  const long long chunk_ks = chunk / KS;
+  const long long nsub = (chunk_ks + 255) / 256;
+  const int sub_ks = (int)((chunk_ks + nsub - 1) / nsub);
+  ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq, sub_ks};
   dim3 grid(split, nbe * nbe, c->n_freq);
   const double fe = (double)c->n_freq * c->n_elem * c->N;
   {

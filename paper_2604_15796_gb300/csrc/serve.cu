@@ -98,10 +98,22 @@ void run_request(fwi_server* srv, Request& r) {
     if (fail_cuda(cudaMemcpyAsync(dobs, r.d_obs.data(), nd, cudaMemcpyHostToDevice, st))) break;
     if ((status = fwi_contrast_from_sos(ctx, (const double*)sos0, nullptr, m)) != FWI_OK) break;
     if ((status = fwi_admm_init(ctx, m, g, u)) != FWI_OK) break;
+    double iters_sum = 0.0;
+    int iters_n = 0;
     for (int k = 0; k < r.n_iter; ++k) {
       double mis = 0.0;
-      fwi_status s1 = fwi_gradient(ctx, m, dobs, grad, &mis, nullptr, nullptr, nullptr);
+      fwi_solve_info inf[2];
+      std::memset(inf, 0, sizeof(inf));
+      inf[0].n_rhs = inf[1].n_rhs = r.desc.n_elem * r.desc.n_freq;
+      fwi_status s1 = fwi_gradient(ctx, m, dobs, grad, &mis, nullptr, &inf[0], &inf[1]);
       if (s1 != FWI_OK && s1 != FWI_ERR_NOT_CONVERGED) { status = s1; break; }
+      for (const fwi_solve_info& f : inf) {
+        if (f.max_iters > res.krylov_iters_max) res.krylov_iters_max = f.max_iters;
+        iters_sum += f.max_iters;
+        iters_n += 1;
+        res.not_converged += f.n_not_converged;
+      }
+      res.krylov_iters_mean = iters_n ? iters_sum / iters_n : 0.0;
       if (k == 0) res.misfit_first = mis;
       res.misfit_last = mis;
       fwi_status s2 = fwi_admm_tv_step(ctx, m, g, u, grad, &r.admm,

@@ -78,7 +78,9 @@ class fwi_request(Structure):
 class fwi_request_result(Structure):
     _fields_ = [("status", c_int), ("queue_ms", c_double), ("run_ms", c_double),
                 ("latency_ms", c_double), ("misfit_first", c_double), ("misfit_last", c_double),
-                ("rhs_solves", ctypes.c_longlong), ("bytes", c_size_t)]
+                ("rhs_solves", ctypes.c_longlong), ("bytes", c_size_t),
+                ("krylov_iters_max", c_int), ("krylov_iters_mean", c_double),
+                ("not_converged", ctypes.c_longlong)]
 
 
 EXPORTS = {

@@ -139,7 +139,8 @@ def test_full_size_contraction_accuracy(lib):
     ctx.close()
     err = rel_l2(ja_tc, ja_cc)
     print(f"J a tensor cores vs FMA at 256^2: {err:.2e}")
-    assert err < 1e-4
+    # sub-chunks of at most 2048 pixels bound the TMEM accumulation chains
+    assert err < 3e-5
     # data = sum_n R_j(n) m_n p_e(n) (Eq. 4) on the device fields, in FP64
     f = to_np(fields).astype(np.complex128).reshape(w.n_freq, w.n_elem, -1)
     rows = inverse.receiver_rows(oracle_problem(w)).reshape(w.n_freq, w.n_elem, -1)

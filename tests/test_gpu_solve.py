@@ -226,13 +226,23 @@ def test_jacobian_products(lib):
     ctx.close()
 
 
-@pytest.mark.parametrize("shape,prec", [((32, 32), "mixed"), ((8, 8, 16), "mixed"),
-                                        ((64, 64), "fp64")])
-def test_admm_tv_step_matches_oracle(lib, shape, prec):
+@pytest.mark.parametrize("shape,prec,n_elem", [((32, 32), "mixed", 6), ((8, 8, 16), "mixed", 6),
+                                               ((64, 64), "fp64", 0), ((8, 32, 32), "mixed", 136),
+                                               ((16, 128), "mixed", 150)])
+def test_admm_tv_step_matches_oracle(lib, shape, prec, n_elem):
+    """One ADMM-TV iteration (m-step CG with J / J^H, shrink, dual update,
+    SoS) against the oracle, including 2-D and 3-D cases with more than 128
+    elements (two element tiles in the tensor-core contractions)."""
     import torch
     fp64 = prec == "fp64"
-    w = phantoms.disc_phantom() if shape == (64, 64) else \
-        small_workload(shape, n_elem=6, freqs=(1.5e6, 3e6))
+    if shape == (64, 64):
+        w = phantoms.disc_phantom()
+    elif n_elem > 128:
+        width = shape[-1] * 0.1e-3
+        w = phantoms.scaled(shape, 0.1e-3, n_elem, 0.9 * width / n_elem, np.array([1.5e6]), 17,
+                            inclusions=[1520.0, 1580.0], semi_mm=(0.3, 0.6))
+    else:
+        w = small_workload(shape, n_elem=n_elem, freqs=(1.5e6, 3e6))
     prob, m, d_obs = _gradient_case(w)
     ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs,
                       precision=lib.FWI_FP64 if fp64 else lib.FWI_MIXED,
