@@ -235,6 +235,10 @@ typedef struct fwi_request_result {
   double misfit_last;        /* misfit at the last iterate's forward solve */
   long long rhs_solves;      /* forward + adjoint BiCGSTAB solves */
   size_t bytes;              /* admitted device footprint */
+  int krylov_iters_max;      /* most BiCGSTAB iterations of any solve */
+  double krylov_iters_mean;  /* mean over the request's forward / adjoint batches
+                                of their largest iteration count */
+  long long not_converged;   /* solves that stopped at krylov_max_it */
 } fwi_request_result;
 /* hbm_budget: bytes the server may hold for admitted requests (0: 90 % of
    the free device memory at creation); max_active: worker slots (>= 1).
