@@ -357,15 +357,14 @@ template <typename T> struct Jac {
 
   // Y = scale_l * contract(X, a, Q) (c128, [l][e][j]); sym when Q == X
   // (then Y_l is complex-symmetric and only tiles eb <= jb are computed).
-  // `allow_tc`: the tensor cores may take it (J a of the m-step).  The data
-  // projection keeps the FMA kernel: its sums run over all pixels of a CTA's
-  // chunk, where the tensor core's FP32 accumulation drifts further than
-  // FMA accumulation (1e-6 vs several 1e-5 relative at 256^2).
+  // FP32 fields: tensor cores (jac_tc.cu), whose TMEM accumulation runs
+  // over sub-chunks of at most 512 pixels so that it stays within a few
+  // 1e-6 of FMA accumulation.
   static fwi_status contract(fwi_ctx* c, const cplx<T>* X, const cplx<T>* a,
-                             const cplx<T>* Q, double2* Y, bool allow_tc = false) {
+                             const cplx<T>* Q, double2* Y) {
     const long long per = (long long)c->n_freq * c->n_elem * c->n_elem;
     if constexpr (std::is_same<T, float>::value) {
-      if (allow_tc && tc_usable(c)) {
+      if (tc_usable(c)) {
         const int split = tc_contract_partials(c, X, a, Q, (float2*)c->jsplit);
         if (split < 0) return FWI_ERR_CUDA;
         Prof p(c, KC_MISC);
@@ -514,7 +513,7 @@ template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a,
   }
   FWI_CUDA(c, cudaGetLastError());
   return Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
-                          (const cplx<T>*)c->fields, y, true);
+                          (const cplx<T>*)c->fields, y);
 }
 
 fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {

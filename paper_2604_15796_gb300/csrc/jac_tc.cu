@@ -42,6 +42,9 @@ constexpr int BPLANE = BROWS * 32;
 constexpr uint32_t LBO_A = 16 * ROWS, LBO_B = 16 * BROWS, SBO = 128;
 constexpr uint32_t IDESC = tc::idesc_tf32(128, 256, false);
 constexpr int NTHREADS = 160;         // 4 producer warps + 1 MMA warp
+constexpr int C_THREADS = 288;        // contraction: + 4 accumulator-drain warps
+constexpr int C_TILE_STRIDE = 17;     // drain transpose tile: [32 rows][16 + 1] float2
+constexpr int C_TILE_BYTES = 32 * C_TILE_STRIDE * 8;
 
 // Operand planes inside a conversion stage: A = {Ar hi, Ar lo, Ai hi, Ai lo}
 // (one 128-row block each), then B hi and B lo (384 rows each).
@@ -101,6 +104,9 @@ __device__ __forceinline__ float4 lds128(uint32_t addr) {
                : "r"(addr));
   return v;
 }
+__device__ __forceinline__ void sts64(uint32_t addr, float a, float b) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
 __device__ __forceinline__ float2 lds64(uint32_t addr) {
   float2 v;
   asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
@@ -112,18 +118,19 @@ __device__ __forceinline__ float2 lds64(uint32_t addr) {
 // accumulator D[e][j] (128 x [128 Re | 128 Im]) over its pixel chunk,
 // written as FP32 partials part[s][l][e][j].
 // Raw stages: 128 rows of X (and of Q unless the two share rows) plus the
-// 8 weights a[n]; SHARED (X == Q, one element tile) keeps 10 stages in
-// flight, the general case 5, which fills the shared memory left by the
-// three conversion stages.
+// 8 weights a[n]; SHARED (X == Q, one element tile) keeps 8 stages in
+// flight, the general case 4; after them come the four drain warps'
+// transpose tiles.
 constexpr int C_CONV = 3;
 constexpr int C_RAWROW = 80;  // 8 complex (64 bytes) + 16 bytes of padding
 constexpr int C_CONV_BYTES = 4 * PLANE + 2 * BPLANE;
 template <bool SHARED> struct CRaw {
-  static constexpr int N = SHARED ? 10 : 5;
+  static constexpr int N = SHARED ? 8 : 4;
   static constexpr int X = 0, Q = ROWS * C_RAWROW;
   static constexpr int A = (SHARED ? 1 : 2) * ROWS * C_RAWROW;
   static constexpr int BYTES = A + 64;
-  static constexpr int SMEM = C_CONV * C_CONV_BYTES + N * BYTES;
+  static constexpr int TILES = C_CONV * C_CONV_BYTES + N * BYTES;
+  static constexpr int SMEM = TILES + 4 * C_TILE_BYTES;
 };
 
 struct ContractArgs {
@@ -137,14 +144,21 @@ struct ContractArgs {
   int sub_ks;       // k-steps per accumulation sub-chunk
 };
 
+// Two accumulators (TMEM columns 0-255 and 256-511) alternate between
+// sub-chunks: while the MMA warp accumulates sub-chunk s into buffer s % 2,
+// four drain warps add buffer (s - 1) % 2 into the CTA's FP32 partial.  A
+// drain warp owns the 32 TMEM lanes of its quadrant (32 rows e) and moves
+// 16 columns at a time through a shared transpose tile, so that its global
+// read-modify-write covers two 128-byte row segments per instruction.
 template <bool SHARED>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p) {
+__global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs p) {
   using namespace tc;
   using RW = CRaw<SHARED>;
   constexpr int C_RAW = RW::N, C_RAW_BYTES = RW::BYTES;
   constexpr int C_RAW_X = RW::X, C_RAW_Q = RW::Q, C_RAW_A = RW::A;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done;
+  __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done[2],
+      bar_freed[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -164,26 +178,79 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
       mbar_init(smem_addr(&bar_full[i]), 128);
       mbar_init(smem_addr(&bar_empty[i]), 1);
     }
-    mbar_init(smem_addr(&bar_done), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_addr(&bar_done[b]), 1);
+      mbar_init(smem_addr(&bar_freed[b]), 128);
+    }
     abort_flag = 0;
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 256);
+  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 512);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = tmem_base;
   const uint32_t sbase = smem_addr(smem);
   const uint32_t raw0 = sbase + C_CONV * C_CONV_BYTES;
+  const int nsub = (nch + p.sub_ks - 1) / p.sub_ks;
 
-  if (warp < 4) {
+  if (warp >= 5) {
+    const int q = warp & 3;             // TMEM lane quadrant: rows 32q .. 32q + 31
+    const uint32_t tile = sbase + RW::TILES + q * C_TILE_BYTES;
+    const int e0 = eb * ROWS + 32 * q;  // first row of the quadrant
+    float2* part = p.part + ((long long)s * p.n_freq + l) * p.NE * p.NE;
+    const int rsub = lane >> 4, csub = lane & 15;  // read-back position in a tile
+    for (int sub = 0; sub < nsub; ++sub) {
+      const int b = sub & 1;
+      const bool ok = mbar_wait(smem_addr(&bar_done[b]), (sub >> 1) & 1, &abort_flag, p.err,
+                                kErrWaitDone);
+      fence_after_sync();
+      const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + 256u * b;
+#pragma unroll 1
+      for (int cb = 0; cb < ROWS / 16; ++cb) {
+        uint32_t re[16], im[16];
+        tmem_ld16(lane_addr + 16 * cb, re);
+        tmem_ld16(lane_addr + ROWS + 16 * cb, im);
+        tmem_wait_ld();
+        // this lane's row (32q + lane), columns 16 cb .. 16 cb + 15
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+          sts64(tile + (uint32_t)((lane * C_TILE_STRIDE + k) * 8), __uint_as_float(re[k]),
+                __uint_as_float(im[k]));
+        __syncwarp();
+        const int jj = jb * ROWS + 16 * cb + csub;
+#pragma unroll 4
+        for (int ii = 0; ii < 16; ++ii) {
+          const int rr = 2 * ii + rsub;
+          const int e = e0 + rr;
+          const float2 t = lds64(tile + (uint32_t)((rr * C_TILE_STRIDE + csub) * 8));
+          if (e < p.NE && jj < p.NE) {
+            float2* dst = part + (long long)e * p.NE + jj;
+            float2 v = ok ? t : make_float2(0.f, 0.f);
+            if (sub > 0) {
+              const float2 o = *dst;
+              v.x += o.x;
+              v.y += o.y;
+            }
+            *dst = v;
+          }
+        }
+        __syncwarp();
+      }
+      fence_before_sync();  // the TMEM reads precede the buffer's next MMAs
+      mbar_arrive(smem_addr(&bar_freed[b]));
+    }
+    if (nch == 0) {
+      for (int rr = 0; rr < 32; ++rr) {
+        const int e = e0 + rr;
+        for (int jj = jb * ROWS + lane; jj < jb * ROWS + ROWS; jj += 32)
+          if (e < p.NE && jj < p.NE) part[(long long)e * p.NE + jj] = make_float2(0.f, 0.f);
+      }
+    }
+  } else if (warp < 4) {
     const int r = tid;
     const int e = eb * ROWS + r, j = jb * ROWS + r;
     const bool ev = e < p.NE, jv = j < p.NE;
-    // this thread's row of the CTA's partial; TMEM lane r = row e, columns
-    // j (Re) and 128 + j (Im)
-    float2* out = p.part + (((long long)s * p.n_freq + l) * p.NE + (ev ? e : 0)) * p.NE;
-    const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
     const float2* xrow = Xl + (long long)(ev ? e : 0) * p.N;
     const float2* qrow = Ql + (long long)(jv ? j : 0) * p.N;
     auto issue = [&](int g) {
@@ -258,58 +325,28 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
       }
       fence_proxy_async();
       mbar_arrive(smem_addr(&bar_full[cs]));
-      if ((g + 1) % p.sub_ks == 0 || g == nch - 1) {
-        // end of an accumulation sub-chunk: add the accumulator into this
-        // CTA's FP32 partial (the first sub-chunk writes it), fixed order
-        const int sub = g / p.sub_ks;
-        const bool ok = mbar_wait(smem_addr(&bar_done), sub & 1, &abort_flag, p.err,
-                                  kErrWaitDone);
-        fence_after_sync();
-#pragma unroll 1
-        for (int jc = 0; jc < ROWS / 32; ++jc) {
-          uint32_t re[32], im[32];
-          tmem_ld32(lane_addr + 32 * jc, re);
-          tmem_ld32(lane_addr + ROWS + 32 * jc, im);
-          tmem_wait_ld();
-          if (ev) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int jj = jb * ROWS + 32 * jc + i;
-              if (jj < p.NE) {
-                float2 v = ok ? make_float2(__uint_as_float(re[i]), __uint_as_float(im[i]))
-                              : make_float2(0.f, 0.f);
-                if (sub > 0) {
-                  const float2 o = out[jj];
-                  v.x += o.x;
-                  v.y += o.y;
-                }
-                out[jj] = v;
-              }
-            }
-          }
-        }
-        fence_before_sync();  // TMEM reads precede the next sub-chunk's MMAs
-      }
     }
     cp_async_wait<0>();
-    if (nch == 0 && ev) {
-#pragma unroll 1
-      for (int jj = jb * ROWS; jj < jb * ROWS + ROWS && jj < p.NE; ++jj)
-        out[jj] = make_float2(0.f, 0.f);
-    }
   } else {
     for (int g = 0; g < nch; ++g) {
       const int cs = g % C_CONV;
+      const int sub = g / p.sub_ks, b = sub & 1;
+      if (g % p.sub_ks == 0 && sub >= 2) {
+        // buffer b is free once sub-chunk sub - 2 has been drained
+        mbar_wait(smem_addr(&bar_freed[b]), ((sub - 2) >> 1) & 1, &abort_flag, p.err,
+                  kErrWaitEmpty);
+        fence_after_sync();
+      }
       const bool ok = mbar_wait(smem_addr(&bar_full[cs]), (g / C_CONV) & 1, &abort_flag,
                                 p.err, kErrWaitFull);
       fence_after_sync();
       if (lane == 0 && ok) {
         const uint32_t cb = sbase + (uint32_t)(cs * C_CONV_BYTES);
-        issue_kstep(tmem, cb, cb + 4 * PLANE, g % p.sub_ks == 0);
+        issue_kstep(tmem + 256u * b, cb, cb + 4 * PLANE, g % p.sub_ks == 0);
         commit(smem_addr(&bar_empty[cs]));
       }
       if (lane == 0 && ((g + 1) % p.sub_ks == 0 || g == nch - 1))
-        commit(smem_addr(&bar_done));
+        commit(smem_addr(&bar_done[b]));
       __syncwarp();
     }
   }
@@ -317,7 +354,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_contract_kernel(ContractArgs p
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
-    tmem_dealloc(tmem, 256);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -626,10 +663,11 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   long long chunk = (c->N + split - 1) / split;
   chunk = ((chunk + KS - 1) / KS) * KS;
   split = (int)((c->N + chunk - 1) / chunk);
-  // Balanced sub-chunks of at most 2048 pixels bound the FP32 accumulation
-  // chain in TMEM; the partial of a CTA collects its sub-chunks in order.
+  // Balanced sub-chunks of at most 512 pixels bound the FP32 accumulation
+  // chain in TMEM (drained by separate warps while the MMAs continue); the
+  // partial of a CTA collects its sub-chunks in order.
   const long long chunk_ks = chunk / KS;
-  const long long nsub = (chunk_ks + 255) / 256;
+  const long long nsub = (chunk_ks + 63) / 64;
   const int sub_ks = (int)((chunk_ks + nsub - 1) / nsub);
   ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq, sub_ks};
   dim3 grid(split, nbe * nbe, c->n_freq);
@@ -638,9 +676,9 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
     Prof pf(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(float2),
             8.0 * fe * c->n_elem);
     if (X == Q && nbe == 1)
-      tc_contract_kernel<true><<<grid, NTHREADS, CRaw<true>::SMEM, c->stream>>>(args);
+      tc_contract_kernel<true><<<grid, C_THREADS, CRaw<true>::SMEM, c->stream>>>(args);
     else
-      tc_contract_kernel<false><<<grid, NTHREADS, CRaw<false>::SMEM, c->stream>>>(args);
+      tc_contract_kernel<false><<<grid, C_THREADS, CRaw<false>::SMEM, c->stream>>>(args);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {

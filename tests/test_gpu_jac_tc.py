@@ -120,9 +120,9 @@ def test_gradient_with_tensor_core_mixes(lib, shape, n_elem, freqs):
 
 def test_full_size_contraction_accuracy(lib):
     """256^2 grid, 128 elements, 2 frequencies (the thyroid256 geometry):
-    J a on the tensor cores (long split-K chains, FP32 accumulation in TMEM)
-    against the FMA kernel, and the data projection (FMA) against the
-    oracle's definition evaluated on the device fields in FP64."""
+    J a on the tensor cores (FP32 accumulation in TMEM over sub-chunks of
+    at most 512 pixels) against the FMA kernel, and the data projection
+    against the definition (Eq. 4) evaluated on the device fields in FP64."""
     import torch
     w = phantoms.scaled((256, 256), 0.1e-3, 128, 0.2e-3, np.array([1.0e6, 3.0e6]), 21,
                         inclusions=[1520.0, 1580.0])
@@ -139,13 +139,12 @@ def test_full_size_contraction_accuracy(lib):
     ctx.close()
     err = rel_l2(ja_tc, ja_cc)
     print(f"J a tensor cores vs FMA at 256^2: {err:.2e}")
-    # sub-chunks of at most 2048 pixels bound the TMEM accumulation chains
-    assert err < 3e-5
+    assert err < 1e-5
     # data = sum_n R_j(n) m_n p_e(n) (Eq. 4) on the device fields, in FP64
     f = to_np(fields).astype(np.complex128).reshape(w.n_freq, w.n_elem, -1)
     rows = inverse.receiver_rows(oracle_problem(w)).reshape(w.n_freq, w.n_elem, -1)
     mm = m.reshape(1, -1)
     ref = np.stack([(f[l] * mm) @ rows[l].T for l in range(w.n_freq)])
     err_d = rel_l2(to_np(data), ref)
-    print(f"data (FMA contraction) vs FP64 on the same fields: {err_d:.2e}")
-    assert err_d < 1e-5
+    print(f"data (tensor cores) vs FP64 on the same fields: {err_d:.2e}")
+    assert err_d < 2e-5
