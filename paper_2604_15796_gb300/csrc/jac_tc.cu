@@ -17,10 +17,12 @@
 // accuracy; accumulation is FP32 in TMEM and partial sums over CTAs are
 // combined in FP64 by the callers' reduction kernels.
 //
-// Pipelines: four producer warps stream raw FP32 tiles with cp.async (three
-// stages ahead), split them into the TF32 operand planes of a shared-memory
-// stage and signal an mbarrier; one warp issues the MMAs and releases the
-// stage with tcgen05.commit.  Every wait is bounded (tc.cuh).
+// Pipelines: four producer warps stream raw FP32 tiles with cp.async
+// (several stages ahead), split them into the TF32 operand planes of a
+// shared-memory stage and signal an mbarrier; one warp issues the MMAs and
+// releases the stage with tcgen05.commit; two TMEM accumulators alternate so
+// that four more warps read one out while the MMAs fill the other.  Every
+// wait is bounded (tc.cuh).
 #include <mutex>
 #include <string>
 
@@ -41,8 +43,8 @@ constexpr int BROWS = 3 * ROWS;       // B stack [-Bi | Br | Bi]
 constexpr int BPLANE = BROWS * 32;
 constexpr uint32_t LBO_A = 16 * ROWS, LBO_B = 16 * BROWS, SBO = 128;
 constexpr uint32_t IDESC = tc::idesc_tf32(128, 256, false);
-constexpr int NTHREADS = 160;         // 4 producer warps + 1 MMA warp
-constexpr int C_THREADS = 288;        // contraction: + 4 accumulator-drain warps
+// 4 producer warps, 1 MMA warp, 4 accumulator warps (drain / epilogue)
+constexpr int C_THREADS = 288;
 constexpr int C_TILE_STRIDE = 17;     // drain transpose tile: [32 rows][16 + 1] float2
 constexpr int C_TILE_BYTES = 32 * C_TILE_STRIDE * 8;
 
@@ -359,15 +361,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
 }
 
 // ---------------------------------------------------------------------------
-// J^H: persistent CTAs over units (frequency l, element tile eb, block of
-// M_TILES x 128 pixels).  Per unit and pixel tile the accumulator holds
-// W[n][e] (128 pixels x [128 Re | 128 Im]); the epilogue forms
-// s_l sum_e conj(X[e][n]) W[e][n] into zpart[l][eb][n].
-constexpr int M_TILES = 2;
-constexpr int M_CONV = 3, M_RAW = 3;
-constexpr int M_RAW_TILE = KS * ROWS * 8;               // [8 j][128 n] complex
-constexpr int M_RAW_BYTES = M_TILES * M_RAW_TILE;
-constexpr int M_A_BYTES = M_TILES * 4 * PLANE;
+// J^H: persistent CTAs over units (frequency l, element tile eb, tile of 128
+// pixels).  Per unit the accumulator holds W[n][e] (128 pixels x [128 Re |
+// 128 Im]); two accumulators alternate between units, and four epilogue
+// warps form s_l sum_e conj(X[e][n]) W[e][n] into zpart[l][eb][n] (FUSED) or
+// write W itself while the MMAs of the next unit proceed.
+constexpr int M_CONV = 3, M_RAW = 6;
+constexpr int M_RAW_BYTES = KS * ROWS * 8;               // [8 j][128 n] complex
+constexpr int M_A_BYTES = 4 * PLANE;
 constexpr int M_B_BYTES = 2 * BPLANE;                    // one k-step of B hi + lo
 constexpr int M_CONV_BYTES = M_A_BYTES + M_B_BYTES;
 constexpr int M_SMEM = M_CONV * M_CONV_BYTES + M_RAW * M_RAW_BYTES;
@@ -387,10 +388,11 @@ struct JhArgs {
 // mix W_l[e][n] = s_l sum_j B[e][j] X'[j][n] itself is written (adjoint
 // sources conj(s_e) = k^2 dV sum_j p0_j conj(r_ej)).
 template <bool FUSED>
-__global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
+__global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar_full[M_CONV], bar_empty[M_CONV], bar_done;
+  __shared__ __align__(8) uint64_t bar_full[M_CONV], bar_empty[M_CONV], bar_done[2],
+      bar_freed[2];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -404,11 +406,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
       mbar_init(smem_addr(&bar_full[i]), 129);  // 128 producers + expect_tx
       mbar_init(smem_addr(&bar_empty[i]), 1);
     }
-    mbar_init(smem_addr(&bar_done), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_addr(&bar_done[b]), 1);
+      mbar_init(smem_addr(&bar_freed[b]), 128);
+    }
     abort_flag = 0;
     mbar_init_fence();
   }
-  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 256 * M_TILES);
+  if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 512);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
   const uint32_t sbase = smem_addr(smem);
   const uint32_t raw0 = sbase + M_CONV * M_CONV_BYTES;
 
-  // unit index -> (l, eb, pixel block)
+  // unit index -> (l, eb, pixel tile)
   auto unit_of = [&](int k, int& l, int& eb, int& pb) {
     const int u = (int)blockIdx.x + k * (int)gridDim.x;
     pb = u % p.npb;
@@ -424,7 +429,60 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
     l = u / (p.npb * p.nbe);
   };
 
-  if (warp < 4) {
+  if (warp >= 5) {
+    // epilogue warps: TMEM lane = pixel 32 q + lane of the unit's tile
+    const int q = warp & 3;
+    const int r = 32 * q + lane;
+    for (int k = 0; k < my_units; ++k) {
+      int l, eb, pb;
+      unit_of(k, l, eb, pb);
+      const int b = k & 1;
+      const bool ok = mbar_wait(smem_addr(&bar_done[b]), (k >> 1) & 1, &abort_flag, p.err,
+                                kErrWaitDone);
+      fence_after_sync();
+      const float2* Xl = p.X + (long long)l * p.NE * p.N;
+      const float sc = (float)p.scale[l];
+      const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + 256u * b;
+      const long long n = (long long)pb * ROWS + r;
+      const bool nv = n < p.N;
+      float zx = 0.f, zy = 0.f;
+#pragma unroll 1
+      for (int ec = 0; ec < ROWS / 32; ++ec) {
+        uint32_t wr[32], wi[32];
+        tmem_ld32(lane_addr + (uint32_t)(32 * ec), wr);
+        tmem_ld32(lane_addr + (uint32_t)(ROWS + 32 * ec), wi);
+        tmem_wait_ld();
+        if constexpr (FUSED) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int e = eb * ROWS + 32 * ec + i;
+            if (nv && e < p.NE) {
+              const float2 x = __ldg(Xl + (long long)e * p.N + n);
+              const float a = __uint_as_float(wr[i]), bb = __uint_as_float(wi[i]);
+              zx += x.x * a + x.y * bb;
+              zy += x.x * bb - x.y * a;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int e = eb * ROWS + 32 * ec + i;
+            if (nv && e < p.NE)
+              p.zpart[((long long)l * p.NE + e) * p.N + n] =
+                  ok ? make_float2(__uint_as_float(wr[i]) * sc, __uint_as_float(wi[i]) * sc)
+                     : make_float2(0.f, 0.f);
+          }
+        }
+      }
+      if constexpr (FUSED) {
+        if (nv)
+          p.zpart[((long long)l * p.nbe + eb) * p.N + n] =
+              ok ? make_float2(zx * sc, zy * sc) : make_float2(0.f, 0.f);
+      }
+      fence_before_sync();  // the TMEM reads precede the buffer's next MMAs
+      mbar_arrive(smem_addr(&bar_freed[b]));
+    }
+  } else if (warp < 4) {
     const int r = tid;
     auto issue = [&](int g) {
       if (g < nchunks) {
@@ -434,13 +492,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
         const uint32_t rb = raw0 + (uint32_t)((g % M_RAW) * M_RAW_BYTES);
         const float2* Xl = p.X + (long long)l * p.NE * p.N;
 #pragma unroll
-        for (int k = 0; k < (M_TILES * KS * ROWS / 2) / 128; ++k) {
+        for (int k = 0; k < (KS * ROWS / 2) / 128; ++k) {
           const int i = r + 128 * k;
-          const int t = i / (KS * ROWS / 2), jj = (i / (ROWS / 2)) % KS, pr = i % (ROWS / 2);
+          const int jj = i / (ROWS / 2), pr = i % (ROWS / 2);
           const int jrow = ks * KS + jj;
-          const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + 2 * pr;
+          const long long n = (long long)pb * ROWS + 2 * pr;
           const bool ok = (jrow < p.NE) && (n < p.N);
-          cp_async16(rb + (uint32_t)(t * M_RAW_TILE + jj * ROWS * 8 + 16 * pr),
+          cp_async16(rb + (uint32_t)(jj * ROWS * 8 + 16 * pr),
                      ok ? Xl + (long long)jrow * p.N + n : p.X, ok ? 16u : 0u);
         }
       }
@@ -468,98 +526,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
       }
       const uint32_t rb = raw0 + (uint32_t)((g % M_RAW) * M_RAW_BYTES);
 #pragma unroll
-      for (int t = 0; t < M_TILES; ++t) {
-        const uint32_t ab = cb + (uint32_t)(t * 4 * PLANE);
+      for (int half = 0; half < 2; ++half) {
+        float re[4], im[4];
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          float re[4], im[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const float2 v = lds64(rb + (uint32_t)(t * M_RAW_TILE + (4 * half + i) * ROWS * 8 + 8 * r));
-            re[i] = v.x;
-            im[i] = p.conj_x ? -v.y : v.y;
-          }
-          put_a(ab + 0 * PLANE, ab + 1 * PLANE, half, r, re);
-          put_a(ab + 2 * PLANE, ab + 3 * PLANE, half, r, im);
+        for (int i = 0; i < 4; ++i) {
+          const float2 v = lds64(rb + (uint32_t)((4 * half + i) * ROWS * 8 + 8 * r));
+          re[i] = v.x;
+          im[i] = p.conj_x ? -v.y : v.y;
         }
+        put_a(cb + 0 * PLANE, cb + 1 * PLANE, half, r, re);
+        put_a(cb + 2 * PLANE, cb + 3 * PLANE, half, r, im);
       }
       fence_proxy_async();
       mbar_arrive(smem_addr(&bar_full[cs]));
-      if (ks == p.nks - 1) {
-        // epilogue of this unit: TMEM lane r = pixel, columns e (Re), 128 + e (Im)
-        const bool ok = mbar_wait(smem_addr(&bar_done), kunit & 1, &abort_flag, p.err,
-                                  kErrWaitDone);
-        fence_after_sync();
-        const float2* Xl = p.X + (long long)l * p.NE * p.N;
-        const float sc = (float)p.scale[l];
-        const uint32_t lane_addr = tmem + ((uint32_t)(32 * warp) << 16);
-        if constexpr (!FUSED) {
-#pragma unroll 1
-          for (int t = 0; t < M_TILES; ++t) {
-            const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + r;
-            const bool nv = n < p.N;
-#pragma unroll 1
-            for (int ec = 0; ec < ROWS / 32; ++ec) {
-              uint32_t wr[32], wi[32];
-              tmem_ld32(lane_addr + (uint32_t)(t * 256 + 32 * ec), wr);
-              tmem_ld32(lane_addr + (uint32_t)(t * 256 + ROWS + 32 * ec), wi);
-              tmem_wait_ld();
-#pragma unroll
-              for (int i = 0; i < 32; ++i) {
-                const int e = eb * ROWS + 32 * ec + i;
-                if (nv && e < p.NE)
-                  p.zpart[((long long)l * p.NE + e) * p.N + n] =
-                      ok ? make_float2(__uint_as_float(wr[i]) * sc, __uint_as_float(wi[i]) * sc)
-                         : make_float2(0.f, 0.f);
-              }
-            }
-          }
-        }
-#pragma unroll 1
-        for (int t = 0; t < (FUSED ? M_TILES : 0); ++t) {
-          const long long n = (long long)pb * (M_TILES * ROWS) + t * ROWS + r;
-          const bool nv = n < p.N;
-          float zx = 0.f, zy = 0.f;
-#pragma unroll 1
-          for (int ec = 0; ec < ROWS / 32; ++ec) {
-            uint32_t wr[32], wi[32];
-            tmem_ld32(lane_addr + (uint32_t)(t * 256 + 32 * ec), wr);
-            tmem_ld32(lane_addr + (uint32_t)(t * 256 + ROWS + 32 * ec), wi);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int e = eb * ROWS + 32 * ec + i;
-              if (nv && e < p.NE) {
-                const float2 x = __ldg(Xl + (long long)e * p.N + n);
-                const float a = __uint_as_float(wr[i]), b = __uint_as_float(wi[i]);
-                zx += x.x * a + x.y * b;
-                zy += x.x * b - x.y * a;
-              }
-            }
-          }
-          if (nv)
-            p.zpart[((long long)l * p.nbe + eb) * p.N + n] =
-                ok ? make_float2(zx * sc, zy * sc) : make_float2(0.f, 0.f);
-        }
-        fence_before_sync();  // TMEM reads precede the next unit's MMAs
-      }
     }
     cp_async_wait<0>();
   } else {
     for (int g = 0; g < nchunks; ++g) {
-      const int cs = g % M_CONV, ks = g % p.nks;
+      const int cs = g % M_CONV, ks = g % p.nks, kunit = g / p.nks, b = kunit & 1;
+      if (ks == 0 && kunit >= 2) {
+        // buffer b is free once unit kunit - 2 has been read out
+        mbar_wait(smem_addr(&bar_freed[b]), ((kunit - 2) >> 1) & 1, &abort_flag, p.err,
+                  kErrWaitEmpty);
+        fence_after_sync();
+      }
       const bool ok = mbar_wait(smem_addr(&bar_full[cs]), (g / M_CONV) & 1, &abort_flag,
                                 p.err, kErrWaitFull);
       fence_after_sync();
       if (lane == 0 && ok) {
         const uint32_t cb = sbase + (uint32_t)(cs * M_CONV_BYTES);
-#pragma unroll
-        for (int t = 0; t < M_TILES; ++t)
-          issue_kstep(tmem + (uint32_t)(t * 256), cb + (uint32_t)(t * 4 * PLANE),
-                      cb + M_A_BYTES, ks == 0);
+        issue_kstep(tmem + 256u * b, cb, cb + M_A_BYTES, ks == 0);
         commit(smem_addr(&bar_empty[cs]));
-        if (ks == p.nks - 1) commit(smem_addr(&bar_done));
       }
+      if (lane == 0 && ks == p.nks - 1) commit(smem_addr(&bar_done[b]));
       __syncwarp();
     }
   }
@@ -567,7 +566,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) tc_jh_kernel(JhArgs p) {
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
-    tmem_dealloc(tmem, 256 * M_TILES);
+    tmem_dealloc(tmem, 512);
   }
 }
 
@@ -711,14 +710,14 @@ int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int
     cuda_fail(c, e, "tc_jh_bops_kernel");
     return -1;
   }
-  const int npb = (int)((c->N + M_TILES * ROWS - 1) / (M_TILES * ROWS));
+  const int npb = (int)((c->N + ROWS - 1) / ROWS);
   const int units = c->n_freq * nbe * npb;
   const int grid = units < c->n_sm ? units : c->n_sm;
   JhArgs args{X, (const float*)c->tc_bops, c->red, out, c->tc_err, c->N,
               c->n_elem, c->n_freq, nbe, nks, npb, units, conj_x};
   {
     Prof pf(c, kclass, bytes, flops);
-    tc_jh_kernel<FUSED><<<grid, NTHREADS, M_SMEM, c->stream>>>(args);
+    tc_jh_kernel<FUSED><<<grid, C_THREADS, M_SMEM, c->stream>>>(args);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
