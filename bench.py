@@ -197,6 +197,21 @@ def run_reference(args, rank):
     return line
 
 
+def replicas_aggregate(ms_local, units_local, world, device):
+    """Whole-job figures of N independent replicas (one process per GPU, no
+    data exchange): the slowest rank's timed-region duration and the units
+    (RHS solves) all ranks processed."""
+    if world <= 1:
+        return ms_local, units_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, samples):
     import torch
@@ -273,11 +288,7 @@ def run_ours(args, rank, world, samples):
             torch.distributed.barrier()
         ms = e0.elapsed_time(e1)
         launches1, _ = ctx.stats()
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
-        solves = 2.0 * w.n_rhs * args.steps * world
+        ms, solves = replicas_aggregate(ms, 2.0 * w.n_rhs * args.steps, world, "cuda")
         value = solves / (ms / 1e3)
 
         # ---- end to end through the C ABI with host buffers ----
