@@ -63,13 +63,14 @@ def kernel_source_hash():
 
 
 def recorded_traffic(kernel, wname):
-    """DRAM bytes per launch recorded from an ncu capture in profiles/, if
-    the kernel sources have not changed since (hash match); else None."""
+    """(DRAM bytes, algorithmic bytes) of one ncu-captured launch of a kernel
+    class, recorded in profiles/traffic.md, if the kernel sources have not
+    changed since (hash match); else None."""
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
-    pat = re.compile(r"^traffic\s+(\S+)\s+(\S+)\s+bytes_per_launch=([0-9.eE+]+)\s+"
-                     r"units_per_launch=([0-9.eE+]+)\s+src=(\w+)")
+    pat = re.compile(r"^traffic\s+(\S+)\s+(\S+)\s+dram_bytes=([0-9.eE+]+)\s+"
+                     r"algorithmic_bytes=([0-9.eE+]+)\s+src=(\w+)")
     for line in open(path):
         m = pat.match(line.strip())
         if m and m.group(1) == kernel and m.group(2) == wname and \
@@ -466,9 +467,11 @@ def roofline(name, k, peaks, peak_kind, wname, tensor):
                 "algorithmic_flops_per_launch": k["flops"] / k["launches"],
                 "traffic": None})
     if rec is not None:
-        bpl, units = rec
-        out["traffic"] = bpl
-        out["traffic_units_per_launch"] = units
+        # the captured launch's DRAM bytes, scaled to this run's average
+        # launch by algorithmic bytes
+        dram, alg = rec
+        out["traffic"] = dram * (k["bytes"] / k["launches"]) / alg
+        out["traffic_over_algorithmic"] = dram / alg
     return out
 
 
