@@ -50,6 +50,28 @@ template <typename T> using cplx = typename cplx_of<T>::type;
 template <typename T> FWI_HD cplx<T> mk(T re, T im) { cplx<T> z; z.x = re; z.y = im; return z; }
 template <typename V> FWI_HD V cadd(V a, V b) { a.x += b.x; a.y += b.y; return a; }
 template <typename V> FWI_HD V csub(V a, V b) { a.x -= b.x; a.y -= b.y; return a; }
+#if defined(__CUDA_ARCH__)
+// FP32 complex add / subtract as one packed f32x2 instruction (sm_100+):
+// both lanes are rounded exactly as the two scalar operations would be.
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) {
+  unsigned long long ua, ub, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(ua), "l"(ub));
+  float2 o;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+  return o;
+}
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) {
+  unsigned long long ua, ub, r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ua) : "f"(a.x), "f"(a.y));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(ub) : "f"(b.x), "f"(b.y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(ua), "l"(ub));
+  float2 o;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+  return o;
+}
+#endif
 template <typename V> FWI_HD V cmul(V a, V b) {
   V z; z.x = a.x * b.x - a.y * b.y; z.y = a.x * b.y + a.y * b.x; return z;
 }

@@ -251,23 +251,26 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
     }
   } else if (warp < 4) {
     const int r = tid;
-    const int e = eb * ROWS + r, j = jb * ROWS + r;
-    const bool ev = e < p.NE, jv = j < p.NE;
-    const float2* xrow = Xl + (long long)(ev ? e : 0) * p.N;
-    const float2* qrow = Ql + (long long)(jv ? j : 0) * p.N;
+    // raw fill: four lanes copy one row's 64-byte segment, so each warp
+    // instruction reads eight rows in whole 32-byte sectors
+    const int fq = r & 3;   // 16-byte piece of the segment
+    const int fr = r >> 2;  // first row of this thread (rows fr + 32 k)
     auto issue = [&](int g) {
       if (g < nch) {
         const long long n0 = n_begin + (long long)g * KS;
         const uint32_t rb = raw0 + (uint32_t)((g % C_RAW) * C_RAW_BYTES);
+        const long long n = n0 + 2 * fq;
+        const bool okn = n < n_end;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const long long n = n0 + 2 * q;
-          const bool ok = n < n_end;
-          cp_async16(rb + C_RAW_X + r * C_RAWROW + 16 * q, (ok && ev) ? xrow + n : Xl,
-                     (ok && ev) ? 16u : 0u);
+        for (int k = 0; k < 4; ++k) {
+          const int rr = fr + 32 * k;
+          const int er = eb * ROWS + rr, jr = jb * ROWS + rr;
+          const bool okx = okn && er < p.NE, okq = okn && jr < p.NE;
+          cp_async16(rb + C_RAW_X + rr * C_RAWROW + 16 * fq,
+                     okx ? Xl + (long long)er * p.N + n : Xl, okx ? 16u : 0u);
           if (!same_rows)
-            cp_async16(rb + C_RAW_Q + r * C_RAWROW + 16 * q, (ok && jv) ? qrow + n : Ql,
-                       (ok && jv) ? 16u : 0u);
+            cp_async16(rb + C_RAW_Q + rr * C_RAWROW + 16 * fq,
+                       okq ? Ql + (long long)jr * p.N + n : Ql, okq ? 16u : 0u);
         }
         if (has_a && r < 4) {
           const long long n = n0 + 2 * r;
