@@ -208,6 +208,24 @@ def _ptr(t):
     return None if t is None else c_void_p(t.data_ptr())
 
 
+def _dev(t, dtype, numel, name, optional=False):
+    """Pointer to a tensor argument after checking it against the layout the
+    C ABI documents for `name`: a contiguous CUDA tensor of `dtype` with
+    exactly `numel` elements (NULL for None when the argument is optional).
+    A mismatch raises ValueError before anything reaches the library, which
+    reads and writes the buffers by their documented sizes."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not (t.is_cuda and t.dtype == dtype and t.numel() == numel and t.is_contiguous()):
+        raise ValueError(
+            f"{name}: expected a contiguous CUDA {dtype} tensor of {numel} elements, got "
+            f"{t.dtype} of shape {tuple(t.shape)} on {t.device}"
+            + ("" if t.is_contiguous() else " (not contiguous)"))
+    return c_void_p(t.data_ptr())
+
+
 class SolveReport:
     """Host arrays of an fwi_solve_info."""
 
@@ -264,6 +282,15 @@ class Context:
             raise FwiError(st, fwi_last_error(self.handle).decode())
         return st
 
+    def _m(self, t, name="m", optional=False):
+        return _dev(t, self.torch.complex128, self.n, name, optional)
+
+    def _fields(self, t, name, optional=False):
+        return _dev(t, self.field_dtype, self.n_rhs * self.n, name, optional)
+
+    def _data(self, t, name, optional=False):
+        return _dev(t, self.field_dtype, self.n_freq * self.n_elem ** 2, name, optional)
+
     def empty_fields(self):
         return self.torch.empty((self.n_freq, self.n_elem) + self.shape,
                                 dtype=self.field_dtype, device="cuda")
@@ -286,28 +313,33 @@ class Context:
     # -- calls -----------------------------------------------------------
     def contrast_from_sos(self, sos, alpha=None):
         m = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
-        self._check(fwi_contrast_from_sos(self.handle, _ptr(sos), _ptr(alpha), _ptr(m)))
+        f64 = self.torch.float64
+        self._check(fwi_contrast_from_sos(self.handle, _dev(sos, f64, self.n, "sos"),
+                                          _dev(alpha, f64, self.n, "alpha", True), _ptr(m)))
         return m
 
     def forward(self, m, fields=None, warm_start=False, data=None, allow_nonconverged=False):
         rep = SolveReport(self.n_rhs)
         ok = (FWI_OK, FWI_ERR_NOT_CONVERGED) if allow_nonconverged else (FWI_OK,)
-        st = fwi_forward(self.handle, _ptr(m), _ptr(fields), int(warm_start), _ptr(data),
-                         byref(rep.info))
+        st = fwi_forward(self.handle, self._m(m), self._fields(fields, "fields", True),
+                         int(warm_start), self._data(data, "data", True), byref(rep.info))
         self._check(st, ok)
         rep.code = st
         return rep
 
     def adjoint(self, m, src, lam):
         rep = SolveReport(self.n_rhs)
-        self._check(fwi_adjoint(self.handle, _ptr(m), _ptr(src), _ptr(lam), byref(rep.info)))
+        self._check(fwi_adjoint(self.handle, self._m(m), self._fields(src, "src"),
+                                self._fields(lam, "lam"), byref(rep.info)))
         return rep
 
     def gradient(self, m, d_obs, grad, data=None):
         rf, ra = SolveReport(self.n_rhs), SolveReport(self.n_rhs)
         mis = c_double(0.0)
-        self._check(fwi_gradient(self.handle, _ptr(m), _ptr(d_obs), _ptr(grad), byref(mis),
-                                 _ptr(data), byref(rf.info), byref(ra.info)))
+        self._check(fwi_gradient(self.handle, self._m(m), self._data(d_obs, "d_obs"),
+                                 self._m(grad, "grad"), byref(mis),
+                                 self._data(data, "data", True), byref(rf.info),
+                                 byref(ra.info)))
         return float(mis.value), rf, ra
 
     def admm_init(self, m0):
@@ -315,26 +347,30 @@ class Context:
         g = self.torch.empty((self.dim,) + self.shape, dtype=self.torch.complex128,
                              device="cuda")
         u = self.torch.empty_like(g)
-        self._check(fwi_admm_init(self.handle, _ptr(m0), _ptr(g), _ptr(u)))
+        self._check(fwi_admm_init(self.handle, self._m(m0, "m0"), _ptr(g), _ptr(u)))
         return g, u
 
     def admm_tv_step(self, m, g, u, grad, lam=1e-4, rho=1e-3, gamma=1e-5, n_cg=10,
                      dual_step=0.0, m_ref=None, sos=None):
         p = fwi_admm_params()
         p.lambda_, p.rho, p.gamma, p.dual_step, p.n_cg = lam, rho, gamma, dual_step, n_cg
-        p.m_ref = None if m_ref is None else m_ref.data_ptr()
-        self._check(fwi_admm_tv_step(self.handle, _ptr(m), _ptr(g), _ptr(u), _ptr(grad),
-                                     byref(p), _ptr(sos)))
+        m_ref_p = self._m(m_ref, "m_ref", True)
+        p.m_ref = None if m_ref_p is None else m_ref_p.value
+        c128, dn = self.torch.complex128, self.dim * self.n
+        self._check(fwi_admm_tv_step(self.handle, self._m(m), _dev(g, c128, dn, "g"),
+                                     _dev(u, c128, dn, "u"), self._m(grad, "grad"), byref(p),
+                                     _dev(sos, self.torch.float64, self.n, "sos", True)))
 
     def apply(self, kind, vin, freq, m=None):
-        out = self.torch.empty_like(vin)
         nb = vin.shape[0]
+        vp = _dev(vin, self.field_dtype, nb * self.n, "in")
+        out = self.torch.empty_like(vin)
         if kind == "K":
-            st = fwi_apply_K(self.handle, freq, nb, _ptr(vin), _ptr(out))
+            st = fwi_apply_K(self.handle, freq, nb, vp, _ptr(out))
         elif kind == "A":
-            st = fwi_apply_A(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
+            st = fwi_apply_A(self.handle, self._m(m), freq, nb, vp, _ptr(out))
         else:
-            st = fwi_apply_AH(self.handle, _ptr(m), freq, nb, _ptr(vin), _ptr(out))
+            st = fwi_apply_AH(self.handle, self._m(m), freq, nb, vp, _ptr(out))
         self._check(st)
         return out
 
@@ -397,12 +433,14 @@ class Context:
     def jac_forward(self, a):
         y = self.torch.empty((self.n_freq, self.n_elem, self.n_elem),
                              dtype=self.torch.complex128, device="cuda")
-        self._check(fwi_jac_forward(self.handle, _ptr(a), _ptr(y)))
+        self._check(fwi_jac_forward(self.handle, self._m(a, "a"), _ptr(y)))
         return y
 
     def jac_adjoint(self, y):
         z = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
-        self._check(fwi_jac_adjoint(self.handle, _ptr(y), _ptr(z)))
+        self._check(fwi_jac_adjoint(self.handle,
+                                    _dev(y, self.torch.complex128, self.n_freq * self.n_elem ** 2,
+                                         "y"), _ptr(z)))
         return z
 
 
@@ -427,6 +465,10 @@ class Server:
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
         d_obs = np.ascontiguousarray(d_obs, dtype=cdt)
+        n_elem, n_freq = int(np.asarray(elem).shape[0]), int(len(freqs))
+        if sos0.size != int(np.prod(shape)) or d_obs.size != n_freq * n_elem * n_elem:
+            raise ValueError(f"sos0 must hold {int(np.prod(shape))} values and d_obs "
+                             f"{n_freq} x {n_elem} x {n_elem}; got {sos0.shape}, {d_obs.shape}")
         req.sos0 = sos0.ctypes.data_as(POINTER(c_double))
         req.d_obs = d_obs.ctypes.data
         req.admm.lambda_, req.admm.rho, req.admm.gamma = lam, rho, gamma

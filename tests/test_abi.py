@@ -46,3 +46,21 @@ def test_workspace_bytes_and_argument_checks_without_gpu():
     # valid size computation (positions are only read by fwi_create)
     assert libfwi.fwi_workspace_bytes(ctypes.byref(bad3)) > 0
     del keep, keep2, keep3
+
+
+def test_binding_rejects_tensors_that_do_not_match_the_documented_layout():
+    """The binding checks device, dtype, element count and contiguity of a
+    tensor argument before its pointer reaches the library (CPU tensors:
+    every one of them is rejected, and the message names the argument)."""
+    import pytest
+    import torch
+    from paper_2604_15796_gb300 import libfwi
+    assert libfwi._dev(None, torch.complex128, 4, "fields", optional=True) is None
+    with pytest.raises(ValueError, match="m is required"):
+        libfwi._dev(None, torch.complex128, 4, "m")
+    for t in (torch.zeros(4, dtype=torch.complex128),           # host memory
+              torch.zeros(4, dtype=torch.float64),              # wrong dtype
+              torch.zeros(5, dtype=torch.complex128),           # wrong size
+              torch.zeros(4, 2, dtype=torch.complex128).t()[0]):  # strided view
+        with pytest.raises(ValueError, match="^m: expected"):
+            libfwi._dev(t, torch.complex128, 4, "m")
