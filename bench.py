@@ -343,6 +343,12 @@ def run_ours(args, rank, world, samples):
             comp["speedup_solves_per_s"] = value / comp["value"]
             c64.close()
 
+        # ---- comparator: the same matvec through batched cuFFT (library
+        # context for the three fused passes) ----
+        cufft = None
+        if not args.no_comparator:
+            cufft = cufft_matvec_comparator(ctx, w, m0, stream)
+
         # ---- live per-kernel timing (CUDA events, profiling mode) ----
         ctx.reset_stats()
         ctx.set_profiling(True)
@@ -392,12 +398,74 @@ def run_ours(args, rank, world, samples):
         "clocks": clk.summary(),
         "e2e": e2e,
         "comparator_fp64_unbatched": comp,
+        "comparator_cufft_matvec": cufft,
     }
     ctx.close()
     return line
 
 
 TENSOR_CLASSES = ("contract_pixels", "mix_jac_adjoint", "mix_adjoint_sources")
+
+
+def cufft_matvec_comparator(ctx, w, m, stream, reps=5):
+    """Time of one matvec A v = v - K(m v) over all N_E x N_F right-hand
+    sides (Eq. 5-6, K by zero-padded FFT convolution): libfwi's three fused
+    passes (fwi_apply_A per frequency) against the textbook batched route
+    through cuFFT (torch.fft, C2C FP32: product with m, zero-pad to the 2^d N
+    lattice, forward FFT, product with the kernel spectrum, inverse FFT,
+    crop, subtract), both on the same vectors and stream.  The cuFFT route
+    multiplies by a random spectrum (its time does not depend on the
+    values), so only the times are compared."""
+    import torch
+    dim = len(w.shape)
+    pshape = tuple(2 * s for s in w.shape)
+    n_pad = int(np.prod(pshape))
+    chunk = int(max(1, min(w.n_elem, (2 << 30) // (8 * n_pad))))  # <= 2 GB padded
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    spec = torch.randn(pshape, dtype=torch.complex64, device="cuda", generator=gen)
+    v = torch.randn((chunk,) + tuple(w.shape), dtype=torch.complex64, device="cuda",
+                    generator=gen)
+    m32 = m.to(torch.complex64)
+    pad = torch.zeros((chunk,) + pshape, dtype=torch.complex64, device="cuda")
+    crop = tuple(slice(0, s) for s in w.shape)
+    axes = tuple(range(1, dim + 1))
+    blocks = [(l, e0, min(chunk, w.n_elem - e0))
+              for l in range(w.n_freq) for e0 in range(0, w.n_elem, chunk)]
+
+    def ours():
+        for l, _, nb in blocks:
+            ctx.apply("A", v[:nb], l, m)
+
+    def library():
+        for _, _, nb in blocks:
+            pad[:nb].zero_()
+            pad[(slice(0, nb),) + crop].copy_(v[:nb] * m32)
+            f = torch.fft.fftn(pad[:nb], dim=axes)
+            f *= spec
+            v[:nb] - torch.fft.ifftn(f, dim=axes)[(slice(None),) + crop]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    try:
+        with torch.cuda.stream(stream):
+            t_ours, t_lib = timed(ours), timed(library)
+    except Exception as exc:  # e.g. a batch limit below the chunk
+        return {"unavailable": str(exc).splitlines()[0]}
+    finally:
+        del pad
+    return {"kind": "one A v over all RHS: fwi_apply_A (3 fused passes) vs torch.fft/cuFFT "
+                    "C2C FP32 batched (pad, FFT, spectrum, IFFT, crop)",
+            "rhs": w.n_rhs, "rhs_per_call": chunk, "libfwi_ms": t_ours, "cufft_ms": t_lib,
+            "speedup": t_lib / t_ours}
 
 
 def peak_table(peaks, peak_kind):
