@@ -562,6 +562,40 @@ def sampled_error(ctx, m0, samples):
             "samples": len(samples), "tolerance": 1e-4}
 
 
+def serving_fp64_comparator(work, results, rate, n_sample=2):
+    """Latency of the plain unbatched FP64 path (complex128 fields, one RHS
+    per Krylov launch, same tolerance and ADMM parameters) on the smallest
+    requests of the stream (by N x RHS, which bounds its run time), each run
+    alone; beside it the same request alone through the batched path and
+    its latency in the mix.  A path whose service time exceeds the mean
+    inter-arrival time cannot keep up with the stream at all."""
+    from paper_2604_15796_gb300 import libfwi
+    order = sorted(range(len(work)), key=lambda k: int(np.prod(work[k][0].shape)) * work[k][0].n_rhs)
+    rows = []
+    for k in order[:n_sample]:
+        w, s0, d, prm = work[k]
+        row = {"request": k, "grid": "x".join(map(str, reversed(w.shape))), "rhs": int(w.n_rhs),
+               "in_mix_ms": results[k]["latency_ms"]}
+        for name, kw in (("batched_alone_ms", {}),
+                         ("fp64_unbatched_alone_ms", dict(precision=libfwi.FWI_FP64, max_batch=1))):
+            one = libfwi.Server(max_active=1)
+            _, r = one.wait(one.submit(w.shape, w.h, w.c0, w.elem, w.freqs, s0, d, **prm, **kw))
+            one.close()
+            row[name] = r["latency_ms"]
+            row[name.replace("_ms", "_status")] = r["status"]
+        row["factor_alone"] = row["fp64_unbatched_alone_ms"] / row["batched_alone_ms"]
+        row["factor_vs_in_mix"] = row["fp64_unbatched_alone_ms"] / row["in_mix_ms"]
+        rows.append(row)
+        print(f"serving comparator: request {k} {row['grid']} FP64 unbatched "
+              f"{row['fp64_unbatched_alone_ms'] / 1e3:.1f} s, batched alone "
+              f"{row['batched_alone_ms'] / 1e3:.2f} s", file=sys.stderr, flush=True)
+    return {"kind": "plain unbatched FP64 path (complex128 fields, max_batch 1), each request "
+                    "alone, on the smallest requests of the stream",
+            "requests": rows,
+            "factor_alone_min": min(r["factor_alone"] for r in rows),
+            "mean_interarrival_ms": 1e3 / rate}
+
+
 def run_serving(args):
     """Serving stream: Poisson arrivals of whole reconstructions (5 ADMM-TV
     iterations each) over grids {128^2, 256^2, 384^2, 512^2, 96^3}, 64-192
@@ -649,6 +683,7 @@ def run_serving(args):
             th.join()
     wall = time.perf_counter() - start
     srv.close()
+    comp = None if args.no_comparator else serving_fp64_comparator(work, results, rate)
     lat = np.array([r["latency_ms"] for r in results])
     bad = sum(1 for r in results if r["status"] != 0)
     solves = sum(r["rhs_solves"] for r in results)
@@ -671,6 +706,7 @@ def run_serving(args):
                                               "latency_ms", "krylov_iters_max",
                                               "krylov_iters_mean", "not_converged")}
                          for r in results],
+            "comparator_fp64_unbatched": comp,
             "clocks": clk.summary()}
 
 

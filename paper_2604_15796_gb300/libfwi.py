@@ -456,11 +456,14 @@ class Server:
         self._pending = {}
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
-               gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000):
+               gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000,
+               max_batch=0):
         """Queue a reconstruction; host numpy inputs (sos0 float64 of ``shape``,
-        d_obs complex64 [n_freq][n_elem][n_elem]).  Returns the request id."""
+        d_obs [n_freq][n_elem][n_elem], complex64 for FWI_MIXED and complex128
+        for FWI_FP64).  max_batch limits the right-hand sides per Krylov launch
+        (0: all).  Returns the request id."""
         req = fwi_request()
-        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it)
+        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
