@@ -136,3 +136,34 @@ def admm_tv_step(m, g, u, grad, fields, rfields, prob, params, m_ref=None):
     step = params.rho if params.dual_step is None else params.dual_step
     u_new = np.asarray(u) + step * (g_new - gm)
     return m_new, g_new, u_new, model.sos_from_contrast(m_new, prob.c0), dm
+
+
+def reconstruct(m0, d_obs, prob, params, n_iter, method="bicgstab", tol=1e-10, weights=None,
+                refresh_every=1, m_ref=None):
+    """Algorithm 1 for ``n_iter`` iterations with the hybrid Born /
+    distorted-Born Jacobian of Sec. IV-B: every iteration solves the
+    transmit fields and the adjoint states at the current model (gradient),
+    while the receiver fields ptilde_j = A^{-1} R_j (solved separately, one
+    solve per receiver and frequency) are refreshed only on iterations
+    k = 0, refresh_every, 2 refresh_every, ... and kept fixed in between
+    (a Born approximation for the adjoint problem).  refresh_every = 1 is
+    the strict distorted-Born Jacobian.  ``weights``: synthesised transmits
+    (plane waves, Sec. V-A).  Returns (m, g, u, sos, history) with
+    history[k] = (misfit, refreshed)."""
+    shape = prob.shape
+    m = np.asarray(m0, dtype=np.complex128).reshape(shape).copy()
+    g = grad_op(m, shape)
+    u = np.zeros_like(g)
+    rfields = None
+    sos = model.sos_from_contrast(m, prob.c0)
+    history = []
+    for k in range(n_iter):
+        ref = inverse.gradient(m, d_obs, prob, method, tol, weights)
+        refreshed = rfields is None or k % refresh_every == 0
+        if refreshed:
+            rfields = inverse.receiver_fields(m, prob, method, tol)
+        m, g, u, sos, _ = admm_tv_step(m, g, u, ref["grad"], ref["fields"], rfields, prob,
+                                       params, m_ref)
+        history.append((ref["misfit"], refreshed))
+    return m, g, u, sos, history
+

@@ -14,10 +14,13 @@ Discretisation (readings):
       ptilde_{l,j} = A_l^{-1} R_{l,j}   (K is complex-symmetric),
   i.e. Eq. 15 with k^2 and the cell volume carried inside ptilde, and with
   "approximately equal" exact because ptilde is computed at the current
-  iterate.  Because each receiver sits at a transmit position,
-  R_{l,j} = k_l^2 dV p0_{l,j} and ptilde_{l,j} = k_l^2 dV p_{l,j}: no extra
-  solves (the hybrid Born refresh of Sec. IV-B is then exact every
-  iteration).
+  iterate.  Because each receiver sits at an element position,
+  R_{l,j} = k_l^2 dV p0_{l,j} and ptilde_{l,j} = k_l^2 dV p_{l,j} for the
+  element's point-source field.  With point transmits at every element no
+  extra solves are needed; with synthesised transmits (plane waves,
+  Sec. V-A) the transmit fields differ from the receiver fields, which
+  receiver_fields solves separately (refreshed on the schedule of
+  Sec. IV-B, admm.reconstruct).
 * Gradient of phi = 1/2 ||F(m) - d||^2 in the complex (Wirtinger) sense:
   grad = J^H r with r = F(m) - d, so that
   d phi(m + eps a)/d eps = Re <grad, a>.
@@ -59,9 +62,15 @@ def misfit(d, d_obs):
     return 0.5 * float(np.vdot(r, r).real)
 
 
-def forward_model(m, prob, method="lu", tol=1e-10):
-    """F(m): fields and data (Eq. 4-6).  Returns (fields, data)."""
-    fields = operator.solve_forward(m, prob, method, tol)
+def forward_model(m, prob, method="lu", tol=1e-10, weights=None):
+    """F(m): fields and data (Eq. 4-6).  Returns (fields, data).
+
+    With ``weights`` [N_F, N_T, N_E] the transmits are synthesised ones
+    (plane waves, Sec. V-A): each transmit field is solved directly from
+    its own incident field, A_l p_{l,i} = sum_e w_{l,i,e} p0_{l,e}, and the
+    data are [l][i][j] with every element receiving."""
+    p0 = None if weights is None else operator.transmit_incident_fields(prob, weights)
+    fields = operator.solve_forward(m, prob, method, tol, p0=p0)
     return fields, forward_data(m, fields, prob)
 
 
@@ -81,7 +90,7 @@ def adjoint_sources(resid, prob, rows=None):
         rows = receiver_rows(prob)
     R = _flat(rows, prob)
     s = np.einsum("lej,ljn->len", np.asarray(resid), np.conj(R))
-    return s.reshape((prob.n_freq, prob.n_elem) + tuple(prob.shape))
+    return s.reshape(s.shape[:2] + tuple(prob.shape))  # [N_F, N_T, *shape]
 
 
 def apply_AH(v, m, prob, l, spec=None):
@@ -158,11 +167,13 @@ def jac_dense(fields, rfields, prob):
     return J.reshape(-1, prob.n)
 
 
-def gradient(m, d_obs, prob, method="lu", tol=1e-10):
+def gradient(m, d_obs, prob, method="lu", tol=1e-10, weights=None):
     """One gradient evaluation: forward solves, data, misfit, adjoint
     sources, adjoint solves, assembly.  Returns a dict with every
-    intermediate (fields, data, resid, misfit, lam, grad)."""
-    fields, data = forward_model(m, prob, method, tol)
+    intermediate (fields, data, resid, misfit, lam, grad).  ``weights``:
+    synthesised transmits (see forward_model); one forward and one adjoint
+    solve per transmit and frequency."""
+    fields, data = forward_model(m, prob, method, tol, weights)
     resid = data - np.asarray(d_obs)
     src = adjoint_sources(resid, prob)
     lam = solve_adjoint(m, src, prob, method, tol)

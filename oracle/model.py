@@ -107,3 +107,22 @@ def sos_from_contrast(m, c0):
     """Speed of sound from the real part of the contrast, the inverse of
     Eq. 2-3 for a lossless point: c = c0 / sqrt(1 + Re m)."""
     return c0 / np.sqrt(1.0 + np.real(np.asarray(m)))
+
+
+def plane_wave_weights(prob, angles):
+    """Element weights of steered plane-wave transmits (Sec. V-A: plane waves
+    synthesised with the array's elements, steering angles spread over
+    +-60 degrees).
+
+    Reading: transmit i fires element e with the delay
+    tau_{i,e} = x_e sin(theta_i) / c0, x_e the element's lateral position
+    (the array is centred), so that the wavefront leaves the array in the
+    direction (sin theta_i, cos theta_i) of the (x, z) plane, z pointing
+    into the medium.  Under e^{-i omega t} a delay tau multiplies a source
+    by exp(i omega tau), hence w_{l,i,e} = exp(i k_l x_e sin theta_i).
+    Unit amplitude on every element (no apodisation).  [N_F, N_T, N_E]."""
+    k = wavenumbers(prob)
+    xe = np.asarray(prob.elem, dtype=np.float64)[:, 0]
+    s = np.sin(np.asarray(angles, dtype=np.float64))
+    return np.exp(1j * k[:, None, None] * s[None, :, None] * xe[None, None, :])
+

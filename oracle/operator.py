@@ -81,6 +81,16 @@ def incident_fields(prob):
     return out
 
 
+def transmit_incident_fields(prob, weights):
+    """Incident fields of synthesised transmits (Sec. V-A): the elements'
+    point sources superposed with the weights w_{l,i,e},
+    p0_{l,i} = sum_e w_{l,i,e} G_l(., x_e).  [N_F, N_T, *shape]."""
+    p0 = incident_fields(prob)
+    flat = p0.reshape(prob.n_freq, prob.n_elem, prob.n)
+    out = np.einsum("lie,len->lin", np.asarray(weights, dtype=np.complex128), flat)
+    return out.reshape((prob.n_freq, out.shape[1]) + tuple(prob.shape))
+
+
 def bicgstab(apply, b, tol=1e-10, maxit=2000, x0=None):
     """Textbook BiCGSTAB (van der Vorst, 1992) for one right-hand side.
 
