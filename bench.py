@@ -44,14 +44,18 @@ def load_peaks():
 def workload(name):
     from paper_2604_15796_gb300 import phantoms
     return {"thyroid256": phantoms.thyroid_256, "large512": phantoms.large_512,
-            "volume3d": phantoms.volume_3d, "disc64": phantoms.disc_phantom}[name]()
+            "volume3d": phantoms.volume_3d, "disc64": phantoms.disc_phantom,
+            "planewave2d": phantoms.planewave_2d}[name]()
 
 
 def describe(w):
     grid = "x".join(str(s) for s in reversed(w.shape))
+    tx = w.meta.get("tx_angles")
+    txs = "" if tx is None else (f", {len(tx)} plane-wave transmits synthesised from the "
+                                 f"{w.n_elem} element solves")
     return (f"{w.name}: {grid} grid, h={w.h * 1e3:.2f} mm, {w.n_elem} elements x "
-            f"{w.n_freq} freqs ({w.n_rhs} RHS), per step 1 forward + 1 adjoint BiCGSTAB solve "
-            f"per RHS + data + gradient + ADMM-TV step (n_cg=10)")
+            f"{w.n_freq} freqs ({w.n_rhs} RHS){txs}, per step 1 forward + 1 adjoint BiCGSTAB "
+            f"solve per RHS + data + gradient + ADMM-TV step (n_cg=10)")
 
 
 def kernel_source_hash():
@@ -144,24 +148,33 @@ def oracle_solves_per_s(w, budget_s=15.0, seed=0, keep=0):
     prob = oracle.Problem(tuple(w.shape), w.h, w.c0, w.elem, np.asarray(w.freqs))
     m = 0.8 * model.contrast_from_sos(w.sos, w.c0)
     rng = np.random.default_rng(seed)
+    tx = w.meta.get("tx_angles")
     specs = {}
     kept = []
     n, t0 = 0, time.perf_counter()
     while True:
         l = int(rng.integers(0, w.n_freq))
-        e = int(rng.integers(0, w.n_elem))
+        e = int(rng.integers(0, w.n_elem if tx is None else len(tx)))
         if l not in specs:
             specs[l] = operator.kernel_spectrum(prob, l)
-        sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem[[e]],
-                             np.asarray([w.freqs[l]]))
-        b = operator.incident_fields(sub)[0, 0]
+        wrow = None
+        if tx is None:
+            sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem[[e]],
+                                 np.asarray([w.freqs[l]]))
+            b = operator.incident_fields(sub)[0, 0]
+        else:
+            # plane-wave transmit e, solved directly from its incident field
+            sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]))
+            wl = model.plane_wave_weights(sub, [tx[e]])
+            b = operator.transmit_incident_fields(sub, wl)[0, 0]
+            wrow = wl[0, 0]
         spec = specs[l]
         x, _, _ = operator.bicgstab(lambda v: operator.apply_A(v.reshape(prob.shape), m, prob,
                                                               l, spec).ravel(), b.ravel(), 1e-10)
         if len(kept) < keep:
             subr = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]))
             row = inverse.forward_data(m, x.reshape((1, 1) + prob.shape), subr)[0, 0]
-            kept.append((l, e, x.reshape(prob.shape), row))
+            kept.append((l, e, x.reshape(prob.shape), row, wrow))
         n += 1
         if time.perf_counter() - t0 > budget_s and n >= keep:
             break
@@ -225,6 +238,7 @@ def run_ours(args, rank, world, samples):
     peaks, peak_kind = load_peaks()
     with torch.cuda.stream(stream):
         ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6, stream=stream,
+                             tx_angles=w.meta.get("tx_angles"),
                              max_batch=args.max_batch)
         if args.cuda_core_jacobian:
             ctx.set_jac_tensor_cores(False)
@@ -546,15 +560,22 @@ def roofline(name, k, peaks, peak_kind, wname, tensor):
 def sampled_error(ctx, m0, samples):
     """Relative L2 error of sampled forward fields and of their data rows
     against the FP64 oracle solutions (BiCGSTAB tol 1e-10) computed in the
-    CPU-baseline leg, at full size."""
+    CPU-baseline leg, at full size.  For a plane-wave sample the device
+    field is the superposition of the element fields with the oracle's
+    weight row, and the data row is the transmit's row."""
     import torch
     fields = ctx.empty_fields()
     data = ctx.empty_data()
     ctx.forward(m0, fields=fields, data=data)
     torch.cuda.synchronize()
     errs_f, errs_d = [], []
-    for l, e, ref, refd in samples:
-        got = fields[l, e].cpu().numpy()
+    for l, e, ref, refd, wrow in samples:
+        if wrow is None:
+            got = fields[l, e].cpu().numpy()
+        else:
+            wt = torch.from_numpy(wrow).to(device="cuda")
+            got = torch.einsum("e,en->n", wt, fields[l].reshape(ctx.n_elem, -1).to(
+                torch.complex128)).reshape(ctx.shape).cpu().numpy()
         errs_f.append(float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
         gotd = data[l, e].cpu().numpy()
         errs_d.append(float(np.linalg.norm(gotd - refd) / np.linalg.norm(refd)))
@@ -717,7 +738,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thyroid256",
-                    choices=["thyroid256", "large512", "volume3d", "disc64", "serving"])
+                    choices=["thyroid256", "large512", "volume3d", "disc64", "planewave2d",
+                             "serving"])
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

@@ -85,6 +85,18 @@ typedef struct fwi_problem_desc {
   int precision;           /* fwi_precision */
   int max_batch;           /* right-hand sides per Krylov launch
                               (<= 0: all n_elem * n_freq in one launch) */
+  /* Transmits (Sec. V-A).  n_tx = 0: every element transmits a unit point
+     source in turn (N_T = n_elem).  n_tx > 0: N_T = n_tx plane waves
+     synthesised with all elements, transmit i weighting element e by
+     w_{l,i,e} = exp(i k_l x_e sin tx_angle[i]) (delay x_e sin(theta) / c0
+     under e^{-i omega t}; x_e the element's lateral coordinate).  By
+     superposition the library solves the n_elem point-source fields and
+     synthesises: data, residuals and Jacobian rows of transmit i are the
+     w-weighted sums over elements.  Every element receives.  Data arrays
+     (data, d_obs, J a, J^H b input) are [n_freq][N_T][n_elem]. */
+  int n_tx;
+  const double* tx_angle;  /* host [n_tx] steering angles [rad] or NULL when
+                              n_tx = 0; copied in fwi_create */
 } fwi_problem_desc;
 
 /* Per-call Krylov report.  The caller sets n_rhs and the optional host
@@ -147,8 +159,10 @@ FWI_API fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos,
    P^s_{l,e,j} = k_l^2 dV sum_n G_l(x_j, x_n) m_n p_{l,e}(n).
    m: dev c128 [N].  fields: dev cF [n_freq][n_elem][N] or NULL (out; with
    warm_start != 0 also the initial guess, otherwise the guess is 0).
-   data: dev cF [n_freq][n_elem][n_elem] or NULL (out).  The fields stay in
-   the context for fwi_admm_tv_step.  info: host or NULL. */
+   data: dev cF [n_freq][N_T][n_elem] or NULL (out; with plane-wave
+   transmits the w-weighted sums of the point-source data).  The fields
+   (always the n_elem point-source fields) stay in the context for
+   fwi_admm_tv_step.  info: host or NULL. */
 FWI_API fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields,
                        int warm_start, void* data, fwi_solve_info* info);
 
@@ -162,9 +176,12 @@ FWI_API fwi_status fwi_adjoint(fwi_ctx* ctx, const void* m, const void* src,
    forward solves, residual r = F(m) - d_obs, adjoint sources
    s_{l,e} = sum_j conj(R_{l,j}) r_{l,e,j}, adjoint solves, and
    grad_n = sum_{l,e} conj(p_{l,e}(n)) lambda_{l,e}(n) = (J^H r)_n.
-   d_obs: dev cF [n_freq][n_elem][n_elem]; grad: dev c128 [N] (out);
+   d_obs: dev cF [n_freq][N_T][n_elem]; grad: dev c128 [N] (out);
    misfit: host double (out) or NULL; data: dev cF (out, the predicted
-   data F(m)) or NULL.  The forward fields stay in the context. */
+   data F(m)) or NULL.  The forward fields stay in the context.  With
+   plane-wave transmits r is the plane-wave residual and the adjoint
+   sources of element e carry the residual W^H r (the gradient of the
+   synthesised data map by the chain rule). */
 FWI_API fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs,
                         void* grad, double* misfit, void* data,
                         fwi_solve_info* info_fwd, fwi_solve_info* info_adj);
@@ -176,6 +193,9 @@ FWI_API fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs,
    fwi_gradient), m += dm, g = shrink_{lambda/rho}(nabla m - u),
    u += dual_step (g - nabla m), and optionally c = c0 / sqrt(1 + Re m).
    nabla: forward differences in index units, zero on the last slice.
+   With plane-wave transmits J^H J = J_point^H (W^H W) J_point: the exact
+   distorted-Born Jacobian at the current model every iteration (the
+   receiver fields are the point-source fields solved anyway).
    m: dev c128 [N] (in/out); g, u: dev c128 [dim][N] (in/out, component
    order x, [y], z); grad: dev c128 [N]; sos_out: dev double [N] or NULL. */
 FWI_API fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u,
@@ -201,8 +221,9 @@ FWI_API fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs
    (Eq. 16-17, receiver fields ptilde_{l,j} = k_l^2 dV p_{l,j}):
    (J a)_{l,e,j} = sum_n p_{l,e}(n) ptilde_{l,j}(n) a_n and
    (J^H b)_n = sum_{l,e,j} conj(p_{l,e}(n) ptilde_{l,j}(n)) b_{l,e,j}.
-   a: dev c128 [N]; y: dev c128 [n_freq][n_elem][n_elem] (out of J, in of
-   J^H); z: dev c128 [N] (out). */
+   a: dev c128 [N]; y: dev c128 [n_freq][N_T][n_elem] (out of J, in of
+   J^H; with plane-wave transmits J = W J_point, J^H = J_point^H W^H);
+   z: dev c128 [N] (out). */
 FWI_API fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y);
 FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
 
@@ -222,7 +243,7 @@ typedef struct fwi_server fwi_server;
 typedef struct fwi_request {
   fwi_problem_desc problem;  /* host arrays are copied at submit */
   const double* sos0;        /* host double [N]: starting speed of sound */
-  const void* d_obs;         /* host cF [n_freq][n_elem][n_elem]: observed data */
+  const void* d_obs;         /* host cF [n_freq][N_T][n_elem]: observed data */
   fwi_admm_params admm;      /* m_ref must be NULL */
   int n_iter;                /* ADMM-TV iterations (>= 1) */
 } fwi_request;

@@ -301,7 +301,14 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   for (int it = 0; it < p->n_cg; ++it) {
     fwi_status st = jac_forward(c, d, c->dres);
     if (st != FWI_OK) return st;
-    st = jac_adjoint(c, c->dres, z);
+    const double2* y = c->dres;
+    if (c->n_tx > 0) {
+      // plane-wave transmits: J^H J = J_point^H (W^H W) J_point
+      st = synth(c, c->WhW, 0, c->n_elem, c->n_elem, c->dres, c->dsyn, nullptr);
+      if (st != FWI_OK) return st;
+      y = c->dsyn;
+    }
+    st = jac_adjoint(c, y, z);
     if (st != FWI_OK) return st;
     {
       Prof pf(c, KC_ADMM);

@@ -38,6 +38,7 @@ bool fft_len_ok(int L) {
 // Everything fwi_create derives from the descriptor.
 struct Layout {
   int dim, nx, ny, nz, lx, ly, lz, rows, n_elem, n_freq, n_rhs, batch, ntiles, split;
+  int n_tx, n_t;  // plane-wave transmits (0: point transmits); N_T
   long long N;
   size_t csz;
   size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec, b_tc;
@@ -62,7 +63,13 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   for (int l = 0; l < d->n_freq; ++l)
     if (!(d->freq_hz[l] > 0)) return bad("frequencies must be positive");
   if (d->precision != FWI_MIXED && d->precision != FWI_FP64) return bad("unknown precision");
+  if (d->n_tx < 0 || (d->n_tx > 0 && !d->tx_angle))
+    return bad("n_tx must be >= 0, with tx_angle when positive");
+  for (int i = 0; i < d->n_tx; ++i)
+    if (!std::isfinite(d->tx_angle[i])) return bad("tx_angle must be finite");
   L.n_elem = d->n_elem; L.n_freq = d->n_freq;
+  L.n_tx = d->n_tx;
+  L.n_t = d->n_tx > 0 ? d->n_tx : d->n_elem;
   L.n_rhs = d->n_elem * d->n_freq;
   L.batch = (d->max_batch > 0 && d->max_batch < L.n_rhs) ? d->max_batch : L.n_rhs;
   L.N = (long long)L.nx * L.ny * L.nz;
@@ -91,9 +98,14 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.b_kv = (size_t)L.batch * L.N * L.csz;
   L.b_plane1 = (size_t)L.batch * L.rows * L.lx * L.csz;
   L.b_plane2 = (d->dim == 3) ? (size_t)L.batch * L.nz * L.ly * L.lx * L.csz : 0;
+  // data-space buffers: dres and (plane waves) W, W^H W, dpw, dsyn; dF holds
+  // max(N_T, n_elem) rows of field-precision data
+  const long long NTE = (long long)L.n_t * L.n_elem;
+  const long long NDF = std::max(NTE, NE2);
+  const size_t b_pw = L.n_tx > 0 ? (size_t)L.n_freq * (2 * NTE + 2 * NE2) * 16 : 0;
   L.b_small = (size_t)L.batch * (sizeof(Scal) + NSLOT * (size_t)L.rows * sizeof(double2) +
                                  sizeof(int)) +
-              64 + (size_t)L.n_freq * NE2 * (16 + L.csz) + 3 * 1024 * L.csz;
+              64 + (size_t)L.n_freq * (NE2 * 16 + NDF * L.csz) + b_pw + 3 * 1024 * L.csz;
   size_t js1 = (size_t)L.split * L.n_freq * NE2 * L.csz;
   size_t js2 = (size_t)8 * L.N * sizeof(double2);
   L.b_jsplit = js1 > js2 ? js1 : js2;
@@ -129,6 +141,7 @@ static void release(fwi_ctx* c) {
   void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
+                  c->W, c->WhW, c->dpw, c->dsyn,
                   c->jsplit, c->zpart, c->aF, c->red, c->tc_bops, c->tc_err};
   // stream-ordered frees: no device-wide synchronisation, so a context can be
   // retired while other contexts' work runs
@@ -189,6 +202,9 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   c->elem.assign(d->elem_pos, d->elem_pos + (size_t)d->n_elem * d->dim);
   c->freq.assign(d->freq_hz, d->freq_hz + d->n_freq);
   for (double f : c->freq) c->kwave.push_back(2.0 * 3.141592653589793238462643383279502884 * f / c->c0);
+  c->n_tx = L.n_tx;
+  c->n_t = L.n_t;
+  if (L.n_tx > 0) c->tx_angle.assign(d->tx_angle, d->tx_angle + L.n_tx);
   c->stream = (cudaStream_t)stream;
   c->bytes = L.total;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -220,8 +236,15 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   alloc((void**)&c->active, sizeof(int) * L.batch);
   alloc((void**)&c->n_active, 64);
   const size_t NE2 = (size_t)L.n_elem * L.n_elem;
+  const size_t NTE = (size_t)L.n_t * L.n_elem;
   alloc((void**)&c->dres, 16 * L.n_freq * NE2);
-  alloc(&c->dF, L.csz * L.n_freq * NE2);
+  alloc(&c->dF, L.csz * L.n_freq * std::max(NTE, NE2));
+  if (L.n_tx > 0) {
+    alloc((void**)&c->W, 16 * L.n_freq * NTE);
+    alloc((void**)&c->WhW, 16 * L.n_freq * NE2);
+    alloc((void**)&c->dpw, 16 * L.n_freq * NTE);
+    alloc((void**)&c->dsyn, 16 * L.n_freq * NE2);
+  }
   alloc(&c->jsplit, L.b_jsplit);
   alloc(&c->zpart, L.b_zpart);
   alloc(&c->aF, (size_t)L.N * L.csz);
@@ -253,6 +276,36 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   std::vector<double> sc(L.n_freq);
   for (int l = 0; l < L.n_freq; ++l) sc[l] = c->kwave[l] * c->kwave[l] * std::pow(c->h, c->dim);
   e = cudaMemcpy(c->red, sc.data(), sizeof(double) * L.n_freq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && L.n_tx > 0) {
+    // plane-wave weights w_{l,i,e} = exp(i k_l x_e sin theta_i) and W^H W
+    const int nt = L.n_tx, ne = L.n_elem;
+    std::vector<double2> w((size_t)L.n_freq * nt * ne), whw((size_t)L.n_freq * ne * ne);
+    for (int l = 0; l < L.n_freq; ++l) {
+      for (int i = 0; i < nt; ++i)
+        for (int q = 0; q < ne; ++q) {
+          const double ph = c->kwave[l] * c->elem[(size_t)q * c->dim] * std::sin(c->tx_angle[i]);
+          w[((size_t)l * nt + i) * ne + q] = make_double2(std::cos(ph), std::sin(ph));
+        }
+      for (int a = 0; a < ne; ++a)
+        for (int b = 0; b < ne; ++b) {
+          double sx = 0.0, sy = 0.0;
+          for (int i = 0; i < nt; ++i) {
+            const double2 u = w[((size_t)l * nt + i) * ne + a], v = w[((size_t)l * nt + i) * ne + b];
+            sx += u.x * v.x + u.y * v.y;  // conj(u) v
+            sy += u.x * v.y - u.y * v.x;
+          }
+          whw[((size_t)l * ne + a) * ne + b] = make_double2(sx, sy);
+        }
+    }
+    // ordered after the stream-ordered allocations; the host vectors live
+    // until the synchronisation
+    e = cudaMemcpyAsync(c->W, w.data(), sizeof(double2) * w.size(), cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->WhW, whw.data(), sizeof(double2) * whw.size(),
+                          cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e != cudaSuccess) {
     fail(nullptr, FWI_ERR_CUDA, std::string("scale upload: ") + cudaGetErrorString(e));
     release(c);
@@ -403,7 +456,11 @@ fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y) {
   if (!a || !y) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
   ctx->err.clear();
-  return jac_forward(ctx, a, (double2*)y);
+  if (ctx->n_tx == 0) return jac_forward(ctx, a, (double2*)y);
+  // J = W J_point
+  fwi_status st = jac_forward(ctx, a, ctx->dres);
+  if (st != FWI_OK) return st;
+  return synth(ctx, ctx->W, 0, ctx->n_tx, ctx->n_elem, ctx->dres, (double2*)y, nullptr);
 }
 
 fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
@@ -411,7 +468,12 @@ fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
   if (!y || !z) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
   ctx->err.clear();
-  return jac_adjoint(ctx, (const double2*)y, (double2*)z);
+  if (ctx->n_tx == 0) return jac_adjoint(ctx, (const double2*)y, (double2*)z);
+  // J^H = J_point^H W^H
+  fwi_status st = synth(ctx, ctx->W, 1, ctx->n_elem, ctx->n_tx, (const double2*)y, ctx->dsyn,
+                        nullptr);
+  if (st != FWI_OK) return st;
+  return jac_adjoint(ctx, ctx->dsyn, (double2*)z);
 }
 
 fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {

@@ -24,6 +24,9 @@ struct fwi_ctx {
   bool fp64 = false;
   size_t csz = 8;                   // bytes of one field element
   std::vector<double> elem, freq, kwave;
+  // plane-wave transmits (0: point transmits at every element); n_t = N_T
+  int n_tx = 0, n_t = 0;
+  std::vector<double> tx_angle;
   // ---- device ----
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;  // created when the caller passes NULL
@@ -53,7 +56,11 @@ struct fwi_ctx {
   fwi::Scal* h_scal = nullptr;      // pinned host mirror [batch]
   // Jacobian / data / ADMM workspace
   double2* dres = nullptr;          // [n_freq][n_elem][n_elem] c128 scratch
-  void* dF = nullptr;               // [n_freq][n_elem][n_elem] field precision
+  void* dF = nullptr;               // [n_freq][max(n_t, n_elem)][n_elem] field precision
+  double2* W = nullptr;             // [n_freq][n_tx][n_elem] plane-wave weights
+  double2* WhW = nullptr;           // [n_freq][n_elem][n_elem] W^H W
+  double2* dpw = nullptr;           // [n_freq][n_tx][n_elem] plane-wave data / residual
+  double2* dsyn = nullptr;          // [n_freq][n_elem][n_elem] synthesis scratch
   void* jsplit = nullptr;           // split-K partials of pixel contractions
   int jsplit_n = 0;
   void* zpart = nullptr;            // per-(freq, e-block) partials of J^H
@@ -112,6 +119,10 @@ fwi_status adjoint_sources_conj(fwi_ctx* c, void* out);
 fwi_status assemble_gradient(fwi_ctx* c, void* grad);
 fwi_status jac_forward(fwi_ctx* c, const void* a_c128, double2* y);
 fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z);
+// plane-wave synthesis out[l] = op(A[l]) in[l] (op: A, or A^H when herm),
+// op(A[l]) of R x K, in[l] of K x n_elem; conj_out (field precision) or NULL
+fwi_status synth(fwi_ctx* c, const double2* A, int herm, int R, int K, const double2* in,
+                 double2* out, void* conj_out);
 fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u);
 fwi_status admm_step(fwi_ctx* c, void* m, void* g, void* u, const void* grad,
                      const fwi_admm_params* p, double* sos);

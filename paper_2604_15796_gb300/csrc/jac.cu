@@ -404,6 +404,51 @@ template <typename T> struct Jac {
 
 }  // namespace
 
+// Plane-wave synthesis in data space: out[l][r][j] = sum_k op(A)[l][r][k]
+// in[l][k][j], op(A) = A (stored [l][R][K]) or, herm, A^H (A stored
+// [l][K][R]).  The matrices are small (N_T, n_elem of a few hundred), so one
+// thread per output entry with a fixed-order FP64 sum; conj_out (field
+// precision, optional) receives conj(out) for the adjoint sources.
+template <typename T>
+__global__ void synth_kernel(double2* __restrict__ out, cplx<T>* __restrict__ conj_out,
+                             const double2* __restrict__ A, const double2* __restrict__ in,
+                             int R, int K, int J, int herm, long long total) {
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % J);
+    const long long t = idx / J;
+    const int r = (int)(t % R);
+    const long long l = t / R;
+    const double2* Al = A + l * (long long)R * K;
+    const double2* il = in + l * (long long)K * J;
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < K; ++k) {
+      const double2 a = herm ? Al[(long long)k * R + r] : Al[(long long)r * K + k];
+      const double ay = herm ? -a.y : a.y;
+      const double2 b = il[(long long)k * J + j];
+      sx += a.x * b.x - ay * b.y;
+      sy += a.x * b.y + ay * b.x;
+    }
+    out[idx] = make_double2(sx, sy);
+    if (conj_out) conj_out[idx] = mk<T>((T)sx, (T)(-sy));
+  }
+}
+
+fwi_status synth(fwi_ctx* c, const double2* A, int herm, int R, int K, const double2* in,
+                 double2* out, void* conj_out) {
+  const long long total = (long long)c->n_freq * R * c->n_elem;
+  const int nb = blocks_for(total, 256, c->n_sm * 8);
+  Prof p(c, KC_MISC);
+  if (c->fp64)
+    synth_kernel<double><<<nb, 256, 0, c->stream>>>(out, (cplx<double>*)conj_out, A, in, R, K,
+                                                     c->n_elem, herm, total);
+  else
+    synth_kernel<float><<<nb, 256, 0, c->stream>>>(out, (cplx<float>*)conj_out, A, in, R, K,
+                                                    c->n_elem, herm, total);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
 // Layout of c->red: [0, n_freq) per-frequency scales k_l^2 dV; then misfit
 // block partials.
 static inline double* misfit_parts(fwi_ctx* c) { return c->red + c->n_freq; }
@@ -415,11 +460,16 @@ template <typename T> static fwi_status project_data_t(fwi_ctx* c, void* data_ou
   st = Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->mF,
                         (const cplx<T>*)c->p0, c->dres);
   if (st != FWI_OK) return st;
+  // plane-wave transmits: data of transmit i = sum_e w_{l,i,e} (point data of e)
+  if (c->n_tx > 0) {
+    st = synth(c, c->W, 0, c->n_tx, c->n_elem, c->dres, c->dpw, nullptr);
+    if (st != FWI_OK) return st;
+  }
   if (data_out) {
-    const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
+    const long long nd = (long long)c->n_freq * c->n_t * c->n_elem;
     Prof p(c, KC_MISC);
     to_field_kernel<T><<<blocks_for(nd, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-        (cplx<T>*)data_out, c->dres, nd);
+        (cplx<T>*)data_out, c->n_tx > 0 ? c->dpw : c->dres, nd);
     FWI_CUDA(c, cudaGetLastError());
   }
   return FWI_OK;
@@ -431,14 +481,22 @@ fwi_status project_data(fwi_ctx* c, const void* m, void* data_out) {
 }
 
 template <typename T> static fwi_status residual_t(fwi_ctx* c, const void* d_obs, double* misfit) {
-  const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
-  // c->dres holds F(m); overwrite with r = F(m) - d_obs, conj(r) into dF
+  const long long nd = (long long)c->n_freq * c->n_t * c->n_elem;
+  // c->dres (plane waves: c->dpw) holds F(m); overwrite with r = F(m) - d_obs,
+  // conj(r) into dF
+  double2* d = c->n_tx > 0 ? c->dpw : c->dres;
   {
     Prof p(c, KC_MISC);
     residual_kernel<T><<<kMisfitBlocks, 256, 0, c->stream>>>(
-        c->dres, (cplx<T>*)c->dF, c->dres, (const cplx<T>*)d_obs, nd, misfit_parts(c));
+        d, (cplx<T>*)c->dF, d, (const cplx<T>*)d_obs, nd, misfit_parts(c));
   }
   FWI_CUDA(c, cudaGetLastError());
+  // plane waves: the point-source residual of the chain rule, y = W^H r, into
+  // dres and conj(y) into dF (the adjoint sources read dF)
+  if (c->n_tx > 0) {
+    fwi_status st = synth(c, c->W, 1, c->n_elem, c->n_tx, c->dpw, c->dres, c->dF);
+    if (st != FWI_OK) return st;
+  }
   if (misfit) {
     FWI_CUDA(c, cudaMemcpyAsync(c->h_red, misfit_parts(c), sizeof(double) * kMisfitBlocks,
                                 cudaMemcpyDeviceToHost, c->stream));

@@ -26,7 +26,7 @@ double ms_between(Clock::time_point a, Clock::time_point b) {
 struct Request {
   long long id = 0;
   fwi_problem_desc desc{};
-  std::vector<double> elem, freq, sos0, sos_out;
+  std::vector<double> elem, freq, tx, sos0, sos_out;
   std::vector<char> d_obs;
   fwi_admm_params admm{};
   int n_iter = 1;
@@ -44,9 +44,10 @@ size_t request_bytes(const fwi_problem_desc& d, long long n, size_t csz, size_t&
   ws = fwi_workspace_bytes(&d);
   if (ws == 0) return 0;
   const size_t ne = (size_t)d.n_elem;
+  const size_t nt = d.n_tx > 0 ? (size_t)d.n_tx : ne;  // transmits N_T
   const size_t vec = (size_t)n * (16 /*m*/ + 16 /*grad*/ + 8 /*sos*/ + 8 /*sos0*/ +
                                   2 * (size_t)d.dim * 16 /*g, u*/);
-  return ws + vec + (size_t)d.n_freq * ne * ne * csz + (1 << 20);
+  return ws + vec + (size_t)d.n_freq * nt * ne * csz + (1 << 20);
 }
 
 }  // namespace
@@ -82,6 +83,7 @@ void run_request(fwi_server* srv, Request& r) {
     if (fail_cuda(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) break;
     r.desc.elem_pos = r.elem.data();
     r.desc.freq_hz = r.freq.data();
+    r.desc.tx_angle = r.tx.empty() ? nullptr : r.tx.data();
     status = fwi_create(&r.desc, st, &ctx);
     if (status != FWI_OK) break;
     const size_t nd = r.d_obs.size();
@@ -210,16 +212,19 @@ fwi_status fwi_server_submit(fwi_server* s, const fwi_request* r, long long* id)
   if (!s || !r || !id || !r->sos0 || !r->d_obs || r->n_iter < 1 || r->admm.m_ref)
     return fail(nullptr, FWI_ERR_INVALID_ARG, "bad request");
   const fwi_problem_desc& d = r->problem;
-  if (!d.elem_pos || !d.freq_hz || d.n_elem <= 0 || d.n_freq <= 0 || (d.dim != 2 && d.dim != 3))
+  if (!d.elem_pos || !d.freq_hz || d.n_elem <= 0 || d.n_freq <= 0 || (d.dim != 2 && d.dim != 3) ||
+      d.n_tx < 0 || (d.n_tx > 0 && !d.tx_angle))
     return fail(nullptr, FWI_ERR_INVALID_ARG, "bad request problem descriptor");
   auto q = std::make_shared<Request>();
   q->desc = d;
   q->elem.assign(d.elem_pos, d.elem_pos + (size_t)d.n_elem * d.dim);
   q->freq.assign(d.freq_hz, d.freq_hz + d.n_freq);
+  if (d.n_tx > 0) q->tx.assign(d.tx_angle, d.tx_angle + d.n_tx);
   q->n = (long long)d.n[0] * (d.dim == 3 ? d.n[1] : 1) * d.n[2];
   q->csz = (d.precision == FWI_FP64) ? 16 : 8;
   q->sos0.assign(r->sos0, r->sos0 + q->n);
-  const size_t nd = (size_t)d.n_freq * d.n_elem * d.n_elem * q->csz;
+  const size_t nt = d.n_tx > 0 ? (size_t)d.n_tx : (size_t)d.n_elem;
+  const size_t nd = (size_t)d.n_freq * nt * d.n_elem * q->csz;
   q->d_obs.assign((const char*)r->d_obs, (const char*)r->d_obs + nd);
   q->admm = r->admm;
   q->n_iter = r->n_iter;

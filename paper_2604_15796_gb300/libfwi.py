@@ -37,7 +37,8 @@ class fwi_problem_desc(Structure):
     _fields_ = [("dim", c_int), ("n", c_int * 3), ("h", c_double), ("c0", c_double),
                 ("n_elem", c_int), ("elem_pos", POINTER(c_double)), ("n_freq", c_int),
                 ("freq_hz", POINTER(c_double)), ("krylov_tol", c_double),
-                ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int)]
+                ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int),
+                ("n_tx", c_int), ("tx_angle", POINTER(c_double))]
 
 
 class fwi_solve_info(Structure):
@@ -182,8 +183,10 @@ class FwiError(RuntimeError):
 
 
 def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-              max_batch=0):
+              max_batch=0, tx_angles=None):
     """fwi_problem_desc from array-order ``shape`` ((Nz, Nx) or (Nz, Ny, Nx)).
+    ``tx_angles``: steering angles [rad] of plane-wave transmits, or None for
+    point transmits at every element.
     Returns (desc, keepalive) -- keep the second item alive while desc is used."""
     dim = len(shape)
     elem = np.ascontiguousarray(elem, dtype=np.float64)
@@ -201,7 +204,12 @@ def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1
     d.freq_hz = freqs.ctypes.data_as(POINTER(c_double))
     d.krylov_tol, d.krylov_max_it = tol, max_it
     d.precision, d.max_batch = precision, max_batch
-    return d, (elem, freqs)
+    tx = None
+    if tx_angles is not None and len(tx_angles) > 0:
+        tx = np.ascontiguousarray(tx_angles, dtype=np.float64)
+        d.n_tx = tx.shape[0]
+        d.tx_angle = tx.ctypes.data_as(POINTER(c_double))
+    return d, (elem, freqs, tx)
 
 
 def _ptr(t):
@@ -253,7 +261,7 @@ class Context:
     FWI_MIXED, complex128 for FWI_FP64; m, grad, g, u always complex128)."""
 
     def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
-                 max_it=1000, max_batch=0, stream=None):
+                 max_it=1000, max_batch=0, stream=None, tx_angles=None):
         import torch
         self.torch = torch
         self.shape = tuple(shape)
@@ -262,10 +270,12 @@ class Context:
         self.n_elem = int(np.asarray(elem).shape[0])
         self.n_freq = int(len(freqs))
         self.n_rhs = self.n_elem * self.n_freq
+        # transmits N_T: plane waves (tx_angles) or one point source per element
+        self.n_t = len(tx_angles) if tx_angles is not None and len(tx_angles) > 0 else self.n_elem
         self.precision = precision
         self.field_dtype = torch.complex128 if precision == FWI_FP64 else torch.complex64
         self.desc, self._keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it,
-                                          max_batch)
+                                          max_batch, tx_angles)
         self.workspace_bytes = int(fwi_workspace_bytes(byref(self.desc)))
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -289,14 +299,15 @@ class Context:
         return _dev(t, self.field_dtype, self.n_rhs * self.n, name, optional)
 
     def _data(self, t, name, optional=False):
-        return _dev(t, self.field_dtype, self.n_freq * self.n_elem ** 2, name, optional)
+        return _dev(t, self.field_dtype, self.n_freq * self.n_t * self.n_elem, name, optional)
 
     def empty_fields(self):
         return self.torch.empty((self.n_freq, self.n_elem) + self.shape,
                                 dtype=self.field_dtype, device="cuda")
 
     def empty_data(self):
-        return self.torch.empty((self.n_freq, self.n_elem, self.n_elem),
+        """[n_freq][N_T][n_elem]: transmits x receivers per frequency."""
+        return self.torch.empty((self.n_freq, self.n_t, self.n_elem),
                                 dtype=self.field_dtype, device="cuda")
 
     def close(self):
@@ -431,7 +442,7 @@ class Context:
         self._check(fwi_reset_stats(self.handle))
 
     def jac_forward(self, a):
-        y = self.torch.empty((self.n_freq, self.n_elem, self.n_elem),
+        y = self.torch.empty((self.n_freq, self.n_t, self.n_elem),
                              dtype=self.torch.complex128, device="cuda")
         self._check(fwi_jac_forward(self.handle, self._m(a, "a"), _ptr(y)))
         return y
@@ -439,8 +450,8 @@ class Context:
     def jac_adjoint(self, y):
         z = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
         self._check(fwi_jac_adjoint(self.handle,
-                                    _dev(y, self.torch.complex128, self.n_freq * self.n_elem ** 2,
-                                         "y"), _ptr(z)))
+                                    _dev(y, self.torch.complex128,
+                                         self.n_freq * self.n_t * self.n_elem, "y"), _ptr(z)))
         return z
 
 
@@ -457,21 +468,24 @@ class Server:
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
                gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-               max_batch=0):
+               max_batch=0, tx_angles=None):
         """Queue a reconstruction; host numpy inputs (sos0 float64 of ``shape``,
-        d_obs [n_freq][n_elem][n_elem], complex64 for FWI_MIXED and complex128
+        d_obs [n_freq][N_T][n_elem], complex64 for FWI_MIXED and complex128
         for FWI_FP64).  max_batch limits the right-hand sides per Krylov launch
-        (0: all).  Returns the request id."""
+        (0: all); tx_angles selects plane-wave transmits.  Returns the request
+        id."""
         req = fwi_request()
-        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch)
+        desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch,
+                               tx_angles)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
         d_obs = np.ascontiguousarray(d_obs, dtype=cdt)
-        n_elem, n_freq = int(np.asarray(elem).shape[0]), int(len(freqs))
-        if sos0.size != int(np.prod(shape)) or d_obs.size != n_freq * n_elem * n_elem:
+        n_elem, n_freq, n_t = int(np.asarray(elem).shape[0]), int(len(freqs)), int(desc.n_tx)
+        n_t = n_t if n_t > 0 else n_elem
+        if sos0.size != int(np.prod(shape)) or d_obs.size != n_freq * n_t * n_elem:
             raise ValueError(f"sos0 must hold {int(np.prod(shape))} values and d_obs "
-                             f"{n_freq} x {n_elem} x {n_elem}; got {sos0.shape}, {d_obs.shape}")
+                             f"{n_freq} x {n_t} x {n_elem}; got {sos0.shape}, {d_obs.shape}")
         req.sos0 = sos0.ctypes.data_as(POINTER(c_double))
         req.d_obs = d_obs.ctypes.data
         req.admm.lambda_, req.admm.rho, req.admm.gamma = lam, rho, gamma

@@ -180,6 +180,19 @@ def volume_3d(seed=1003):
                           inclusions=[1520.0, 1580.0], name="volume3d")
 
 
+def planewave_2d(seed=1005):
+    """The 2-D acquisition of the paper's numerical study (Sec. V-A): 64
+    elements at 0.78 mm pitch (49.9 mm aperture), 15 frequencies 0.2-3 MHz,
+    60 plane waves steered over [-60, 60] degrees, every element receiving.
+    Grid 384^2 at 0.13 mm (the aperture's width; 3.95 pixels per wavelength
+    at 3 MHz), texture sigma 10 m/s / 0.5 mm with a fluid (1520 m/s) and a
+    solid (1580 m/s) cyst standing in for the paper's cyst phantoms."""
+    w = tissue_phantom((384, 384), 0.13e-3, 64, 0.78e-3, np.linspace(0.2e6, 3.0e6, 15), seed,
+                       inclusions=[1520.0, 1580.0], name="planewave2d")
+    w.meta["tx_angles"] = np.deg2rad(np.linspace(-60.0, 60.0, 60))
+    return w
+
+
 def scaled(shape, h, n_elem, pitch, freqs, seed, **kw):
     """A downscaled workload with the tissue statistics (parity tests)."""
     return tissue_phantom(shape, h, n_elem, pitch, freqs, seed, **kw)

@@ -48,6 +48,31 @@ def test_workspace_bytes_and_argument_checks_without_gpu():
     del keep, keep2, keep3
 
 
+def test_plane_wave_descriptor_sizes_and_checks():
+    """Plane-wave transmits (n_tx > 0) add the weights, W^H W and the
+    data-space synthesis buffers to the workspace; n_tx > 0 without angles,
+    or a non-finite angle, is rejected (0 bytes)."""
+    import numpy as np
+    from paper_2604_15796_gb300 import build, libfwi
+    build.build()
+    elem = np.stack([np.linspace(-1e-3, 1e-3, 8), np.full(8, -1e-4)], axis=1)
+    d0, k0 = libfwi.make_desc((32, 32), 1e-4, 1540.0, elem, [1e6, 2e6])
+    ang = np.linspace(-1.0, 1.0, 12)
+    d1, k1 = libfwi.make_desc((32, 32), 1e-4, 1540.0, elem, [1e6, 2e6], tx_angles=ang)
+    assert d1.n_tx == 12
+    n0 = libfwi.fwi_workspace_bytes(ctypes.byref(d0))
+    n1 = libfwi.fwi_workspace_bytes(ctypes.byref(d1))
+    nf, nt, ne = 2, 12, 8
+    assert n1 - n0 >= nf * (2 * nt * ne + 2 * ne * ne) * 16
+    d1.tx_angle = None
+    assert libfwi.fwi_workspace_bytes(ctypes.byref(d1)) == 0
+    bad_ang = ang.copy()
+    bad_ang[3] = np.nan
+    d2, k2 = libfwi.make_desc((32, 32), 1e-4, 1540.0, elem, [1e6], tx_angles=bad_ang)
+    assert libfwi.fwi_workspace_bytes(ctypes.byref(d2)) == 0
+    del k0, k1, k2
+
+
 def test_binding_rejects_tensors_that_do_not_match_the_documented_layout():
     """The binding checks device, dtype, element count and contiguity of a
     tensor argument before its pointer reaches the library (CPU tensors:
