@@ -27,19 +27,16 @@ Discretisation (readings):
 """
 import numpy as np
 
-from . import green, model, operator
+from . import model, operator
 
 
 def receiver_rows(prob):
-    """R_{l,j}(n) = k_l^2 dV G_l(x_j, x_n).  [N_F, N_R, *shape]."""
-    x = model.pixel_centres(prob.shape, prob.h)
-    r = np.sqrt(((x[None, :, :] - prob.elem[:, None, :]) ** 2).sum(-1))
-    out = np.empty((prob.n_freq, prob.n_elem) + tuple(prob.shape),
-                   dtype=np.complex128)
-    for l, k in enumerate(model.wavenumbers(prob)):
-        out[l] = (k * k * prob.cell_volume) * green.green_point(
-            k, r, prob.dim).reshape((prob.n_elem,) + tuple(prob.shape))
-    return out
+    """R_{l,j}(n) = k_l^2 dV G_l(x_j, x_n), the receiver's sensing of pixel n
+    (for 3-D line elements the mean of G over the element, see
+    operator.element_green).  [N_F, N_R, *shape]."""
+    k = model.wavenumbers(prob)
+    g = operator.element_green(prob)
+    return g * (k * k * prob.cell_volume).reshape((-1,) + (1,) * (prob.dim + 1))
 
 
 def _flat(a, prob):

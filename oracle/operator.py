@@ -13,6 +13,7 @@ on the doubled lattice with zero padding and cropping.
 import numpy as np
 import scipy.fft as sfft
 import scipy.linalg as sla
+from scipy.integrate import quad_vec
 
 from . import green, model
 
@@ -68,17 +69,45 @@ def dense_A(m, prob, l):
     return np.eye(prob.n, dtype=np.complex128) - dense_K(prob, l) * m[None, :]
 
 
-def incident_fields(prob):
-    """p0_{e,l}(x_n) = G_l(x_n, x_e): a unit point source at each element
-    (reading: the paper fixes no source normalisation).  [N_F, N_E, *shape]."""
+def element_green(prob):
+    """Green's function of each element seen from every pixel,
+    [N_F, N_E, *shape].
+
+    Point elements: G_l(x_n, x_e).  3-D line elements (Sec. V-B: elements of
+    finite elevation, prob.extra["elem_length"] = L > 0 along y, centred on
+    the element position): the mean over the element,
+        (1 / L) int_{-L/2}^{L/2} G_l(x_n, x_e + s e_y) ds,
+    by adaptive quadrature over s (all pixels at once).  Reading: the mean
+    (not the integral) keeps the point element as the limit L -> 0; the same
+    mean is the transmit field and the receiver's sensing (Eq. 4's integral
+    over Omega_j up to the factor L, which the paper leaves open)."""
     x = model.pixel_centres(prob.shape, prob.h)
+    length = float(prob.extra.get("elem_length", 0.0))
+    out = np.empty((prob.n_freq, prob.n_elem) + tuple(prob.shape), dtype=np.complex128)
+    k = model.wavenumbers(prob)
+    if prob.dim == 3 and length > 0:
+        for e in range(prob.n_elem):
+            d0 = x - prob.elem[e][None, :]
+
+            def g(s, d0=d0):
+                r = np.sqrt(d0[:, 0] ** 2 + (d0[:, 1] - s) ** 2 + d0[:, 2] ** 2)
+                return np.stack([green.green_point(kl, r, 3) for kl in k])
+
+            val, _ = quad_vec(g, -0.5 * length, 0.5 * length, epsabs=0.0, epsrel=1e-12,
+                              norm="max", limit=4000)
+            out[:, e] = (val / length).reshape((prob.n_freq,) + tuple(prob.shape))
+        return out
     r = np.sqrt(((x[None, :, :] - prob.elem[:, None, :]) ** 2).sum(-1))
-    out = np.empty((prob.n_freq, prob.n_elem) + tuple(prob.shape),
-                   dtype=np.complex128)
-    for l, k in enumerate(model.wavenumbers(prob)):
-        out[l] = green.green_point(k, r, prob.dim).reshape(
-            (prob.n_elem,) + tuple(prob.shape))
+    for l, kl in enumerate(k):
+        out[l] = green.green_point(kl, r, prob.dim).reshape((prob.n_elem,) + tuple(prob.shape))
     return out
+
+
+def incident_fields(prob):
+    """p0_{e,l} = the element's Green's function (element_green): a unit
+    source at each element (reading: the paper fixes no source
+    normalisation).  [N_F, N_E, *shape]."""
+    return element_green(prob)
 
 
 def transmit_incident_fields(prob, weights):
