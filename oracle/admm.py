@@ -88,11 +88,15 @@ def cg(apply, b, n_iter):
 
 
 def normal_matrix_apply(a, fields, rfields, prob, params):
-    """A_k a = J^H J a + rho nabla^T nabla a + gamma a   (Eq. 12)."""
-    shape = prob.shape
+    """A_k a = J^H J a + rho nabla^T nabla a + gamma a   (Eq. 12), on the
+    inversion mesh: J acts on the prolonged vector and J^H is restricted
+    (J_inv = J P, model.prolong / model.restrict; identity when the meshes
+    coincide)."""
+    shape = model.inversion_shape(prob)
     a = np.asarray(a, dtype=np.complex128).reshape(shape)
-    out = inverse.jac_adjoint(inverse.jac_forward(a, fields, rfields, prob),
-                              fields, rfields, prob).reshape(shape)
+    af = model.prolong(a, prob)
+    out = model.restrict(inverse.jac_adjoint(inverse.jac_forward(af, fields, rfields, prob),
+                                             fields, rfields, prob).reshape(prob.shape), prob)
     out += params.rho * grad_op_T(grad_op(a, shape), shape)
     out += params.gamma * a
     return out
@@ -100,8 +104,9 @@ def normal_matrix_apply(a, fields, rfields, prob, params):
 
 def normal_rhs(m, g, u, grad, prob, params, m_ref=None):
     """b_k = J^H(d - F(m)) + rho nabla^T(g + u - nabla m) + gamma(m_ref - m)
-    (Eq. 12), with J^H(d - F(m)) = -grad."""
-    shape = prob.shape
+    (Eq. 12), with J^H(d - F(m)) = -grad; m, g, u, grad on the inversion
+    mesh."""
+    shape = model.inversion_shape(prob)
     m = np.asarray(m, dtype=np.complex128).reshape(shape)
     b = -np.asarray(grad, dtype=np.complex128).reshape(shape)
     b = b + params.rho * grad_op_T(np.asarray(g) + np.asarray(u)
@@ -125,8 +130,9 @@ def shrink(a, tau):
 def admm_tv_step(m, g, u, grad, fields, rfields, prob, params, m_ref=None):
     """One iteration of Algorithm 1 after the forward simulation and the
     gradient: Gauss-Newton m-step (Eq. 10-12), g-step (Eq. 13), u-step.
-    Returns (m_new, g_new, u_new, sos_new, dm)."""
-    shape = prob.shape
+    m, g, u, grad (and the results) live on the inversion mesh, the fields
+    on the forward mesh.  Returns (m_new, g_new, u_new, sos_new, dm)."""
+    shape = model.inversion_shape(prob)
     b = normal_rhs(m, g, u, grad, prob, params, m_ref)
     dm = cg(lambda v: normal_matrix_apply(v, fields, rfields, prob, params),
             b, params.n_cg)
@@ -148,9 +154,10 @@ def reconstruct(m0, d_obs, prob, params, n_iter, method="bicgstab", tol=1e-10, w
     k = 0, refresh_every, 2 refresh_every, ... and kept fixed in between
     (a Born approximation for the adjoint problem).  refresh_every = 1 is
     the strict distorted-Born Jacobian.  ``weights``: synthesised transmits
-    (plane waves, Sec. V-A).  Returns (m, g, u, sos, history) with
+    (plane waves, Sec. V-A).  The model lives on the inversion mesh
+    (model.prolong).  Returns (m, g, u, sos, history) with
     history[k] = (misfit, refreshed)."""
-    shape = prob.shape
+    shape = model.inversion_shape(prob)
     m = np.asarray(m0, dtype=np.complex128).reshape(shape).copy()
     g = grad_op(m, shape)
     u = np.zeros_like(g)
@@ -158,11 +165,11 @@ def reconstruct(m0, d_obs, prob, params, n_iter, method="bicgstab", tol=1e-10, w
     sos = model.sos_from_contrast(m, prob.c0)
     history = []
     for k in range(n_iter):
-        ref = inverse.gradient(m, d_obs, prob, method, tol, weights)
+        ref = inverse.gradient_inversion_mesh(m, d_obs, prob, method, tol, weights)
         refreshed = rfields is None or k % refresh_every == 0
         if refreshed:
-            rfields = inverse.receiver_fields(m, prob, method, tol)
-        m, g, u, sos, _ = admm_tv_step(m, g, u, ref["grad"], ref["fields"], rfields, prob,
+            rfields = inverse.receiver_fields(model.prolong(m, prob), prob, method, tol)
+        m, g, u, sos, _ = admm_tv_step(m, g, u, ref["grad_inv"], ref["fields"], rfields, prob,
                                        params, m_ref)
         history.append((ref["misfit"], refreshed))
     return m, g, u, sos, history

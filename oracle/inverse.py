@@ -177,3 +177,13 @@ def gradient(m, d_obs, prob, method="lu", tol=1e-10, weights=None):
     return dict(fields=fields, data=data, resid=resid,
                 misfit=misfit(data, d_obs), src=src, lam=lam,
                 grad=gradient_adjoint_state(fields, lam, prob))
+
+
+def gradient_inversion_mesh(m_inv, d_obs, prob, method="lu", tol=1e-10, weights=None):
+    """Gradient with respect to the contrast on the inversion mesh: the
+    forward model runs on the prolonged contrast, F(P m), and the gradient
+    is P^T J^H r (chain rule).  The dict of gradient() plus "grad_inv"."""
+    ref = gradient(model.prolong(m_inv, prob), d_obs, prob, method, tol, weights)
+    ref["grad_inv"] = model.restrict(ref["grad"], prob)
+    return ref
+

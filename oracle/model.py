@@ -126,3 +126,37 @@ def plane_wave_weights(prob, angles):
     s = np.sin(np.asarray(angles, dtype=np.float64))
     return np.exp(1j * k[:, None, None] * s[None, :, None] * xe[None, None, :])
 
+
+def inversion_factor(prob):
+    """r of the inversion mesh (prob.extra["inv_factor"], default 1)."""
+    return int(prob.extra.get("inv_factor", 1))
+
+
+def inversion_shape(prob):
+    """Shape of the inversion mesh: every axis of the forward mesh / r."""
+    r = inversion_factor(prob)
+    return tuple(s // r for s in prob.shape)
+
+
+def prolong(m_inv, prob):
+    """Contrast on the forward mesh from its vector on the inversion mesh
+    (Sec. IV: the forward mesh is finer than the inversion mesh).  Reading:
+    each inversion cell covers r^d forward pixels (r = inversion_factor)
+    and the contrast is constant over it."""
+    r = inversion_factor(prob)
+    m = np.asarray(m_inv).reshape(inversion_shape(prob))
+    for ax in range(m.ndim):
+        m = np.repeat(m, r, axis=ax)
+    return m
+
+
+def restrict(v, prob):
+    """Adjoint of prolong: the sum over the forward pixels of each
+    inversion cell (takes gradients and J^H products to the inversion
+    mesh)."""
+    r = inversion_factor(prob)
+    blocks = []
+    for s in inversion_shape(prob):
+        blocks += [s, r]
+    return np.asarray(v).reshape(blocks).sum(axis=tuple(range(1, 2 * len(prob.shape), 2)))
+
