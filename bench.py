@@ -45,7 +45,7 @@ def workload(name):
     from paper_2604_15796_gb300 import phantoms
     return {"thyroid256": phantoms.thyroid_256, "large512": phantoms.large_512,
             "volume3d": phantoms.volume_3d, "disc64": phantoms.disc_phantom,
-            "planewave2d": phantoms.planewave_2d}[name]()
+            "planewave2d": phantoms.planewave_2d, "elev3d": phantoms.elevation_3d}[name]()
 
 
 def describe(w):
@@ -53,14 +53,25 @@ def describe(w):
     tx = w.meta.get("tx_angles")
     txs = "" if tx is None else (f", {len(tx)} plane-wave transmits synthesised from the "
                                  f"{w.n_elem} element solves")
+    if w.meta.get("elem_length"):
+        txs += f", line elements of {w.meta['elem_length'] * 1e3:.0f} mm elevation"
     return (f"{w.name}: {grid} grid, h={w.h * 1e3:.2f} mm, {w.n_elem} elements x "
             f"{w.n_freq} freqs ({w.n_rhs} RHS){txs}, per step 1 forward + 1 adjoint BiCGSTAB "
             f"solve per RHS + data + gradient + ADMM-TV step (n_cg=10)")
 
 
-def kernel_source_hash():
+# the sources each kernel class is compiled from: the FFT operator passes
+# (row_*, col_*) and the pixel contractions (everything else)
+KERNEL_SOURCES = {"operator": ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "lsop_f32.cu"),
+                  "contraction": ("common.cuh", "jac.cu", "jac_tc.cu", "tc.cuh")}
+
+
+def kernel_source_hash(kernel="col_conv"):
+    """Hash of the sources of ``kernel``'s class (a recorded ncu figure is
+    used only while they are unchanged)."""
+    cls = "operator" if kernel.startswith(("row_", "col_")) else "contraction"
     h = hashlib.sha256()
-    for f in ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "jac.cu", "jac_tc.cu", "tc.cuh"):
+    for f in KERNEL_SOURCES[cls]:
         with open(os.path.join(ROOT, "paper_2604_15796_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -78,7 +89,7 @@ def recorded_traffic(kernel, wname):
     for line in open(path):
         m = pat.match(line.strip())
         if m and m.group(1) == kernel and m.group(2) == wname and \
-                m.group(5) == kernel_source_hash():
+                m.group(5) == kernel_source_hash(kernel):
             return float(m.group(3)), float(m.group(4))
     return None
 
@@ -141,17 +152,26 @@ def oracle_solves_per_s(w, budget_s=15.0, seed=0, keep=0):
     """FP64 oracle (numpy/scipy, all host cores) on a bounded sample of the
     workload: BiCGSTAB solves (tol 1e-10) of transmit/frequency pairs drawn
     from the workload at the benchmark's iterate m = 0.8 m_true, until the
-    time budget is spent.  The first ``keep`` solutions and their data rows
-    are returned for the accuracy check of the GPU result."""
+    time budget is spent.  Only the solves are timed (the right-hand sides,
+    like the device's incident fields, are setup).  The first ``keep``
+    solutions and their data rows are returned for the accuracy check of
+    the GPU result.  Line elements: the oracle's element quadrature takes
+    about a minute per element at full size, so the solves take point-source
+    right-hand sides (the same operator and iteration) and no solution is
+    kept.  Returns (rate, solves, solve seconds, kept, line elements)."""
     import oracle
     from oracle import inverse, model, operator
-    prob = oracle.Problem(tuple(w.shape), w.h, w.c0, w.elem, np.asarray(w.freqs))
+    line = float(w.meta.get("elem_length", 0.0)) > 0.0
+    extra = {"elem_length": 0.0 if line else float(w.meta.get("elem_length", 0.0))}
+    if line:
+        keep = 0
+    prob = oracle.Problem(tuple(w.shape), w.h, w.c0, w.elem, np.asarray(w.freqs), dict(extra))
     m = 0.8 * model.contrast_from_sos(w.sos, w.c0)
     rng = np.random.default_rng(seed)
     tx = w.meta.get("tx_angles")
     specs = {}
     kept = []
-    n, t0 = 0, time.perf_counter()
+    n, t0, t_solve = 0, time.perf_counter(), 0.0
     while True:
         l = int(rng.integers(0, w.n_freq))
         e = int(rng.integers(0, w.n_elem if tx is None else len(tx)))
@@ -160,26 +180,29 @@ def oracle_solves_per_s(w, budget_s=15.0, seed=0, keep=0):
         wrow = None
         if tx is None:
             sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem[[e]],
-                                 np.asarray([w.freqs[l]]))
+                                 np.asarray([w.freqs[l]]), dict(extra))
             b = operator.incident_fields(sub)[0, 0]
         else:
             # plane-wave transmit e, solved directly from its incident field
-            sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]))
+            sub = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]),
+                                 dict(extra))
             wl = model.plane_wave_weights(sub, [tx[e]])
             b = operator.transmit_incident_fields(sub, wl)[0, 0]
             wrow = wl[0, 0]
         spec = specs[l]
+        ts = time.perf_counter()
         x, _, _ = operator.bicgstab(lambda v: operator.apply_A(v.reshape(prob.shape), m, prob,
                                                               l, spec).ravel(), b.ravel(), 1e-10)
+        t_solve += time.perf_counter() - ts
         if len(kept) < keep:
-            subr = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]))
+            subr = oracle.Problem(prob.shape, prob.h, prob.c0, prob.elem, np.asarray([w.freqs[l]]),
+                                  dict(extra))
             row = inverse.forward_data(m, x.reshape((1, 1) + prob.shape), subr)[0, 0]
             kept.append((l, e, x.reshape(prob.shape), row, wrow))
         n += 1
         if time.perf_counter() - t0 > budget_s and n >= keep:
             break
-    dt = time.perf_counter() - t0
-    return n / dt, n, dt, kept
+    return n / t_solve, n, t_solve, kept, line
 
 
 def run_reference(args, rank):
@@ -190,7 +213,7 @@ def run_reference(args, rank):
     per_step = []
     solves = 0
     for i in range(args.warmup + args.steps):
-        rate, n, dt, _ = oracle_solves_per_s(w, budget_s=args.ref_step_s, seed=i)
+        rate, n, dt, _, _ = oracle_solves_per_s(w, budget_s=args.ref_step_s, seed=i)
         if i >= args.warmup:
             per_step.append(dt)
             solves += n
@@ -239,6 +262,7 @@ def run_ours(args, rank, world, samples):
     with torch.cuda.stream(stream):
         ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6, stream=stream,
                              tx_angles=w.meta.get("tx_angles"),
+                             elem_length=float(w.meta.get("elem_length", 0.0)),
                              max_batch=args.max_batch)
         if args.cuda_core_jacobian:
             ctx.set_jac_tensor_cores(False)
@@ -739,7 +763,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thyroid256",
                     choices=["thyroid256", "large512", "volume3d", "disc64", "planewave2d",
-                             "serving"])
+                             "elev3d", "serving"])
     ap.add_argument("--max-batch", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -776,11 +800,13 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         # oracle timed on the host cores before the GPU work starts
         w = workload(args.workload)
-        rate, n, dt, samples = oracle_solves_per_s(w, budget_s=args.cpu_budget_s,
-                                                   keep=args.check_samples)
+        rate, n, dt, samples, line = oracle_solves_per_s(w, budget_s=args.cpu_budget_s,
+                                                         keep=args.check_samples)
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} FP64 BiCGSTAB solves (tol 1e-10) of random transmit/frequency "
-                         f"pairs of {w.name}, {dt:.1f} s, scipy.fft over all host cores"}
+                         f"pairs of {w.name}, {dt:.1f} s of solves, scipy.fft over all host "
+                         f"cores" + ("; point-source right-hand sides on the line-element "
+                                     "workload's operator" if line else "")}
     line = run_ours(args, rank, world, samples)
     if rank == 0:
         line["cpu_baseline"] = cpu

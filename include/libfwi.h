@@ -97,6 +97,19 @@ typedef struct fwi_problem_desc {
   int n_tx;
   const double* tx_angle;  /* host [n_tx] steering angles [rad] or NULL when
                               n_tx = 0; copied in fwi_create */
+  double elem_length;      /* 3D: length of each element along y [m] (finite
+                              elevation, Sec. V-B); 0 = point elements.  A
+                              line element transmits and senses the mean of
+                              the point Green's function over its length
+                              (centred on elem_pos).  Ignored when dim == 2. */
+  int inv_factor;          /* inversion mesh (Sec. IV): cells of inv_factor^dim
+                              forward pixels (<= 1: the forward mesh).  Each
+                              of Nx, Nz (and Ny in 3D) must be a multiple.
+                              The contrast m, its gradient, J's input a and
+                              J^H's output z, the TV variables g, u, m_ref
+                              and sos are then [N_inv] = N / inv_factor^dim
+                              on the inversion mesh (contrast constant over a
+                              cell; gradients summed over its pixels). */
 } fwi_problem_desc;
 
 /* Per-call Krylov report.  The caller sets n_rhs and the optional host

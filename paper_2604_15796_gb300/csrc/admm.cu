@@ -252,9 +252,9 @@ inline int blocks_for(long long n, int threads, int cap) {
 }  // namespace
 
 fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u) {
-  Grid3 G{c->nx, c->ny, c->nz, c->N};
+  Grid3 G{c->inx, c->iny, c->inz, c->Ninv};  // inversion mesh
   Prof pf(c, KC_ADMM);
-  admm_init_kernel<<<blocks_for(c->N, 256, kRedBlocks), 256, 0, c->stream>>>(
+  admm_init_kernel<<<blocks_for(c->Ninv, 256, kRedBlocks), 256, 0, c->stream>>>(
       (double2*)g, (double2*)u, (const double2*)m0, G, c->dim);
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
@@ -268,7 +268,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   double2* g = (double2*)gv;
   double2* u = (double2*)uv;
   const double2* grad = (const double2*)gradv;
-  Grid3 G{c->nx, c->ny, c->nz, c->N};
+  Grid3 G{c->inx, c->iny, c->inz, c->Ninv};  // inversion mesh
   const int dim = c->dim;
   const int nb = kRedBlocks;
   double* part = c->red + c->n_freq + 256;
@@ -284,7 +284,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   const double rho = p->rho, gamma = p->gamma;
   {
     Prof pf(c, KC_ADMM);
-    w_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(w, g, u, m, G, dim);
+    w_kernel<<<blocks_for(c->Ninv, 256, nb), 256, 0, s>>>(w, g, u, m, G, dim);
   }
   FWI_CUDA(c, cudaGetLastError());
   {
@@ -321,7 +321,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
     }
     {
       Prof pf(c, KC_ADMM);
-      xr_kernel<<<nb, 256, 0, s>>>(x, r, d, q, sc, c->N, part);
+      xr_kernel<<<nb, 256, 0, s>>>(x, r, d, q, sc, c->Ninv, part);
     }
     {
       Prof pf(c, KC_ADMM);
@@ -329,19 +329,19 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
     }
     {
       Prof pf(c, KC_ADMM);
-      d_kernel<<<nb, 256, 0, s>>>(d, r, sc, c->N);
+      d_kernel<<<nb, 256, 0, s>>>(d, r, sc, c->Ninv);
     }
     FWI_CUDA(c, cudaGetLastError());
   }
   {
     Prof pf(c, KC_ADMM);
-    add_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(m, x, c->N);
+    add_kernel<<<blocks_for(c->Ninv, 256, nb), 256, 0, s>>>(m, x, c->Ninv);
   }
   const double tau = p->lambda / p->rho;
   const double step = p->dual_step > 0.0 ? p->dual_step : p->rho;
   {
     Prof pf(c, KC_ADMM);
-    shrink_dual_kernel<<<blocks_for(c->N, 256, nb), 256, 0, s>>>(g, u, m, sos, tau, step, c->c0,
+    shrink_dual_kernel<<<blocks_for(c->Ninv, 256, nb), 256, 0, s>>>(g, u, m, sos, tau, step, c->c0,
                                                                G, dim);
   }
   FWI_CUDA(c, cudaGetLastError());

@@ -39,6 +39,8 @@ bool fft_len_ok(int L) {
 struct Layout {
   int dim, nx, ny, nz, lx, ly, lz, rows, n_elem, n_freq, n_rhs, batch, ntiles, split;
   int n_tx, n_t;  // plane-wave transmits (0: point transmits); N_T
+  int rf, ry;     // inversion-mesh cell (rf x ry x rf pixels)
+  long long Ninv;
   long long N;
   size_t csz;
   size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec, b_tc;
@@ -67,6 +69,10 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
     return bad("n_tx must be >= 0, with tx_angle when positive");
   for (int i = 0; i < d->n_tx; ++i)
     if (!std::isfinite(d->tx_angle[i])) return bad("tx_angle must be finite");
+  if (!(d->elem_length >= 0) || !std::isfinite(d->elem_length))
+    return bad("elem_length must be finite and >= 0");
+  L.rf = d->inv_factor > 1 ? d->inv_factor : 1;
+  L.ry = (d->dim == 3) ? L.rf : 1;
   L.n_elem = d->n_elem; L.n_freq = d->n_freq;
   L.n_tx = d->n_tx;
   L.n_t = d->n_tx > 0 ? d->n_tx : d->n_elem;
@@ -83,6 +89,9 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
     if (L.batch > cap) L.batch = (int)cap;
   }
   L.rows = L.ny * L.nz;
+  if (L.nx % L.rf || L.nz % L.rf || L.ny % L.ry)
+    return bad("every grid size must be a multiple of inv_factor");
+  L.Ninv = L.N / ((long long)L.rf * L.rf * L.ry);
   L.csz = (d->precision == FWI_FP64) ? 16 : 8;
   const int lpc = (d->precision == FWI_FP64) ? Lsop<double>::row_lines_per_cta(L.lx)
                                              : Lsop<float>::row_lines_per_cta(L.lx);
@@ -111,6 +120,7 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.b_jsplit = js1 > js2 ? js1 : js2;
   L.b_zpart = (size_t)L.n_freq * nbe * L.N * L.csz;
   L.b_vec = (size_t)L.N * L.csz * 2 + (size_t)8 * L.N * 16 + (size_t)3 * L.dim * L.N * 16 +
+            (L.rf > 1 ? (size_t)L.N * 16 : 0) +
             sizeof(double) * (L.n_freq + 256 + 512 + 16);
   L.b_tc = (d->precision == FWI_FP64) ? 0 : tc_bops_bytes(L.n_elem, L.n_freq);
   L.total = L.b_ghat + 4 * L.b_field + 5 * L.b_kv + L.b_plane1 + L.b_plane2 + L.b_small +
@@ -141,7 +151,7 @@ static void release(fwi_ctx* c) {
   void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
-                  c->W, c->WhW, c->dpw, c->dsyn,
+                  c->W, c->WhW, c->dpw, c->dsyn, c->vfwd,
                   c->jsplit, c->zpart, c->aF, c->red, c->tc_bops, c->tc_err};
   // stream-ordered frees: no device-wide synchronisation, so a context can be
   // retired while other contexts' work runs
@@ -205,6 +215,13 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   c->n_tx = L.n_tx;
   c->n_t = L.n_t;
   if (L.n_tx > 0) c->tx_angle.assign(d->tx_angle, d->tx_angle + L.n_tx);
+  c->elem_length = (L.dim == 3) ? d->elem_length : 0.0;
+  c->rf = L.rf;
+  c->ry = L.ry;
+  c->inx = L.nx / L.rf;
+  c->iny = L.ny / L.ry;
+  c->inz = L.nz / L.rf;
+  c->Ninv = L.Ninv;
   c->stream = (cudaStream_t)stream;
   c->bytes = L.total;
   cudaError_t e = cudaGetDevice(&c->device);
@@ -250,6 +267,7 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   alloc(&c->aF, (size_t)L.N * L.csz);
   for (int i = 0; i < 6; ++i) alloc((void**)&c->vN[i], (size_t)L.N * 16);
   alloc((void**)&c->vD[0], (size_t)L.dim * L.N * 16);
+  if (L.rf > 1) alloc((void**)&c->vfwd, (size_t)L.N * 16);
   c->red_n = L.n_freq + 256 + 512 + 16;
   alloc((void**)&c->red, sizeof(double) * c->red_n);
   alloc(&c->tc_bops, L.b_tc);

@@ -27,6 +27,10 @@ struct fwi_ctx {
   // plane-wave transmits (0: point transmits at every element); n_t = N_T
   int n_tx = 0, n_t = 0;
   std::vector<double> tx_angle;
+  double elem_length = 0;           // 3D line elements along y (0: points)
+  // inversion mesh: cells of rf x ry x rf pixels (ry = 1 in 2D)
+  int rf = 1, ry = 1, inx = 0, iny = 1, inz = 0;
+  long long Ninv = 0;
   // ---- device ----
   cudaStream_t stream = nullptr;
   cudaStream_t own_stream = nullptr;  // created when the caller passes NULL
@@ -67,6 +71,7 @@ struct fwi_ctx {
   void* aF = nullptr;               // [N] field-precision vector
   double2* vN[8] = {};              // [N] c128 ADMM / CG vectors
   double2* vD[3] = {};              // [dim][N] c128 ADMM vectors
+  double2* vfwd = nullptr;          // [N] c128 forward-mesh scratch (inversion mesh only)
   void* tc_bops = nullptr;          // tensor-core J^H: B operand stages (FP32 only)
   int* tc_err = nullptr;            // error word of the tensor-core kernels
   int* h_tc_err = nullptr;          // pinned host mirror

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "mesh.cuh"
 #include "prof.cuh"
 
 namespace fwi {
@@ -449,6 +450,17 @@ fwi_status synth(fwi_ctx* c, const double2* A, int herm, int R, int K, const dou
   return FWI_OK;
 }
 
+// Inversion mesh: forward-mesh results written to c->vfwd are summed over
+// each cell into out (no-op on the forward mesh, where they went to out).
+static fwi_status to_inversion_mesh(fwi_ctx* c, double2* out) {
+  if (c->rf == 1) return FWI_OK;
+  Prof p(c, KC_MISC);
+  restrict_kernel<<<blocks_for(c->Ninv, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      out, c->vfwd, c->nx, c->ny, c->rf, c->ry, c->Ninv);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
 // Layout of c->red: [0, n_freq) per-frequency scales k_l^2 dV; then misfit
 // block partials.
 static inline double* misfit_parts(fwi_ctx* c) { return c->red + c->n_freq; }
@@ -549,11 +561,13 @@ template <typename T> static fwi_status gradient_t(fwi_ctx* c, void* grad) {
         part, (const cplx<T>*)c->fields, (const cplx<T>*)c->lam, c->n_rhs, per, c->N);
   }
   FWI_CUDA(c, cudaGetLastError());
-  Prof p(c, KC_MISC);
-  grad_reduce_kernel<<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-      (double2*)grad, part, ns, c->N);
+  {
+    Prof p(c, KC_MISC);
+    grad_reduce_kernel<<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+        c->rf > 1 ? c->vfwd : (double2*)grad, part, ns, c->N);
+  }
   FWI_CUDA(c, cudaGetLastError());
-  return FWI_OK;
+  return to_inversion_mesh(c, (double2*)grad);
 }
 
 fwi_status assemble_gradient(fwi_ctx* c, void* grad) {
@@ -566,8 +580,12 @@ template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a,
   if (st != FWI_OK) return st;
   {
     Prof p(c, KC_MISC);
-    to_field_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
-        (cplx<T>*)c->aF, (const double2*)a, c->N);
+    if (c->rf > 1)
+      prolong_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+          (cplx<T>*)c->aF, (const double2*)a, c->nx, c->ny, c->rf, c->ry, c->N);
+    else
+      to_field_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+          (cplx<T>*)c->aF, (const double2*)a, c->N);
   }
   FWI_CUDA(c, cudaGetLastError());
   return Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
@@ -579,9 +597,12 @@ fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {
 }
 
 // (J^H b)_n = sum_l k_l^2 dV sum_e conj(p_e(n)) sum_j conj(p_j(n)) b_ej
-template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2* y, double2* z) {
+template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2* y,
+                                                      double2* z_out) {
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
+  // forward-mesh result, summed over the inversion cells at the end
+  double2* z = c->rf > 1 ? c->vfwd : z_out;
   if constexpr (std::is_same<T, float>::value) {
     if (tc_usable(c)) {
       const int np = tc_jh_partials(c, y, (const float2*)c->fields, (float2*)c->zpart);
@@ -590,7 +611,7 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
       sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
           z, (const cplx<T>*)c->zpart, np, c->N, 0);
       FWI_CUDA(c, cudaGetLastError());
-      return FWI_OK;
+      return to_inversion_mesh(c, z_out);
     }
   }
   const long long nd = (long long)c->n_freq * c->n_elem * c->n_elem;
@@ -614,7 +635,7 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
   sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
       z, (const cplx<T>*)c->zpart, c->n_freq * nbe, c->N, 0);
   FWI_CUDA(c, cudaGetLastError());
-  return FWI_OK;
+  return to_inversion_mesh(c, z_out);
 }
 
 fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z) {

@@ -220,7 +220,10 @@ fwi_status fwi_server_submit(fwi_server* s, const fwi_request* r, long long* id)
   q->elem.assign(d.elem_pos, d.elem_pos + (size_t)d.n_elem * d.dim);
   q->freq.assign(d.freq_hz, d.freq_hz + d.n_freq);
   if (d.n_tx > 0) q->tx.assign(d.tx_angle, d.tx_angle + d.n_tx);
-  q->n = (long long)d.n[0] * (d.dim == 3 ? d.n[1] : 1) * d.n[2];
+  // the request's model vectors (m, g, u, grad, sos) live on the inversion mesh
+  const long long rfac = d.inv_factor > 1 ? d.inv_factor : 1;
+  q->n = (long long)d.n[0] * (d.dim == 3 ? d.n[1] : 1) * d.n[2] /
+         (rfac * rfac * (d.dim == 3 ? rfac : 1));
   q->csz = (d.precision == FWI_FP64) ? 16 : 8;
   q->sos0.assign(r->sos0, r->sos0 + q->n);
   const size_t nt = d.n_tx > 0 ? (size_t)d.n_tx : (size_t)d.n_elem;

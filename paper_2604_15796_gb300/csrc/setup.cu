@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ctx.cuh"
+#include "mesh.cuh"
 #include "prof.cuh"
 
 namespace fwi {
@@ -137,6 +138,103 @@ __global__ void incident_kernel(cplx<T>* p0, const double* elem, const double* k
   }
 }
 
+// Gauss-Legendre rule on [-1, 1] (12 points) for the element quadrature.
+struct GaussRule { double x[12], w[12]; };
+
+// Nodes by Newton's method on P_12 (three-term recurrence), weights
+// 2 / ((1 - x^2) P_12'(x)^2).
+GaussRule gauss_legendre12() {
+  const int n = 12;
+  const double PI = 3.141592653589793238462643383279502884;
+  GaussRule g;
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 64; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int j = 2; j <= n; ++j) {
+        const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      const double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    g.x[i] = x;
+    g.w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+  return g;
+}
+
+// Mean over a line element (length L along y, offset dy of the pixel along
+// the element, distance rho from its axis) of exp(ikr) / (4 pi r).  With
+// v = rho sinh t along the element, r = rho cosh t and dv / r = dt:
+//   (1 / (4 pi L)) int_{t1}^{t2} exp(i k rho cosh t) dt,
+// an entire integrand.  The integrand is even in t; panels end where the
+// phase has advanced by 2 pi or t by 1, 12-point Gauss-Legendre on each
+// (at most 4096 panels).
+__device__ double2 line_mean_green(double k, double rho, double dy, double L,
+                                   const GaussRule& g) {
+  const double PI = 3.141592653589793238462643383279502884;
+  const double a = asinh((-0.5 * L - dy) / rho), b = asinh((0.5 * L - dy) / rho);
+  const double kr = k * rho, dphase = 2.0 * PI / kr;
+  double re = 0.0, im = 0.0;
+  auto piece = [&](double t0, double t1) {  // 0 <= t0 <= t1
+    double t = t0;
+    for (int p = 0; p < 4096 && t < t1; ++p) {
+      double tn = acosh(cosh(t) + dphase);
+      tn = fmin(fmin(tn, t + 1.0), t1);
+      const double hw = 0.5 * (tn - t), mid = 0.5 * (tn + t);
+      for (int q = 0; q < 12; ++q) {
+        double s, c;
+        sincos(kr * cosh(mid + hw * g.x[q]), &s, &c);
+        re += g.w[q] * hw * c;
+        im += g.w[q] * hw * s;
+      }
+      t = tn;
+    }
+  };
+  if (a >= 0.0) {
+    piece(a, b);
+  } else if (b <= 0.0) {
+    piece(-b, -a);
+  } else {
+    piece(0.0, -a);
+    piece(0.0, b);
+  }
+  const double f = 1.0 / (4.0 * PI * L);
+  return make_double2(re * f, im * f);
+}
+
+// Incident fields of 3-D line elements (finite elevation along y).
+template <typename T>
+__global__ void incident_line_kernel(cplx<T>* p0, const double* elem, const double* kw,
+                                     int n_elem, int n_freq, int nx, int ny, int nz, double h,
+                                     double L, GaussRule g) {
+  const long long N = (long long)nx * ny * nz;
+  const long long total = N * n_elem * n_freq;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const long long n = id % N;
+    const long long le = id / N;
+    const int e = (int)(le % n_elem);
+    const int l = (int)(le / n_elem);
+    const int ix = (int)(n % nx);
+    const long long q = n / nx;
+    const int iy = (int)(q % ny);
+    const int iz = (int)(q / ny);
+    const double dx = (ix + 0.5 - 0.5 * nx) * h - elem[3 * e];
+    const double dy = (iy + 0.5 - 0.5 * ny) * h - elem[3 * e + 1];
+    const double dz = iz * h - elem[3 * e + 2];
+    // pixels on the element's axis would make the mean singular; the array
+    // sits outside the grid, so rho >= h there
+    const double rho = fmax(sqrt(dx * dx + dz * dz), 1e-3 * h);
+    const double2 v = line_mean_green(kw[l], rho, dy, L, g);
+    p0[id] = mk<T>((T)v.x, (T)v.y);
+  }
+}
+
 template <typename T>
 __global__ void convert_kernel(cplx<T>* dst, const double2* src, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -258,8 +356,13 @@ fwi_status setup_t(fwi_ctx* c) {
                         cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) {
     const long long total = c->N * c->n_rhs;
-    incident_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
-        (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
+    if (c->dim == 3 && c->elem_length > 0.0)
+      incident_line_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
+          (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->h,
+          c->elem_length, gauss_legendre12());
+    else
+      incident_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
+          (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
     e = cudaGetLastError();
   }
   cudaFreeAsync(elem, c->stream);
@@ -272,8 +375,12 @@ fwi_status setup_t(fwi_ctx* c) {
 template <typename T>
 fwi_status set_contrast_t(fwi_ctx* c, const void* m) {
   Prof p(c, KC_MISC);
-  convert_kernel<T><<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
-      (cplx<T>*)c->mF, (const double2*)m, c->N);
+  if (c->rf > 1)
+    prolong_kernel<T><<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+        (cplx<T>*)c->mF, (const double2*)m, c->nx, c->ny, c->rf, c->ry, c->N);
+  else
+    convert_kernel<T><<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+        (cplx<T>*)c->mF, (const double2*)m, c->N);
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
 }
@@ -290,8 +397,8 @@ fwi_status set_contrast(fwi_ctx* c, const void* m) {
 
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m) {
   Prof p(c, KC_MISC);
-  contrast_kernel<<<grid1d(c->N, 256, c->n_sm * 16), 256, 0, c->stream>>>(
-      (double2*)m, sos, alpha, c->N, c->c0);
+  contrast_kernel<<<grid1d(c->Ninv, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+      (double2*)m, sos, alpha, c->Ninv, c->c0);
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
 }

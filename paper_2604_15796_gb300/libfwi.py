@@ -38,7 +38,8 @@ class fwi_problem_desc(Structure):
                 ("n_elem", c_int), ("elem_pos", POINTER(c_double)), ("n_freq", c_int),
                 ("freq_hz", POINTER(c_double)), ("krylov_tol", c_double),
                 ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int),
-                ("n_tx", c_int), ("tx_angle", POINTER(c_double))]
+                ("n_tx", c_int), ("tx_angle", POINTER(c_double)), ("elem_length", c_double),
+                ("inv_factor", c_int)]
 
 
 class fwi_solve_info(Structure):
@@ -183,10 +184,12 @@ class FwiError(RuntimeError):
 
 
 def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-              max_batch=0, tx_angles=None):
+              max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1):
     """fwi_problem_desc from array-order ``shape`` ((Nz, Nx) or (Nz, Ny, Nx)).
     ``tx_angles``: steering angles [rad] of plane-wave transmits, or None for
-    point transmits at every element.
+    point transmits at every element.  ``elem_length``: 3-D line elements of
+    that length along y [m] (0: point elements).  ``inv_factor``: inversion
+    mesh of cells of inv_factor^d forward pixels (1: the forward mesh).
     Returns (desc, keepalive) -- keep the second item alive while desc is used."""
     dim = len(shape)
     elem = np.ascontiguousarray(elem, dtype=np.float64)
@@ -204,6 +207,8 @@ def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1
     d.freq_hz = freqs.ctypes.data_as(POINTER(c_double))
     d.krylov_tol, d.krylov_max_it = tol, max_it
     d.precision, d.max_batch = precision, max_batch
+    d.elem_length = float(elem_length)
+    d.inv_factor = int(inv_factor)
     tx = None
     if tx_angles is not None and len(tx_angles) > 0:
         tx = np.ascontiguousarray(tx_angles, dtype=np.float64)
@@ -261,10 +266,15 @@ class Context:
     FWI_MIXED, complex128 for FWI_FP64; m, grad, g, u always complex128)."""
 
     def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
-                 max_it=1000, max_batch=0, stream=None, tx_angles=None):
+                 max_it=1000, max_batch=0, stream=None, tx_angles=None, elem_length=0.0,
+                 inv_factor=1):
         import torch
         self.torch = torch
         self.shape = tuple(shape)
+        # the model (m, gradient, TV variables, SoS) lives on the inversion mesh
+        self.inv_factor = max(int(inv_factor), 1)
+        self.inv_shape = tuple(s // self.inv_factor for s in self.shape)
+        self.n_inv = int(np.prod(self.inv_shape))
         self.dim = len(shape)
         self.n = int(np.prod(shape))
         self.n_elem = int(np.asarray(elem).shape[0])
@@ -275,7 +285,7 @@ class Context:
         self.precision = precision
         self.field_dtype = torch.complex128 if precision == FWI_FP64 else torch.complex64
         self.desc, self._keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it,
-                                          max_batch, tx_angles)
+                                          max_batch, tx_angles, elem_length, inv_factor)
         self.workspace_bytes = int(fwi_workspace_bytes(byref(self.desc)))
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -293,7 +303,7 @@ class Context:
         return st
 
     def _m(self, t, name="m", optional=False):
-        return _dev(t, self.torch.complex128, self.n, name, optional)
+        return _dev(t, self.torch.complex128, self.n_inv, name, optional)
 
     def _fields(self, t, name, optional=False):
         return _dev(t, self.field_dtype, self.n_rhs * self.n, name, optional)
@@ -323,10 +333,10 @@ class Context:
 
     # -- calls -----------------------------------------------------------
     def contrast_from_sos(self, sos, alpha=None):
-        m = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
+        m = self.torch.empty(self.inv_shape, dtype=self.torch.complex128, device="cuda")
         f64 = self.torch.float64
-        self._check(fwi_contrast_from_sos(self.handle, _dev(sos, f64, self.n, "sos"),
-                                          _dev(alpha, f64, self.n, "alpha", True), _ptr(m)))
+        self._check(fwi_contrast_from_sos(self.handle, _dev(sos, f64, self.n_inv, "sos"),
+                                          _dev(alpha, f64, self.n_inv, "alpha", True), _ptr(m)))
         return m
 
     def forward(self, m, fields=None, warm_start=False, data=None, allow_nonconverged=False):
@@ -355,7 +365,7 @@ class Context:
 
     def admm_init(self, m0):
         """(g, u) = (nabla m0, 0) on the device (Algorithm 1 initialisation)."""
-        g = self.torch.empty((self.dim,) + self.shape, dtype=self.torch.complex128,
+        g = self.torch.empty((self.dim,) + self.inv_shape, dtype=self.torch.complex128,
                              device="cuda")
         u = self.torch.empty_like(g)
         self._check(fwi_admm_init(self.handle, self._m(m0, "m0"), _ptr(g), _ptr(u)))
@@ -367,10 +377,10 @@ class Context:
         p.lambda_, p.rho, p.gamma, p.dual_step, p.n_cg = lam, rho, gamma, dual_step, n_cg
         m_ref_p = self._m(m_ref, "m_ref", True)
         p.m_ref = None if m_ref_p is None else m_ref_p.value
-        c128, dn = self.torch.complex128, self.dim * self.n
+        c128, dn = self.torch.complex128, self.dim * self.n_inv
         self._check(fwi_admm_tv_step(self.handle, self._m(m), _dev(g, c128, dn, "g"),
                                      _dev(u, c128, dn, "u"), self._m(grad, "grad"), byref(p),
-                                     _dev(sos, self.torch.float64, self.n, "sos", True)))
+                                     _dev(sos, self.torch.float64, self.n_inv, "sos", True)))
 
     def apply(self, kind, vin, freq, m=None):
         nb = vin.shape[0]
@@ -448,7 +458,7 @@ class Context:
         return y
 
     def jac_adjoint(self, y):
-        z = self.torch.empty(self.shape, dtype=self.torch.complex128, device="cuda")
+        z = self.torch.empty(self.inv_shape, dtype=self.torch.complex128, device="cuda")
         self._check(fwi_jac_adjoint(self.handle,
                                     _dev(y, self.torch.complex128,
                                          self.n_freq * self.n_t * self.n_elem, "y"), _ptr(z)))
@@ -468,24 +478,28 @@ class Server:
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
                gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-               max_batch=0, tx_angles=None):
-        """Queue a reconstruction; host numpy inputs (sos0 float64 of ``shape``,
+               max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1):
+        """Queue a reconstruction; host numpy inputs (sos0 float64 of the inversion mesh,
         d_obs [n_freq][N_T][n_elem], complex64 for FWI_MIXED and complex128
         for FWI_FP64).  max_batch limits the right-hand sides per Krylov launch
-        (0: all); tx_angles selects plane-wave transmits.  Returns the request
-        id."""
+        (0: all); tx_angles selects plane-wave transmits, elem_length 3-D line
+        elements, inv_factor an inversion mesh (sos0 and the result on it).
+        Returns the request id."""
         req = fwi_request()
         desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch,
-                               tx_angles)
+                               tx_angles, elem_length, inv_factor)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
         d_obs = np.ascontiguousarray(d_obs, dtype=cdt)
         n_elem, n_freq, n_t = int(np.asarray(elem).shape[0]), int(len(freqs)), int(desc.n_tx)
         n_t = n_t if n_t > 0 else n_elem
-        if sos0.size != int(np.prod(shape)) or d_obs.size != n_freq * n_t * n_elem:
-            raise ValueError(f"sos0 must hold {int(np.prod(shape))} values and d_obs "
-                             f"{n_freq} x {n_t} x {n_elem}; got {sos0.shape}, {d_obs.shape}")
+        rf = max(int(inv_factor), 1)
+        inv_shape = tuple(s // rf for s in shape)
+        if sos0.size != int(np.prod(inv_shape)) or d_obs.size != n_freq * n_t * n_elem:
+            raise ValueError(f"sos0 must hold {int(np.prod(inv_shape))} values (inversion mesh) "
+                             f"and d_obs {n_freq} x {n_t} x {n_elem}; got {sos0.shape}, "
+                             f"{d_obs.shape}")
         req.sos0 = sos0.ctypes.data_as(POINTER(c_double))
         req.d_obs = d_obs.ctypes.data
         req.admm.lambda_, req.admm.rho, req.admm.gamma = lam, rho, gamma
@@ -495,7 +509,7 @@ class Server:
         st = fwi_server_submit(self.handle, byref(req), byref(rid))
         if st != FWI_OK:
             raise FwiError(st, fwi_last_error(None).decode())
-        self._pending[rid.value] = tuple(shape)
+        self._pending[rid.value] = inv_shape
         del keep
         return rid.value
 

@@ -193,6 +193,25 @@ def planewave_2d(seed=1005):
     return w
 
 
+def elevation_3d(seed=1006):
+    """The paper's 3-D study (Sec. V-B): 64 line elements of 1 cm elevation
+    at 0.3 mm pitch (19.2 mm aperture), each element transmitting in turn,
+    10 frequencies 0.2-2 MHz; homogeneous 1540 m/s background with two small
+    spherical cysts (radius 0.8 mm at 1400 m/s, radius 0.5 mm at 1600 m/s)
+    at two depths (seeded lateral positions).  Grid 96 x 64 x 64 (x, y,
+    depth) at 0.2 mm (3.85 pixels per wavelength at 2 MHz)."""
+    shape, h = (64, 64, 96), 0.2e-3
+    rng = np.random.default_rng(seed)
+    x, y, z = _coords(shape, h)
+    sos = np.full(shape, C0)
+    for radius, c_in, depth in ((0.8e-3, 1400.0, 4.0e-3), (0.5e-3, 1600.0, 8.0e-3)):
+        cx, cy = rng.uniform(-3e-3, 3e-3), rng.uniform(-1e-3, 1e-3)
+        sos[(x - cx) ** 2 + (y - cy) ** 2 + (z - depth) ** 2 <= radius ** 2] = c_in
+    return Workload("elev3d", shape, h, C0, array_positions(64, 0.3e-3, h, 3),
+                    np.linspace(0.2e6, 2.0e6, 10), sos, seed,
+                    dict(elem_length=1e-2, inclusions=[1400.0, 1600.0]))
+
+
 def scaled(shape, h, n_elem, pitch, freqs, seed, **kw):
     """A downscaled workload with the tissue statistics (parity tests)."""
     return tissue_phantom(shape, h, n_elem, pitch, freqs, seed, **kw)
