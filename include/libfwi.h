@@ -366,6 +366,12 @@ typedef struct fwi_tuning {
                            fill the SMs the other half's passes leave idle;
                            results are bitwise the same as with 0 (one
                            chain). */
+  int debug_stall_once; /* test of the failure path: 1 makes the next
+                           tensor-core contraction withhold its first
+                           pipeline stage, so that its bounded waits give up
+                           after about 1 s and the call returns FWI_ERR_CUDA
+                           ("pipeline wait timed out"); the context stays
+                           usable.  Applies once; reads back as 0. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

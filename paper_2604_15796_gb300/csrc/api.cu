@@ -523,6 +523,9 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
     return fail(ctx, FWI_ERR_INVALID_ARG, "jac_tensor_cores must be 0 or 1");
   if (in->overlap_halves != 0 && in->overlap_halves != 1)
     return fail(ctx, FWI_ERR_INVALID_ARG, "overlap_halves must be 0 or 1");
+  if (in->debug_stall_once != 0 && in->debug_stall_once != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "debug_stall_once must be 0 or 1");
+  ctx->tc_stall = in->debug_stall_once;
   ctx->use_tc = in->jac_tensor_cores == 1;
   ctx->overlap = in->overlap_halves == 1;
   ctx->var_rf = req[0];

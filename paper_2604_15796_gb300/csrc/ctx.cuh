@@ -76,6 +76,7 @@ struct fwi_ctx {
   int* tc_err = nullptr;            // error word of the tensor-core kernels
   int* h_tc_err = nullptr;          // pinned host mirror
   bool use_tc = true;               // tensor-core pixel contractions (FP32 fields)
+  int tc_stall = 0;                 // next contraction withholds its first stage (test)
   double* red = nullptr;            // reduction scratch (doubles)
   double* h_red = nullptr;          // pinned host mirror
   int red_n = 0;

@@ -144,6 +144,7 @@ struct ContractArgs {
   long long N, chunk;
   int NE, n_freq;
   int sub_ks;       // k-steps per accumulation sub-chunk
+  int stall;        // test of the failure path: withhold the first stage
 };
 
 // Two accumulators (TMEM columns 0-255 and 256-511) alternate between
@@ -160,7 +161,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
   constexpr int C_RAW_X = RW::X, C_RAW_Q = RW::Q, C_RAW_A = RW::A;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done[2],
-      bar_freed[2];
+      bar_freed[2], bar_final;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -184,6 +185,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
       mbar_init(smem_addr(&bar_done[b]), 1);
       mbar_init(smem_addr(&bar_freed[b]), 128);
     }
+    mbar_init(smem_addr(&bar_final), 1);
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
         put_b(bhi, blo, half, r, qr, qi);
       }
       fence_proxy_async();
-      mbar_arrive(smem_addr(&bar_full[cs]));
+      if (!(p.stall && g == 0)) mbar_arrive(smem_addr(&bar_full[cs]));
     }
     cp_async_wait<0>();
   } else {
@@ -354,11 +356,16 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
         commit(smem_addr(&bar_done[b]));
       __syncwarp();
     }
+    if (lane == 0) commit(smem_addr(&bar_final));  // after every MMA of this CTA
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
+    // no MMA of this CTA may still write the columns being freed (also when
+    // a wait gave up)
+    if (lane == 0) mbar_wait_drain(smem_addr(&bar_final), 0, p.err, kErrWaitDrain);
+    __syncwarp();
     tmem_dealloc(tmem, 512);
   }
 }
@@ -395,7 +402,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[M_CONV], bar_empty[M_CONV], bar_done[2],
-      bar_freed[2];
+      bar_freed[2], bar_final;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -413,6 +420,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
       mbar_init(smem_addr(&bar_done[b]), 1);
       mbar_init(smem_addr(&bar_freed[b]), 128);
     }
+    mbar_init(smem_addr(&bar_final), 1);
     abort_flag = 0;
     mbar_init_fence();
   }
@@ -564,11 +572,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
       if (lane == 0 && ks == p.nks - 1) commit(smem_addr(&bar_done[b]));
       __syncwarp();
     }
+    if (lane == 0) commit(smem_addr(&bar_final));  // after every MMA of this CTA
   }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     fence_after_sync();
+    if (lane == 0) mbar_wait_drain(smem_addr(&bar_final), 0, p.err, kErrWaitDrain);
+    __syncwarp();
     tmem_dealloc(tmem, 512);
   }
 }
@@ -671,7 +682,9 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   const long long chunk_ks = chunk / KS;
   const long long nsub = (chunk_ks + 63) / 64;
   const int sub_ks = (int)((chunk_ks + nsub - 1) / nsub);
-  ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq, sub_ks};
+  ContractArgs args{X, Q, a, part, c->tc_err, c->N, chunk, c->n_elem, c->n_freq, sub_ks,
+                    c->tc_stall};
+  c->tc_stall = 0;  // one launch
   dim3 grid(split, nbe * nbe, c->n_freq);
   const double fe = (double)c->n_freq * c->n_elem * c->N;
   {

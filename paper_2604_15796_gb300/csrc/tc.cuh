@@ -21,6 +21,7 @@ namespace tc {
 constexpr int kErrWaitFull = 1;
 constexpr int kErrWaitEmpty = 2;
 constexpr int kErrWaitDone = 3;
+constexpr int kErrWaitDrain = 4;
 
 // Wall-clock limit of every pipeline wait (ns).
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
@@ -156,6 +157,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       *abort = 1;
       atomicCAS(err, 0, code);
       return false;
+    }
+  }
+}
+
+// Wait, regardless of the abort flag, for the phase of parity `parity`:
+// the final drain of a CTA's own tensor-core operations before its TMEM is
+// freed.  Gives up after kWaitLimitNs and records `code`.
+__device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity, int* err,
+                                                int code) {
+  if (mbar_try_wait(bar, parity)) return;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_ns() - t0 > kWaitLimitNs) {
+      atomicCAS(err, 0, code);
+      return;
     }
   }
 }

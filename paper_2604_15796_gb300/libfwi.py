@@ -64,7 +64,8 @@ class fwi_stats(Structure):
 class fwi_tuning(Structure):
     _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
                 ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
-                ("jac_tensor_cores", c_int), ("overlap_halves", c_int)]
+                ("jac_tensor_cores", c_int), ("overlap_halves", c_int),
+                ("debug_stall_once", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -433,6 +434,21 @@ class Context:
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.jac_tensor_cores = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def debug_stall_once(self):
+        """Test of the failure path: the next tensor-core contraction
+        withholds its first pipeline stage, so that its bounded waits give up
+        (about 1 s) and the call raises FwiError (FWI_ERR_CUDA)."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.debug_stall_once = 1
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def cancel(self):
+        """Ask a running (or the next) solve on this context to stop at its
+        next host check; that call raises FwiError (FWI_ERR_CANCELLED).
+        Thread-safe."""
+        self._check(fwi_cancel(self.handle))
 
     def set_profiling(self, on):
         self._check(fwi_set_profiling(self.handle, int(bool(on))))
