@@ -141,7 +141,8 @@ def admm_tv_step(m, g, u, grad, fields, rfields, prob, params, m_ref=None):
     g_new = shrink(gm - np.asarray(u), params.lam / params.rho)
     step = params.rho if params.dual_step is None else params.dual_step
     u_new = np.asarray(u) + step * (g_new - gm)
-    return m_new, g_new, u_new, model.sos_from_contrast(m_new, prob.c0), dm
+    sos = model.sos_from_contrast(m_new, prob.c0, model.background_alpha(prob))
+    return m_new, g_new, u_new, sos, dm
 
 
 def reconstruct(m0, d_obs, prob, params, n_iter, method="bicgstab", tol=1e-10, weights=None,
@@ -162,7 +163,7 @@ def reconstruct(m0, d_obs, prob, params, n_iter, method="bicgstab", tol=1e-10, w
     g = grad_op(m, shape)
     u = np.zeros_like(g)
     rfields = None
-    sos = model.sos_from_contrast(m, prob.c0)
+    sos = model.sos_from_contrast(m, prob.c0, model.background_alpha(prob))
     history = []
     for k in range(n_iter):
         ref = inverse.gradient_inversion_mesh(m, d_obs, prob, method, tol, weights)

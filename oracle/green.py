@@ -22,7 +22,8 @@ from scipy import special
 
 
 def green_point(k, r, dim):
-    """Outgoing free-space Green's function of (lap + k^2) G = -delta."""
+    """Outgoing free-space Green's function of (lap + k^2) G = -delta (k may
+    be complex with Im k > 0: a lossy background)."""
     r = np.asarray(r, dtype=np.float64)
     if dim == 2:
         return 0.25j * special.hankel1(0, k * r)
@@ -43,8 +44,8 @@ def green_cell(k, r, h, dim):
     out = np.empty(r.shape, dtype=np.complex128)
     far = r > 0
     if dim == 2:
-        out[far] = (1j * np.pi * a / (2.0 * k)) * special.j1(ka) \
-            * special.hankel1(0, k * r[far])
+        j1 = special.j1(ka) if np.isrealobj(ka) else special.jv(1, ka)
+        out[far] = (1j * np.pi * a / (2.0 * k)) * j1 * special.hankel1(0, k * r[far])
         out[~far] = (1j * np.pi * a / (2.0 * k)) * special.hankel1(1, ka) \
             - 1.0 / (k * k)
     else:

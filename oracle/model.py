@@ -83,30 +83,66 @@ def pixel_centres(shape, h):
                      (z * h).ravel().astype(np.float64)], axis=1)
 
 
+def background_alpha(prob):
+    """Attenuation of the background alpha0 [Np/m/Hz] (prob.extra["alpha0"],
+    default 0: lossless)."""
+    return float(prob.extra.get("alpha0", 0.0))
+
+
 def wavenumbers(prob):
-    """k_l = omega_l / c0 (real: lossless background; k^2 = omega^2 kappa0
-    rho0 with kappa0 = 1/(c0^2 rho0), Sec. II)."""
-    return 2.0 * np.pi * np.asarray(prob.freqs, dtype=np.float64) / prob.c0
+    """k_l^2 = omega_l^2 kappa0 rho0 (Sec. II) with the background's
+    compressibility kappa0 = 1/(c0^2 rho0) + i alpha0/(pi c0 rho0) (Eq. 1-2
+    under e^{-i omega t}): k_l = omega_l sqrt(1/c0^2 + i alpha0/(pi c0)),
+    the root with Im k > 0 (outgoing waves decay; Im k ~ alpha0 f).  Real,
+    omega_l / c0, for a lossless background."""
+    w = 2.0 * np.pi * np.asarray(prob.freqs, dtype=np.float64)
+    a0 = background_alpha(prob)
+    if a0 == 0.0:
+        return w / prob.c0
+    return w * np.sqrt(1.0 / prob.c0 ** 2 + 1j * a0 / (np.pi * prob.c0))
 
 
-def contrast_from_sos(c, c0, alpha=None):
+def _kappa(c, alpha):
+    """rho0 kappa = 1/c^2 + i alpha/(pi c) (Eq. 1-2, the alpha^2 term dropped
+    as the approximation of Eq. 2 does)."""
+    return 1.0 / (c * c) + 1j * alpha / (np.pi * c)
+
+
+def contrast_from_sos(c, c0, alpha=None, alpha0=0.0):
     """Contrast m = kappa/kappa0 - 1 (Eq. 3).
 
-    kappa' = 1/(c^2 rho0) (the alpha^2 term dropped, as the approximation of
-    Eq. 2 does), kappa'' = alpha/(pi c rho0) with alpha in Np/m/Hz, and under
-    e^{-i omega t} kappa = kappa' + i kappa''.  rho0 cancels in the ratio.
+    kappa' = 1/(c^2 rho0), kappa'' = alpha/(pi c rho0) with alpha in
+    Np/m/Hz, and under e^{-i omega t} kappa = kappa' + i kappa''.  rho0
+    cancels in the ratio.  With a lossy background (alpha0 > 0) kappa0 is
+    complex too, and a pixel without an attenuation value (alpha None) takes
+    the background's, so that the background has m = 0.
     """
     c = np.asarray(c, dtype=np.float64)
-    m = (c0 * c0) / (c * c) - 1.0
-    if alpha is None:
-        return m.astype(np.complex128)
-    return m + 1j * np.asarray(alpha, dtype=np.float64) * c0 * c0 / (np.pi * c)
+    if alpha0 == 0.0:
+        m = (c0 * c0) / (c * c) - 1.0
+        if alpha is None:
+            return m.astype(np.complex128)
+        return m + 1j * np.asarray(alpha, dtype=np.float64) * c0 * c0 / (np.pi * c)
+    a = alpha0 if alpha is None else np.asarray(alpha, dtype=np.float64)
+    return _kappa(c, a) / _kappa(c0, alpha0) - 1.0
 
 
-def sos_from_contrast(m, c0):
-    """Speed of sound from the real part of the contrast, the inverse of
-    Eq. 2-3 for a lossless point: c = c0 / sqrt(1 + Re m)."""
-    return c0 / np.sqrt(1.0 + np.real(np.asarray(m)))
+def sos_from_contrast(m, c0, alpha0=0.0):
+    """Speed of sound from the contrast, the inverse of Eq. 2-3:
+    1/c^2 = Re(rho0 kappa0 (1 + m)); c = c0 / sqrt(1 + Re m) for a lossless
+    background."""
+    m = np.asarray(m)
+    if alpha0 == 0.0:
+        return c0 / np.sqrt(1.0 + np.real(m))
+    return 1.0 / np.sqrt(np.real(_kappa(c0, alpha0) * (1.0 + m)))
+
+
+def attenuation_from_contrast(m, c0, alpha0=0.0):
+    """Attenuation alpha [Np/m/Hz] from the contrast (Eq. 1-3):
+    alpha / (pi c) = Im(rho0 kappa0 (1 + m)), c from sos_from_contrast."""
+    m = np.asarray(m)
+    c = sos_from_contrast(m, c0, alpha0)
+    return np.pi * c * np.imag(_kappa(c0, alpha0) * (1.0 + m))
 
 
 def plane_wave_weights(prob, angles):
@@ -121,7 +157,7 @@ def plane_wave_weights(prob, angles):
     into the medium.  Under e^{-i omega t} a delay tau multiplies a source
     by exp(i omega tau), hence w_{l,i,e} = exp(i k_l x_e sin theta_i).
     Unit amplitude on every element (no apodisation).  [N_F, N_T, N_E]."""
-    k = wavenumbers(prob)
+    k = 2.0 * np.pi * np.asarray(prob.freqs, dtype=np.float64) / prob.c0  # delays: real
     xe = np.asarray(prob.elem, dtype=np.float64)[:, 0]
     s = np.sin(np.asarray(angles, dtype=np.float64))
     return np.exp(1j * k[:, None, None] * s[None, :, None] * xe[None, None, :])
