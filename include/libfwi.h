@@ -110,6 +110,14 @@ typedef struct fwi_problem_desc {
                               and sos are then [N_inv] = N / inv_factor^dim
                               on the inversion mesh (contrast constant over a
                               cell; gradients summed over its pixels). */
+  double alpha0;           /* attenuation of the background [Np/m/Hz] (Eq. 1-2;
+                              0: lossless).  Then k_l = omega_l sqrt(1/c0^2 +
+                              i alpha0/(pi c0)) (Im k > 0), the Green's
+                              functions are those of complex k, and the
+                              contrast is m = kappa/kappa0 - 1 with both
+                              compressibilities complex (a background pixel
+                              has m = 0; fwi_contrast_from_sos without an
+                              alpha map gives every pixel alpha0). */
 } fwi_problem_desc;
 
 /* Per-call Krylov report.  The caller sets n_rhs and the optional host

@@ -200,7 +200,8 @@ __global__ void add_kernel(double2* m, const double2* dm, long long N) {
 
 // g = shrink_tau(nabla m - u); u += step (g - nabla m); sos = c0/sqrt(1+Re m)
 __global__ void shrink_dual_kernel(double2* g, double2* u, const double2* m, double* sos,
-                                   double tau, double step, double c0, Grid3 G, int dim) {
+                                   double tau, double step, double c0, double alpha0, Grid3 G,
+                                   int dim) {
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < G.N;
        n += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
@@ -225,7 +226,15 @@ __global__ void shrink_dual_kernel(double2* g, double2* u, const double2* m, dou
       g[q * G.N + n] = gq;
       u[q * G.N + n] = u[q * G.N + n] + step * (gq - gm[q]);
     }
-    if (sos) sos[n] = c0 / sqrt(1.0 + m[n].x);
+    if (sos) {
+      if (alpha0 > 0.0) {
+        // 1/c^2 = Re(rho0 kappa0 (1 + m)), rho0 kappa0 = 1/c0^2 + i alpha0/(pi c0)
+        const double qr = 1.0 / (c0 * c0), qi = alpha0 / (3.141592653589793238462643383279502884 * c0);
+        sos[n] = 1.0 / sqrt(qr * (1.0 + m[n].x) - qi * m[n].y);
+      } else {
+        sos[n] = c0 / sqrt(1.0 + m[n].x);
+      }
+    }
   }
 }
 
@@ -342,6 +351,7 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
   {
     Prof pf(c, KC_ADMM);
     shrink_dual_kernel<<<blocks_for(c->Ninv, 256, nb), 256, 0, s>>>(g, u, m, sos, tau, step, c->c0,
+                                                                  c->alpha0,
                                                                G, dim);
   }
   FWI_CUDA(c, cudaGetLastError());

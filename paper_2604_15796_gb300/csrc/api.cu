@@ -3,6 +3,7 @@
 // steps into the calls of the paper's problem statement (Sec. II-III).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <string>
 
@@ -71,6 +72,8 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
     if (!std::isfinite(d->tx_angle[i])) return bad("tx_angle must be finite");
   if (!(d->elem_length >= 0) || !std::isfinite(d->elem_length))
     return bad("elem_length must be finite and >= 0");
+  if (!(d->alpha0 >= 0) || !std::isfinite(d->alpha0))
+    return bad("alpha0 must be finite and >= 0");
   L.rf = d->inv_factor > 1 ? d->inv_factor : 1;
   L.ry = (d->dim == 3) ? L.rf : 1;
   L.n_elem = d->n_elem; L.n_freq = d->n_freq;
@@ -112,9 +115,10 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   const long long NTE = (long long)L.n_t * L.n_elem;
   const long long NDF = std::max(NTE, NE2);
   const size_t b_pw = L.n_tx > 0 ? (size_t)L.n_freq * (2 * NTE + 2 * NE2) * 16 : 0;
+  const size_t b_lossy = d->alpha0 > 0 ? (size_t)L.n_freq * (NE2 + 1) * 16 : 0;
   L.b_small = (size_t)L.batch * (sizeof(Scal) + NSLOT * (size_t)L.rows * sizeof(double2) +
                                  sizeof(int)) +
-              64 + (size_t)L.n_freq * (NE2 * 16 + NDF * L.csz) + b_pw + 3 * 1024 * L.csz;
+              64 + (size_t)L.n_freq * (NE2 * 16 + NDF * L.csz) + b_pw + b_lossy + 3 * 1024 * L.csz;
   size_t js1 = (size_t)L.split * L.n_freq * NE2 * L.csz;
   size_t js2 = (size_t)8 * L.N * sizeof(double2);
   L.b_jsplit = js1 > js2 ? js1 : js2;
@@ -151,7 +155,7 @@ static void release(fwi_ctx* c) {
   void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
-                  c->W, c->WhW, c->dpw, c->dsyn, c->vfwd,
+                  c->W, c->WhW, c->dpw, c->dsyn, c->vfwd, c->sdat, c->dlossy,
                   c->jsplit, c->zpart, c->aF, c->red, c->tc_bops, c->tc_err};
   // stream-ordered frees: no device-wide synchronisation, so a context can be
   // retired while other contexts' work runs
@@ -216,6 +220,15 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   c->n_t = L.n_t;
   if (L.n_tx > 0) c->tx_angle.assign(d->tx_angle, d->tx_angle + L.n_tx);
   c->elem_length = (L.dim == 3) ? d->elem_length : 0.0;
+  c->alpha0 = d->alpha0;
+  for (double f : c->freq) {
+    // k = omega sqrt(1/c0^2 + i alpha0 / (pi c0)), the root with Im k >= 0
+    const double w = 2.0 * 3.141592653589793238462643383279502884 * f;
+    const std::complex<double> kk =
+        w * std::sqrt(std::complex<double>(1.0 / (c->c0 * c->c0),
+                                           c->alpha0 / (3.141592653589793238462643383279502884 * c->c0)));
+    c->kc.push_back(make_double2(kk.real(), kk.imag()));
+  }
   c->rf = L.rf;
   c->ry = L.ry;
   c->inx = L.nx / L.rf;
@@ -256,6 +269,10 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   const size_t NTE = (size_t)L.n_t * L.n_elem;
   alloc((void**)&c->dres, 16 * L.n_freq * NE2);
   alloc(&c->dF, L.csz * L.n_freq * std::max(NTE, NE2));
+  if (d->alpha0 > 0) {
+    alloc((void**)&c->sdat, 16 * L.n_freq);
+    alloc((void**)&c->dlossy, 16 * L.n_freq * NE2);
+  }
   if (L.n_tx > 0) {
     alloc((void**)&c->W, 16 * L.n_freq * NTE);
     alloc((void**)&c->WhW, 16 * L.n_freq * NE2);
@@ -291,9 +308,23 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
     return st;
   }
   // per-frequency scales k_l^2 dV for the Jacobian / data contractions
+  // (lossy background: the contraction kernels scale by 1 and the complex
+  // k_l^2 dV is applied in data space)
   std::vector<double> sc(L.n_freq);
-  for (int l = 0; l < L.n_freq; ++l) sc[l] = c->kwave[l] * c->kwave[l] * std::pow(c->h, c->dim);
+  std::vector<double2> scc(L.n_freq);
+  for (int l = 0; l < L.n_freq; ++l) {
+    const double dv = std::pow(c->h, c->dim);
+    sc[l] = c->alpha0 > 0 ? 1.0 : c->kwave[l] * c->kwave[l] * dv;
+    const std::complex<double> kk(c->kc[l].x, c->kc[l].y);
+    const std::complex<double> s = kk * kk * dv;
+    scc[l] = make_double2(s.real(), s.imag());
+  }
   e = cudaMemcpy(c->red, sc.data(), sizeof(double) * L.n_freq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->alpha0 > 0) {
+    e = cudaMemcpyAsync(c->sdat, scc.data(), sizeof(double2) * L.n_freq, cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  }
   if (e == cudaSuccess && L.n_tx > 0) {
     // plane-wave weights w_{l,i,e} = exp(i k_l x_e sin theta_i) and W^H W
     const int nt = L.n_tx, ne = L.n_elem;

@@ -28,6 +28,12 @@ struct fwi_ctx {
   int n_tx = 0, n_t = 0;
   std::vector<double> tx_angle;
   double elem_length = 0;           // 3D line elements along y (0: points)
+  // attenuating background: complex k_l, and the complex scales k_l^2 dV
+  // applied in data space (the contraction kernels then scale by 1)
+  double alpha0 = 0;
+  std::vector<double2> kc;
+  double2* sdat = nullptr;          // [n_freq] k_l^2 dV (lossy only)
+  double2* dlossy = nullptr;        // [n_freq][n_elem][n_elem] scratch (lossy only)
   // inversion mesh: cells of rf x ry x rf pixels (ry = 1 in 2D)
   int rf = 1, ry = 1, inx = 0, iny = 1, inz = 0;
   long long Ninv = 0;

@@ -450,6 +450,37 @@ fwi_status synth(fwi_ctx* c, const double2* A, int herm, int R, int K, const dou
   return FWI_OK;
 }
 
+// Attenuating background: out[l][..] = s_l in[l][..] (conj: conj(s_l)), s_l
+// = k_l^2 dV complex, on [n_freq][per] data-space arrays (FP64 or field
+// precision); the contraction kernels themselves scale by 1 then.
+template <typename V>
+__global__ void data_scale_kernel(V* out, const V* in, const double2* s, long long per,
+                                  long long total, int conj) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 f = s[i / per];
+    const double fr = f.x, fi = conj ? -f.y : f.y;
+    const V v = in[i];
+    const double vr = (double)v.x, vi = (double)v.y;
+    V o;
+    o.x = (decltype(o.x))(vr * fr - vi * fi);
+    o.y = (decltype(o.y))(vr * fi + vi * fr);
+    out[i] = o;
+  }
+}
+
+template <typename V>
+static fwi_status data_scale(fwi_ctx* c, V* out, const V* in, int conj) {
+  if (c->alpha0 <= 0.0) return FWI_OK;
+  const long long per = (long long)c->n_elem * c->n_elem;
+  const long long total = per * c->n_freq;
+  Prof p(c, KC_MISC);
+  data_scale_kernel<V><<<blocks_for(total, 256, c->n_sm * 8), 256, 0, c->stream>>>(
+      out, in, c->sdat, per, total, conj);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
+}
+
 // Inversion mesh: forward-mesh results written to c->vfwd are summed over
 // each cell into out (no-op on the forward mesh, where they went to out).
 static fwi_status to_inversion_mesh(fwi_ctx* c, double2* out) {
@@ -471,6 +502,8 @@ template <typename T> static fwi_status project_data_t(fwi_ctx* c, void* data_ou
   if (st != FWI_OK) return st;
   st = Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->mF,
                         (const cplx<T>*)c->p0, c->dres);
+  if (st != FWI_OK) return st;
+  st = data_scale(c, c->dres, c->dres, 0);  // lossy background: k_l^2 dV
   if (st != FWI_OK) return st;
   // plane-wave transmits: data of transmit i = sum_e w_{l,i,e} (point data of e)
   if (c->n_tx > 0) {
@@ -507,6 +540,12 @@ template <typename T> static fwi_status residual_t(fwi_ctx* c, const void* d_obs
   // dres and conj(y) into dF (the adjoint sources read dF)
   if (c->n_tx > 0) {
     fwi_status st = synth(c, c->W, 1, c->n_elem, c->n_tx, c->dpw, c->dres, c->dF);
+    if (st != FWI_OK) return st;
+  }
+  // lossy background: the receiver rows carry the complex k_l^2 dV, so the
+  // adjoint sources sum_j R_j conj(r) take it on conj(r)
+  {
+    fwi_status st = data_scale(c, (cplx<T>*)c->dF, (const cplx<T>*)c->dF, 0);
     if (st != FWI_OK) return st;
   }
   if (misfit) {
@@ -588,8 +627,10 @@ template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a,
           (cplx<T>*)c->aF, (const double2*)a, c->N);
   }
   FWI_CUDA(c, cudaGetLastError());
-  return Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
-                          (const cplx<T>*)c->fields, y);
+  st = Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
+                        (const cplx<T>*)c->fields, y);
+  if (st != FWI_OK) return st;
+  return data_scale(c, y, (const double2*)y, 0);  // lossy background: k_l^2 dV
 }
 
 fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {
@@ -603,6 +644,12 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
   if (st != FWI_OK) return st;
   // forward-mesh result, summed over the inversion cells at the end
   double2* z = c->rf > 1 ? c->vfwd : z_out;
+  if (c->alpha0 > 0.0) {
+    // lossy background: J^H carries conj(k_l^2 dV)
+    st = data_scale(c, c->dlossy, y, 1);
+    if (st != FWI_OK) return st;
+    y = c->dlossy;
+  }
   if constexpr (std::is_same<T, float>::value) {
     if (tc_usable(c)) {
       const int np = tc_jh_partials(c, y, (const float2*)c->fields, (float2*)c->zpart);

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <vector>
 
+#include "bessel_c.cuh"
 #include "ctx.cuh"
 #include "mesh.cuh"
 #include "prof.cuh"
@@ -79,6 +80,111 @@ __global__ void green_lattice_kernel(double2* lat, int nx, int ny, int nz, int d
       }
     }
     lat[id] = out;
+  }
+}
+
+// Ghat of an attenuating background (complex k = kr + i ki): the closed
+// forms above with complex arithmetic; 2D through the complex-argument
+// Bessel / Hankel functions (bessel_c.cuh).
+__global__ void green_lattice_lossy_kernel(double2* lat, int nx, int ny, int nz, int dim,
+                                           double h, double kr, double ki) {
+  using namespace bes;
+  const int lx = 2 * nx, ly = (dim == 3) ? 2 * ny : 1, lz = 2 * nz;
+  const long long total = (long long)lx * ly * lz;
+  const cd k{kr, ki};
+  const cd k2 = k * k;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(id % lx);
+    const long long rem = id / lx;
+    const int iy = (int)(rem % ly);
+    const int iz = (int)(rem / ly);
+    cd out{0.0, 0.0};
+    const bool half = (ix == nx) || (iz == nz) || (dim == 3 && iy == ny);
+    if (!half) {
+      const double ox = lattice_offset(ix, nx) * h;
+      const double oy = (dim == 3) ? lattice_offset(iy, ny) * h : 0.0;
+      const double oz = lattice_offset(iz, nz) * h;
+      const double r = sqrt(ox * ox + oy * oy + oz * oz);
+      if (dim == 2) {
+        const double a = h / sqrt(bes::kPi);
+        const cd ka = a * k;
+        const cd ic = cdiv(cd{0.0, bes::kPi * a / 2.0}, k);  // i pi a / (2k)
+        if (r > 0.0) {
+          out = ic * (besselj_1(ka) * hankel1_0(r * k));
+        } else {
+          out = ic * hankel1_1(ka) - cdiv(cd{1.0, 0.0}, k2);
+        }
+      } else {
+        const double a = h * cbrt(3.0 / (4.0 * bes::kPi));
+        const cd ka = a * k;
+        const cd eika = cexp_(cd{-ka.im, ka.re});  // e^{i ka}
+        const cd sn = cdiv(eika - cexp_(cd{ka.im, -ka.re}), cd{0.0, 2.0});  // sin ka
+        const cd cs = 0.5 * (eika + cexp_(cd{ka.im, -ka.re}));              // cos ka
+        if (r > 0.0) {
+          const cd vol = cdiv((4.0 * bes::kPi) * (sn - ka * cs), k2 * k);
+          const cd eikr = cexp_(cd{-r * k.im, r * k.re});
+          out = (1.0 / (4.0 * bes::kPi * r)) * (vol * eikr);
+        } else {
+          // ((1 - i ka) e^{i ka} - 1) / k^2
+          out = cdiv((cd{1.0 + ka.im, -ka.re} * eika) - cd{1.0, 0.0}, k2);
+        }
+      }
+    }
+    lat[id] = make_double2(out.re, out.im);
+  }
+}
+
+template <typename T>
+__global__ void scale_spectrum_c_kernel(cplx<T>* dst, const double2* src, long long n,
+                                        double sr, double si) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = src[i];
+    dst[i] = mk<T>((T)(v.x * sr - v.y * si), (T)(v.x * si + v.y * sr));
+  }
+}
+
+// Incident fields of point elements in an attenuating background:
+// 2D (i/4) H0^(1)(k r), 3D e^{ikr}/(4 pi r), complex k per frequency.
+template <typename T>
+__global__ void incident_lossy_kernel(cplx<T>* p0, const double* elem, const double2* kc,
+                                      int n_elem, int n_freq, int nx, int ny, int nz, int dim,
+                                      double h) {
+  using namespace bes;
+  const long long N = (long long)nx * ny * nz;
+  const long long total = N * n_elem * n_freq;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    const long long n = id % N;
+    const long long le = id / N;
+    const int e = (int)(le % n_elem);
+    const int l = (int)(le / n_elem);
+    const int ix = (int)(n % nx);
+    const long long q = n / nx;
+    const int iy = (int)(q % ny);
+    const int iz = (int)(q / ny);
+    const double x = (ix + 0.5 - 0.5 * nx) * h;
+    const double z = iz * h;
+    double dx, dy = 0.0, dz;
+    if (dim == 2) {
+      dx = x - elem[2 * e];
+      dz = z - elem[2 * e + 1];
+    } else {
+      dx = x - elem[3 * e];
+      dy = (iy + 0.5 - 0.5 * ny) * h - elem[3 * e + 1];
+      dz = z - elem[3 * e + 2];
+    }
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const cd k{kc[l].x, kc[l].y};
+    cd g;
+    if (dim == 2) {
+      const cd hk = hankel1_0(r * k);
+      g = cd{-0.25 * hk.im, 0.25 * hk.re};  // (i/4) H0
+    } else {
+      g = (1.0 / (4.0 * bes::kPi * r)) * cexp_(cd{-r * k.im, r * k.re});
+    }
+    p0[id] = mk<T>((T)g.re, (T)g.im);
   }
 }
 
@@ -174,7 +280,7 @@ GaussRule gauss_legendre12() {
 // an entire integrand.  The integrand is even in t; panels end where the
 // phase has advanced by 2 pi or t by 1, 12-point Gauss-Legendre on each
 // (at most 4096 panels).
-__device__ double2 line_mean_green(double k, double rho, double dy, double L,
+__device__ double2 line_mean_green(double k, double ki, double rho, double dy, double L,
                                    const GaussRule& g) {
   const double PI = 3.141592653589793238462643383279502884;
   const double a = asinh((-0.5 * L - dy) / rho), b = asinh((0.5 * L - dy) / rho);
@@ -187,10 +293,13 @@ __device__ double2 line_mean_green(double k, double rho, double dy, double L,
       tn = fmin(fmin(tn, t + 1.0), t1);
       const double hw = 0.5 * (tn - t), mid = 0.5 * (tn + t);
       for (int q = 0; q < 12; ++q) {
+        const double ch = cosh(mid + hw * g.x[q]);
         double s, c;
-        sincos(kr * cosh(mid + hw * g.x[q]), &s, &c);
-        re += g.w[q] * hw * c;
-        im += g.w[q] * hw * s;
+        sincos(kr * ch, &s, &c);
+        // attenuating background (k + i ki): the factor exp(-ki rho cosh t)
+        const double wq = ki > 0.0 ? g.w[q] * hw * exp(-ki * rho * ch) : g.w[q] * hw;
+        re += wq * c;
+        im += wq * s;
       }
       t = tn;
     }
@@ -210,8 +319,8 @@ __device__ double2 line_mean_green(double k, double rho, double dy, double L,
 // Incident fields of 3-D line elements (finite elevation along y).
 template <typename T>
 __global__ void incident_line_kernel(cplx<T>* p0, const double* elem, const double* kw,
-                                     int n_elem, int n_freq, int nx, int ny, int nz, double h,
-                                     double L, GaussRule g) {
+                                     const double* kwi, int n_elem, int n_freq, int nx, int ny,
+                                     int nz, double h, double L, GaussRule g) {
   const long long N = (long long)nx * ny * nz;
   const long long total = N * n_elem * n_freq;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
@@ -230,7 +339,7 @@ __global__ void incident_line_kernel(cplx<T>* p0, const double* elem, const doub
     // pixels on the element's axis would make the mean singular; the array
     // sits outside the grid, so rho >= h there
     const double rho = fmax(sqrt(dx * dx + dz * dz), 1e-3 * h);
-    const double2 v = line_mean_green(kw[l], rho, dy, L, g);
+    const double2 v = line_mean_green(kw[l], kwi ? kwi[l] : 0.0, rho, dy, L, g);
     p0[id] = mk<T>((T)v.x, (T)v.y);
   }
 }
@@ -244,14 +353,25 @@ __global__ void convert_kernel(cplx<T>* dst, const double2* src, long long n) {
 
 // m = c0^2/c^2 - 1 + i alpha c0^2 / (pi c)   (Eq. 1-3, e^{-i omega t})
 __global__ void contrast_kernel(double2* m, const double* sos, const double* alpha,
-                                long long n, double c0) {
+                                long long n, double c0, double alpha0) {
   const double PI = 3.141592653589793238462643383279502884;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const double c = sos[i];
     double2 v;
-    v.x = c0 * c0 / (c * c) - 1.0;
-    v.y = alpha ? alpha[i] * c0 * c0 / (PI * c) : 0.0;
+    if (alpha0 > 0.0) {
+      // kappa / kappa0 - 1, rho0 kappa = 1/c^2 + i a/(pi c); a pixel without
+      // an attenuation value carries the background's
+      const double a = alpha ? alpha[i] : alpha0;
+      const double pr = 1.0 / (c * c), pi = a / (PI * c);
+      const double qr = 1.0 / (c0 * c0), qi = alpha0 / (PI * c0);
+      const double d = qr * qr + qi * qi;
+      v.x = (pr * qr + pi * qi) / d - 1.0;
+      v.y = (pi * qr - pr * qi) / d;
+    } else {
+      v.x = c0 * c0 / (c * c) - 1.0;
+      v.y = alpha ? alpha[i] * c0 * c0 / (PI * c) : 0.0;
+    }
     m[i] = v;
   }
 }
@@ -292,8 +412,12 @@ fwi_status compute_spectra(fwi_ctx* c) {
     if (c->dim == 3 && (e = upload_twiddles<double>(c->ly, &ty, c->stream)) != cudaSuccess) break;
     for (int l = 0; l < c->n_freq && e == cudaSuccess; ++l) {
       const double k = c->kwave[l];
-      green_lattice_kernel<<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
-          lat, c->nx, c->ny, c->nz, c->dim, c->h, k);
+      if (c->alpha0 > 0)
+        green_lattice_lossy_kernel<<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+            lat, c->nx, c->ny, c->nz, c->dim, c->h, c->kc[l].x, c->kc[l].y);
+      else
+        green_lattice_kernel<<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+            lat, c->nx, c->ny, c->nz, c->dim, c->h, k);
       if ((e = cudaGetLastError()) != cudaSuccess) break;
       // x lines (full, unpadded input)
       RowFwdArgs<double> r{};
@@ -321,9 +445,17 @@ fwi_status compute_spectra(fwi_ctx* c) {
       z.line_stride = (long long)c->ly * c->lx; z.ncols = c->ly * c->lx; z.nplanes = 1;
       z.tw = (const double2*)tz; z.nb = 1; z.n_elem = 1;
       if ((e = Lsop<double>::col(c->lz, z, c->stream)) != cudaSuccess) break;
-      const double scale = k * k / (double)P;
-      scale_spectrum_kernel<T><<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
-          (cplx<T>*)c->ghat + (long long)l * P, z.out, P, scale);
+      if (c->alpha0 > 0) {
+        // complex k^2 / P
+        const double kr = c->kc[l].x, ki = c->kc[l].y;
+        scale_spectrum_c_kernel<T><<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+            (cplx<T>*)c->ghat + (long long)l * P, z.out, P, (kr * kr - ki * ki) / (double)P,
+            2.0 * kr * ki / (double)P);
+      } else {
+        const double scale = k * k / (double)P;
+        scale_spectrum_kernel<T><<<grid1d(P, 256, cap), 256, 0, c->stream>>>(
+            (cplx<T>*)c->ghat + (long long)l * P, z.out, P, scale);
+      }
       if ((e = cudaGetLastError()) != cudaSuccess) break;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -347,19 +479,35 @@ fwi_status setup_t(fwi_ctx* c) {
   if (st != FWI_OK) return st;
   // incident fields
   double *elem = nullptr, *kw = nullptr;
+  double2* kc = nullptr;  // complex k (lossy background)
+  std::vector<double> kre(c->n_freq), kim(c->n_freq);
+  for (int l = 0; l < c->n_freq; ++l) {
+    kre[l] = c->alpha0 > 0 ? c->kc[l].x : c->kwave[l];
+    kim[l] = c->kc[l].y;
+  }
   FWI_CUDA(c, cudaMallocAsync(&elem, sizeof(double) * c->elem.size(), c->stream));
-  FWI_CUDA(c, cudaMallocAsync(&kw, sizeof(double) * c->kwave.size(), c->stream));
+  FWI_CUDA(c, cudaMallocAsync(&kw, sizeof(double) * 2 * c->n_freq, c->stream));
+  FWI_CUDA(c, cudaMallocAsync(&kc, sizeof(double2) * c->n_freq, c->stream));
   cudaError_t e = cudaMemcpyAsync(elem, c->elem.data(), sizeof(double) * c->elem.size(),
                                   cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(kw, c->kwave.data(), sizeof(double) * c->kwave.size(),
+    e = cudaMemcpyAsync(kw, kre.data(), sizeof(double) * c->n_freq, cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(kw + c->n_freq, kim.data(), sizeof(double) * c->n_freq,
                         cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(kc, c->kc.data(), sizeof(double2) * c->n_freq, cudaMemcpyHostToDevice,
+                        c->stream);
   if (e == cudaSuccess) {
     const long long total = c->N * c->n_rhs;
     if (c->dim == 3 && c->elem_length > 0.0)
       incident_line_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
-          (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->h,
-          c->elem_length, gauss_legendre12());
+          (cplx<T>*)c->p0, elem, kw, c->alpha0 > 0 ? kw + c->n_freq : nullptr, c->n_elem,
+          c->n_freq, c->nx, c->ny, c->nz, c->h, c->elem_length, gauss_legendre12());
+    else if (c->alpha0 > 0)
+      incident_lossy_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
+          (cplx<T>*)c->p0, elem, kc, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
     else
       incident_kernel<T><<<grid1d(total, 256, c->n_sm * 32), 256, 0, c->stream>>>(
           (cplx<T>*)c->p0, elem, kw, c->n_elem, c->n_freq, c->nx, c->ny, c->nz, c->dim, c->h);
@@ -367,6 +515,7 @@ fwi_status setup_t(fwi_ctx* c) {
   }
   cudaFreeAsync(elem, c->stream);
   cudaFreeAsync(kw, c->stream);
+  cudaFreeAsync(kc, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "incident fields");
   return FWI_OK;
@@ -398,7 +547,7 @@ fwi_status set_contrast(fwi_ctx* c, const void* m) {
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m) {
   Prof p(c, KC_MISC);
   contrast_kernel<<<grid1d(c->Ninv, 256, c->n_sm * 16), 256, 0, c->stream>>>(
-      (double2*)m, sos, alpha, c->Ninv, c->c0);
+      (double2*)m, sos, alpha, c->Ninv, c->c0, c->alpha0);
   FWI_CUDA(c, cudaGetLastError());
   return FWI_OK;
 }

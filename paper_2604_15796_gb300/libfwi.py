@@ -39,7 +39,7 @@ class fwi_problem_desc(Structure):
                 ("freq_hz", POINTER(c_double)), ("krylov_tol", c_double),
                 ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int),
                 ("n_tx", c_int), ("tx_angle", POINTER(c_double)), ("elem_length", c_double),
-                ("inv_factor", c_int)]
+                ("inv_factor", c_int), ("alpha0", c_double)]
 
 
 class fwi_solve_info(Structure):
@@ -185,12 +185,13 @@ class FwiError(RuntimeError):
 
 
 def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-              max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1):
+              max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0):
     """fwi_problem_desc from array-order ``shape`` ((Nz, Nx) or (Nz, Ny, Nx)).
     ``tx_angles``: steering angles [rad] of plane-wave transmits, or None for
     point transmits at every element.  ``elem_length``: 3-D line elements of
     that length along y [m] (0: point elements).  ``inv_factor``: inversion
     mesh of cells of inv_factor^d forward pixels (1: the forward mesh).
+    ``alpha0``: attenuation of the background [Np/m/Hz] (0: lossless).
     Returns (desc, keepalive) -- keep the second item alive while desc is used."""
     dim = len(shape)
     elem = np.ascontiguousarray(elem, dtype=np.float64)
@@ -210,6 +211,7 @@ def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1
     d.precision, d.max_batch = precision, max_batch
     d.elem_length = float(elem_length)
     d.inv_factor = int(inv_factor)
+    d.alpha0 = float(alpha0)
     tx = None
     if tx_angles is not None and len(tx_angles) > 0:
         tx = np.ascontiguousarray(tx_angles, dtype=np.float64)
@@ -268,7 +270,7 @@ class Context:
 
     def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
                  max_it=1000, max_batch=0, stream=None, tx_angles=None, elem_length=0.0,
-                 inv_factor=1):
+                 inv_factor=1, alpha0=0.0):
         import torch
         self.torch = torch
         self.shape = tuple(shape)
@@ -286,7 +288,8 @@ class Context:
         self.precision = precision
         self.field_dtype = torch.complex128 if precision == FWI_FP64 else torch.complex64
         self.desc, self._keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it,
-                                          max_batch, tx_angles, elem_length, inv_factor)
+                                          max_batch, tx_angles, elem_length, inv_factor,
+                                          alpha0)
         self.workspace_bytes = int(fwi_workspace_bytes(byref(self.desc)))
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -494,16 +497,17 @@ class Server:
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
                gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-               max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1):
+               max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0):
         """Queue a reconstruction; host numpy inputs (sos0 float64 of the inversion mesh,
         d_obs [n_freq][N_T][n_elem], complex64 for FWI_MIXED and complex128
         for FWI_FP64).  max_batch limits the right-hand sides per Krylov launch
         (0: all); tx_angles selects plane-wave transmits, elem_length 3-D line
-        elements, inv_factor an inversion mesh (sos0 and the result on it).
+        elements, inv_factor an inversion mesh (sos0 and the result on it),
+        alpha0 an attenuating background.
         Returns the request id."""
         req = fwi_request()
         desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch,
-                               tx_angles, elem_length, inv_factor)
+                               tx_angles, elem_length, inv_factor, alpha0)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
