@@ -168,11 +168,22 @@ FWI_API const char* fwi_last_error(const fwi_ctx* ctx);
 FWI_API fwi_status fwi_cancel(fwi_ctx* ctx);
 
 /* Contrast m = kappa/kappa0 - 1 (Eq. 1-3) from speed of sound and optional
-   attenuation: m = c0^2/c^2 - 1 + i alpha c0^2/(pi c).
-   sos: dev double [N] (m/s); alpha: dev double [N] (Np/m/Hz) or NULL;
-   m: dev c128 [N] (out). */
+   attenuation: m = c0^2/c^2 - 1 + i alpha c0^2/(pi c) for a lossless
+   background; with alpha0 > 0, rho0 kappa = 1/c^2 + i alpha/(pi c) over
+   rho0 kappa0 = 1/c0^2 + i alpha0/(pi c0), minus 1 (alpha NULL: every pixel
+   has alpha0).  sos: dev double [N_inv] (m/s); alpha: dev double [N_inv]
+   (Np/m/Hz) or NULL; m: dev c128 [N_inv] (out). */
 FWI_API fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos,
                                  const double* alpha, void* m);
+
+/* Speed of sound and attenuation from a contrast, the inverse of Eq. 1-3:
+   with rho0 kappa = (1/c0^2 + i alpha0/(pi c0)) (1 + m), c = 1/sqrt(Re(rho0
+   kappa)) and alpha = pi c Im(rho0 kappa) [Np/m/Hz] (attenuation
+   inversion: the complex contrast that fwi_admm_tv_step updates carries
+   both).  m: dev c128 [N_inv]; sos, alpha: dev double [N_inv] or NULL
+   (out). */
+FWI_API fwi_status fwi_sos_attenuation_from_contrast(fwi_ctx* ctx, const void* m, double* sos,
+                                                     double* alpha);
 
 /* Forward simulation F(m) (Eq. 4-5; Algorithm 1 "forward simulation"):
    solves A_l p = p0_{l,e}, A_l = I - K_l diag(m), for every transmit e and

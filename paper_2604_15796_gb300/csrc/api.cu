@@ -385,6 +385,14 @@ fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos, const double* 
   return contrast_from_sos(ctx, sos, alpha, m);
 }
 
+fwi_status fwi_sos_attenuation_from_contrast(fwi_ctx* ctx, const void* m, double* sos,
+                                             double* alpha) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!m) return fail(ctx, FWI_ERR_INVALID_ARG, "m is required");
+  ctx->err.clear();
+  return sos_attenuation_from_contrast(ctx, m, sos, alpha);
+}
+
 fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields, int warm_start, void* data,
                        fwi_solve_info* info) {
   if (!ctx) return FWI_ERR_INVALID_ARG;

@@ -139,6 +139,7 @@ fwi_status admm_init(fwi_ctx* c, const void* m0, void* g, void* u);
 fwi_status admm_step(fwi_ctx* c, void* m, void* g, void* u, const void* grad,
                      const fwi_admm_params* p, double* sos);
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m);
+fwi_status sos_attenuation_from_contrast(fwi_ctx* c, const void* m, double* sos, double* alpha);
 // tensor-core pixel contractions (jac_tc.cu)
 bool tc_usable(const fwi_ctx* c);
 size_t tc_bops_bytes(int n_elem, int n_freq);

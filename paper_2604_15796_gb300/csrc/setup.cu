@@ -376,6 +376,22 @@ __global__ void contrast_kernel(double2* m, const double* sos, const double* alp
   }
 }
 
+// c = 1/sqrt(Re q), alpha = pi c Im q with q = rho0 kappa0 (1 + m) (the
+// inverse of contrast_kernel).
+__global__ void sos_alpha_kernel(const double2* m, double* sos, double* alpha, long long n,
+                                 double c0, double alpha0) {
+  const double PI = 3.141592653589793238462643383279502884;
+  const double k0r = 1.0 / (c0 * c0), k0i = alpha0 / (PI * c0);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double ar = 1.0 + m[i].x, ai = m[i].y;
+    const double qr = k0r * ar - k0i * ai, qi = k0r * ai + k0i * ar;
+    const double c = 1.0 / sqrt(qr);
+    if (sos) sos[i] = c;
+    if (alpha) alpha[i] = PI * c * qi;
+  }
+}
+
 template <typename T>
 cudaError_t upload_twiddles(int L, void** dst, cudaStream_t s) {
   std::vector<cplx<T>> h(L);
@@ -542,6 +558,14 @@ fwi_status setup_operator(fwi_ctx* c) {
 
 fwi_status set_contrast(fwi_ctx* c, const void* m) {
   return c->fp64 ? set_contrast_t<double>(c, m) : set_contrast_t<float>(c, m);
+}
+
+fwi_status sos_attenuation_from_contrast(fwi_ctx* c, const void* m, double* sos, double* alpha) {
+  Prof p(c, KC_MISC);
+  sos_alpha_kernel<<<grid1d(c->Ninv, 256, c->n_sm * 16), 256, 0, c->stream>>>(
+      (const double2*)m, sos, alpha, c->Ninv, c->c0, c->alpha0);
+  FWI_CUDA(c, cudaGetLastError());
+  return FWI_OK;
 }
 
 fwi_status contrast_from_sos(fwi_ctx* c, const double* sos, const double* alpha, void* m) {

@@ -93,6 +93,7 @@ EXPORTS = {
     "fwi_last_error": (ctypes.c_char_p, [c_void_p]),
     "fwi_cancel": (c_int, [c_void_p]),
     "fwi_contrast_from_sos": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fwi_sos_attenuation_from_contrast": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "fwi_forward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p,
                             POINTER(fwi_solve_info)]),
     "fwi_adjoint": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, POINTER(fwi_solve_info)]),
@@ -154,6 +155,7 @@ fwi_destroy = _bind("fwi_destroy")
 fwi_last_error = _bind("fwi_last_error")
 fwi_cancel = _bind("fwi_cancel")
 fwi_contrast_from_sos = _bind("fwi_contrast_from_sos")
+fwi_sos_attenuation_from_contrast = _bind("fwi_sos_attenuation_from_contrast")
 fwi_forward = _bind("fwi_forward")
 fwi_adjoint = _bind("fwi_adjoint")
 fwi_gradient = _bind("fwi_gradient")
@@ -342,6 +344,16 @@ class Context:
         self._check(fwi_contrast_from_sos(self.handle, _dev(sos, f64, self.n_inv, "sos"),
                                           _dev(alpha, f64, self.n_inv, "alpha", True), _ptr(m)))
         return m
+
+    def sos_attenuation_from_contrast(self, m):
+        """(SoS [m/s], attenuation [Np/m/Hz]) of a contrast on the inversion
+        mesh, the inverse of contrast_from_sos."""
+        f64 = self.torch.float64
+        sos = self.torch.empty(self.inv_shape, dtype=f64, device="cuda")
+        alpha = self.torch.empty(self.inv_shape, dtype=f64, device="cuda")
+        self._check(fwi_sos_attenuation_from_contrast(self.handle, self._m(m), _ptr(sos),
+                                                      _ptr(alpha)))
+        return sos, alpha
 
     def forward(self, m, fields=None, warm_start=False, data=None, allow_nonconverged=False):
         rep = SolveReport(self.n_rhs)

@@ -88,3 +88,22 @@ def test_lossy_data_gradient_and_admm_step(lib, shape, fp64):
     assert rel_l2(to_np(sos) - w.c0, sos1 - w.c0) < tol_g
     assert rel_l2(to_np(g_gpu), g1) < tol_g
     assert rel_l2(to_np(u_gpu), u1) < tol_g
+
+
+@pytest.mark.parametrize("alpha0", [ALPHA0, 0.0])
+def test_sos_and_attenuation_from_the_contrast(lib, alpha0):
+    """Attenuation inversion output: the device's inverse of the contrast map
+    against the oracle's, and the round trip from (SoS, attenuation)."""
+    import torch
+    w, _ = _case((32, 32))
+    alpha = 2e-5 + 1e-5 * phantoms.complex_normal(w.shape, 3).real ** 2
+    m_ref = model.contrast_from_sos(w.sos, w.c0, alpha, alpha0)
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs, alpha0=alpha0)
+    m = ctx.contrast_from_sos(to_gpu(w.sos, torch.float64), to_gpu(alpha, torch.float64))
+    sos, att = ctx.sos_attenuation_from_contrast(m)
+    ctx.close()
+    assert rel_l2(to_np(m), m_ref) < 1e-13
+    assert rel_l2(to_np(sos), model.sos_from_contrast(m_ref, w.c0, alpha0)) < 1e-13
+    assert rel_l2(to_np(att), model.attenuation_from_contrast(m_ref, w.c0, alpha0)) < 1e-10
+    assert rel_l2(to_np(sos), w.sos) < 1e-13 and rel_l2(to_np(att), alpha) < 1e-10
+
