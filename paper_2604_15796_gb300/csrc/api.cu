@@ -7,6 +7,8 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ctx.cuh"
 #include "prof.cuh"
 
@@ -177,6 +179,13 @@ static void release(fwi_ctx* c) {
   cudaSetDevice(cur);
 }
 
+// NVTX range over one library call (visible in nsys / ncu timelines; a no-op
+// without a profiler attached).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+};
+
 extern "C" {
 
 const char* fwi_version(void) { return "libfwi 0.1 (sm_103a)"; }
@@ -196,6 +205,7 @@ fwi_status fwi_cancel(fwi_ctx* ctx) {
 }
 
 fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
+  CallRange nvtx_range("fwi_create");
   if (!out) return fail(nullptr, FWI_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   g_create_error.clear();
@@ -379,6 +389,7 @@ fwi_status fwi_destroy(fwi_ctx* ctx) {
 }
 
 fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos, const double* alpha, void* m) {
+  CallRange nvtx_range("fwi_contrast_from_sos");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!sos || !m) return fail(ctx, FWI_ERR_INVALID_ARG, "sos and m are required");
   ctx->err.clear();
@@ -387,6 +398,7 @@ fwi_status fwi_contrast_from_sos(fwi_ctx* ctx, const double* sos, const double* 
 
 fwi_status fwi_sos_attenuation_from_contrast(fwi_ctx* ctx, const void* m, double* sos,
                                              double* alpha) {
+  CallRange nvtx_range("fwi_sos_attenuation_from_contrast");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m) return fail(ctx, FWI_ERR_INVALID_ARG, "m is required");
   ctx->err.clear();
@@ -395,6 +407,7 @@ fwi_status fwi_sos_attenuation_from_contrast(fwi_ctx* ctx, const void* m, double
 
 fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields, int warm_start, void* data,
                        fwi_solve_info* info) {
+  CallRange nvtx_range("fwi_forward");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m) return fail(ctx, FWI_ERR_INVALID_ARG, "m is NULL");
   if (warm_start && !fields) return fail(ctx, FWI_ERR_INVALID_ARG, "warm start needs fields");
@@ -421,6 +434,7 @@ fwi_status fwi_forward(fwi_ctx* ctx, const void* m, void* fields, int warm_start
 
 fwi_status fwi_adjoint(fwi_ctx* ctx, const void* m, const void* src, void* lambda,
                        fwi_solve_info* info) {
+  CallRange nvtx_range("fwi_adjoint");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m || !src || !lambda) return fail(ctx, FWI_ERR_INVALID_ARG, "m, src, lambda are required");
   ctx->err.clear();
@@ -438,6 +452,7 @@ fwi_status fwi_adjoint(fwi_ctx* ctx, const void* m, const void* src, void* lambd
 fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs, void* grad,
                         double* misfit, void* data, fwi_solve_info* info_fwd,
                         fwi_solve_info* info_adj) {
+  CallRange nvtx_range("fwi_gradient");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m || !d_obs || !grad) return fail(ctx, FWI_ERR_INVALID_ARG, "m, d_obs, grad are required");
   ctx->err.clear();
@@ -465,6 +480,7 @@ fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs, void* gr
 
 fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void* grad,
                             const fwi_admm_params* p, double* sos_out) {
+  CallRange nvtx_range("fwi_admm_tv_step");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m || !g || !u || !grad || !p) return fail(ctx, FWI_ERR_INVALID_ARG, "missing argument");
   if (!(p->rho > 0) || p->lambda < 0 || p->gamma < 0 || p->n_cg < 0)
@@ -479,6 +495,7 @@ fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u, const void*
 }
 
 fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u) {
+  CallRange nvtx_range("fwi_admm_init");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!m0 || !g || !u) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   ctx->err.clear();
@@ -487,6 +504,7 @@ fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u) {
 
 static fwi_status apply_common(fwi_ctx* ctx, int kind, const void* m, int freq, int n_rhs,
                                const void* in, void* out) {
+  CallRange nvtx_range(kind == 0 ? "fwi_apply_K" : kind == 1 ? "fwi_apply_A" : "fwi_apply_AH");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!in || !out || (kind != 0 && !m)) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (in == out) return fail(ctx, FWI_ERR_INVALID_ARG, "in and out must not alias");
@@ -509,6 +527,7 @@ fwi_status fwi_apply_AH(fwi_ctx* ctx, const void* m, int freq, int n_rhs, const 
 }
 
 fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y) {
+  CallRange nvtx_range("fwi_jac_forward");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!a || !y) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
@@ -521,6 +540,7 @@ fwi_status fwi_jac_forward(fwi_ctx* ctx, const void* a, void* y) {
 }
 
 fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
+  CallRange nvtx_range("fwi_jac_adjoint");
   if (!ctx) return FWI_ERR_INVALID_ARG;
   if (!y || !z) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");

@@ -6,7 +6,8 @@
   its tensor memory and returns; the call reports FWI_ERR_CUDA and the
   context gives the same data as before on the next call;
 * cancellation from another host thread stops a running solve at its next
-  host check (FWI_ERR_CANCELLED), and the next solve runs to the end."""
+  host check (FWI_ERR_CANCELLED), and the next solve runs to the end;
+* a non-finite input is reported (FWI_ERR_NONFINITE) without a fault."""
 import threading
 import time
 
@@ -74,3 +75,22 @@ def test_cancel_stops_a_running_solve(lib):
     ctx.close()
     assert rep.max_iters > 0 and rep.info.n_not_converged == 0
     assert cancelled_after < full
+
+
+def test_nonfinite_input_is_reported(lib):
+    """A NaN in the contrast makes every right-hand side non-finite: the
+    bounded BiCGSTAB marks them, the call reports FWI_ERR_NONFINITE, and the
+    context solves the next, finite, contrast."""
+    import torch
+    w = small_workload((32, 32), n_elem=4)
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs)
+    m = to_gpu(contrast(w), torch.complex128)
+    m_bad = m.clone()
+    m_bad[3, 5] = complex(float("nan"), 0.0)
+    with pytest.raises(lib.FwiError) as err:
+        ctx.forward(m_bad)
+    assert err.value.status == lib.FWI_ERR_NONFINITE
+    rep = ctx.forward(m)
+    ctx.close()
+    assert rep.max_iters > 0 and rep.info.n_not_converged == 0
+
