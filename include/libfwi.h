@@ -304,6 +304,12 @@ FWI_API fwi_status fwi_server_submit(fwi_server* s, const fwi_request* r, long l
    NULL; res: host or NULL.  Each id can be waited for once. */
 FWI_API fwi_status fwi_server_wait(fwi_server* s, long long id, double* sos_out,
                                    fwi_request_result* res);
+/* Cancel request id: a queued request leaves the queue at once; a running
+   one stops at its solve's next host check or before its next iteration.
+   Either completes with status FWI_ERR_CANCELLED and no SoS (its wait
+   returns that status); a finished request keeps its result.  Thread-safe.
+   FWI_ERR_INVALID_ARG for an unknown or already waited id. */
+FWI_API fwi_status fwi_server_cancel(fwi_server* s, long long id);
 /* Current admitted count, queued count and admitted bytes (any may be NULL). */
 FWI_API fwi_status fwi_server_stats(fwi_server* s, int* active, int* queued, size_t* bytes);
 /* Finish every submitted request, then release the workers. */

@@ -2,6 +2,8 @@
 // (Algorithm 1) over several contexts and CUDA streams, with FIFO first-fit
 // admission by device-memory footprint.  Host code only; every step of a
 // reconstruction runs through the library's own entry points.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -37,6 +39,8 @@ struct Request {
   fwi_request_result res{};
   bool done = false;
   bool waited = false;
+  std::atomic<bool> cancelled{false};
+  fwi_ctx* ctx = nullptr;  // while running (guarded by the server's mutex)
 };
 
 // Footprint of a request: context workspace plus the request's vectors.
@@ -84,8 +88,13 @@ void run_request(fwi_server* srv, Request& r) {
     r.desc.elem_pos = r.elem.data();
     r.desc.freq_hz = r.freq.data();
     r.desc.tx_angle = r.tx.empty() ? nullptr : r.tx.data();
+    if (r.cancelled.load()) { status = FWI_ERR_CANCELLED; break; }
     status = fwi_create(&r.desc, st, &ctx);
     if (status != FWI_OK) break;
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      r.ctx = ctx;  // fwi_server_cancel can now interrupt its solves
+    }
     const size_t nd = r.d_obs.size();
     const size_t gsz = (size_t)r.desc.dim * r.n * 16;
     bool bad = false;
@@ -103,6 +112,8 @@ void run_request(fwi_server* srv, Request& r) {
     double iters_sum = 0.0;
     int iters_n = 0;
     for (int k = 0; k < r.n_iter; ++k) {
+      // a cancel between calls (a call's own start clears the context's flag)
+      if (r.cancelled.load()) { status = FWI_ERR_CANCELLED; break; }
       double mis = 0.0;
       fwi_solve_info inf[2];
       std::memset(inf, 0, sizeof(inf));
@@ -132,7 +143,13 @@ void run_request(fwi_server* srv, Request& r) {
   } while (0);
   for (void* p : {m, g, u, grad, sos, sos0, dobs})
     if (p) cudaFreeAsync(p, st);
-  if (ctx) fwi_destroy(ctx);
+  if (ctx) {
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      r.ctx = nullptr;
+    }
+    fwi_destroy(ctx);
+  }
   if (st) {
     cudaStreamSynchronize(st);
     cudaStreamDestroy(st);
@@ -265,6 +282,35 @@ fwi_status fwi_server_wait(fwi_server* s, long long id, double* sos_out, fwi_req
   if (sos_out && !r->sos_out.empty())
     std::memcpy(sos_out, r->sos_out.data(), sizeof(double) * r->sos_out.size());
   return (fwi_status)r->res.status;
+}
+
+fwi_status fwi_server_cancel(fwi_server* s, long long id) {
+  if (!s) return FWI_ERR_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end() || it->second->waited)
+      return fail(nullptr, FWI_ERR_INVALID_ARG, "unknown request id");
+    const std::shared_ptr<Request>& r = it->second;
+    if (r->done) return FWI_OK;  // finished already: its result stands
+    r->cancelled.store(true);
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q != s->queue.end()) {
+      // still queued: leaves the queue, completed as cancelled
+      s->queue.erase(q);
+      r->t_admit = r->t_done = Clock::now();
+      r->res.queue_ms = ms_between(r->t_submit, r->t_done);
+      r->res.run_ms = 0.0;
+      r->res.latency_ms = r->res.queue_ms;
+      r->res.status = FWI_ERR_CANCELLED;
+      r->done = true;
+    } else if (r->ctx) {
+      fwi_cancel(r->ctx);  // running: its solve stops at the next host check
+    }
+  }
+  s->cv_done.notify_all();
+  s->cv_work.notify_all();
+  return FWI_OK;
 }
 
 fwi_status fwi_server_stats(fwi_server* s, int* active, int* queued, size_t* bytes) {

@@ -114,6 +114,7 @@ EXPORTS = {
     "fwi_server_submit": (c_int, [c_void_p, POINTER(fwi_request), POINTER(ctypes.c_longlong)]),
     "fwi_server_wait": (c_int, [c_void_p, ctypes.c_longlong, POINTER(c_double),
                                 POINTER(fwi_request_result)]),
+    "fwi_server_cancel": (c_int, [c_void_p, ctypes.c_longlong]),
     "fwi_server_stats": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_size_t)]),
     "fwi_server_destroy": (c_int, [c_void_p]),
     "fwi_get_tuning": (c_int, [c_void_p, POINTER(fwi_tuning)]),
@@ -170,6 +171,7 @@ fwi_contract_pixels_noalloc = _bind("fwi_contract_pixels_noalloc")
 fwi_server_create = _bind("fwi_server_create")
 fwi_server_submit = _bind("fwi_server_submit")
 fwi_server_wait = _bind("fwi_server_wait")
+fwi_server_cancel = _bind("fwi_server_cancel")
 fwi_server_stats = _bind("fwi_server_stats")
 fwi_server_destroy = _bind("fwi_server_destroy")
 fwi_get_tuning = _bind("fwi_get_tuning")
@@ -557,6 +559,13 @@ class Server:
         if st == FWI_ERR_INVALID_ARG and res.status == FWI_OK:
             raise FwiError(st, fwi_last_error(None).decode())
         return (sos if out["status"] == FWI_OK else None), out
+
+    def cancel(self, rid):
+        """Cancel request ``rid`` (queued or running); its wait then returns
+        (None, result with status FWI_ERR_CANCELLED)."""
+        st = fwi_server_cancel(self.handle, ctypes.c_longlong(rid))
+        if st != FWI_OK:
+            raise FwiError(st, fwi_last_error(None).decode())
 
     def stats(self):
         a, q, b = c_int(), c_int(), c_size_t()

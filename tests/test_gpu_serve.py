@@ -126,3 +126,35 @@ def test_admission_respects_the_budget(lib):
     assert e.value.status == lib.FWI_ERR_NOMEM
     small.close()
     srv.close()
+
+
+def test_cancelled_requests(lib):
+    """A queued request cancelled leaves at once; a running one stops at its
+    next check; the request behind them runs as if alone."""
+    import time
+    reqs = _requests()
+    w1, s1, d1, p1 = reqs[1]
+    w0, s0, d0, p0 = reqs[0]
+    w2, s2, d2, p2 = reqs[2]
+    alone = lib.Server(max_active=1)
+    ref, _ = alone.wait(alone.submit(w2.shape, w2.h, w2.c0, w2.elem, w2.freqs, s2, d2, **p2))
+    alone.close()
+    srv = lib.Server(max_active=1)
+    # a: far more iterations than the test waits for (a few ms each)
+    a = srv.submit(w1.shape, w1.h, w1.c0, w1.elem, w1.freqs, s1, d1, **dict(p1, n_iter=20000))
+    b = srv.submit(w0.shape, w0.h, w0.c0, w0.elem, w0.freqs, s0, d0, **p0)
+    c = srv.submit(w2.shape, w2.h, w2.c0, w2.elem, w2.freqs, s2, d2, **p2)
+    srv.cancel(b)                       # queued behind a
+    t0 = time.perf_counter()
+    while srv.stats()[0] == 0 and time.perf_counter() - t0 < 30.0:
+        time.sleep(0.01)                # until a is admitted
+    time.sleep(0.3)
+    srv.cancel(a)                       # running
+    sa, ra = srv.wait(a)
+    sb, rb = srv.wait(b)
+    sc, rc = srv.wait(c)
+    srv.close()
+    assert rb["status"] == lib.FWI_ERR_CANCELLED and sb is None and rb["run_ms"] == 0.0
+    assert ra["status"] == lib.FWI_ERR_CANCELLED and sa is None
+    assert ra["run_ms"] < 60e3
+    assert rc["status"] == 0 and rel_l2(sc, ref) < 1e-12
