@@ -9,7 +9,9 @@ the compiled library raises.
 torch tensors (device memory and the current CUDA stream come from torch).
 """
 import ctypes
+import json
 import os
+import time
 from ctypes import POINTER, Structure, byref, c_double, c_float, c_int, c_size_t, c_void_p
 
 import numpy as np
@@ -267,6 +269,45 @@ class SolveReport:
     def max_iters(self):
         return int(self.info.max_iters)
 
+    def record(self):
+        """The report's summary for the call log."""
+        return {"device_ms": self.device_ms, "max_iters": self.max_iters,
+                "not_converged": int(self.info.n_not_converged),
+                "max_rel_resid": float(self.info.max_rel_resid)}
+
+
+_call_log = {"file": None, "owned": False}
+
+
+def set_call_log(target):
+    """Append one JSON line per solve, gradient and ADMM-TV call to
+    ``target`` (a path, an open text file, or None to stop): the call, its
+    status, wall time, the device time and Krylov iterations of each solve,
+    the grid and the number of right-hand sides.  The environment variable
+    FWI_CALL_LOG=<path> enables it at import."""
+    if _call_log["owned"] and _call_log["file"] is not None:
+        _call_log["file"].close()
+    if target is None:
+        _call_log.update(file=None, owned=False)
+    elif isinstance(target, (str, os.PathLike)):
+        _call_log.update(file=open(target, "a", buffering=1), owned=True)
+    else:
+        _call_log.update(file=target, owned=False)
+
+
+def _log_call(call, ctx, status, wall_s, **reports):
+    f = _call_log["file"]
+    if f is None:
+        return
+    rec = {"call": call, "status": STATUS_NAMES.get(status, status), "wall_ms": 1e3 * wall_s,
+           "grid": list(ctx.shape), "n_rhs": ctx.n_rhs}
+    rec.update({k: r.record() for k, r in reports.items()})
+    f.write(json.dumps(rec) + "\n")
+
+
+if os.environ.get("FWI_CALL_LOG"):
+    set_call_log(os.environ["FWI_CALL_LOG"])
+
 
 class Context:
     """Owns one fwi_ctx.  Tensors are torch CUDA tensors (complex64 fields for
@@ -360,25 +401,33 @@ class Context:
     def forward(self, m, fields=None, warm_start=False, data=None, allow_nonconverged=False):
         rep = SolveReport(self.n_rhs)
         ok = (FWI_OK, FWI_ERR_NOT_CONVERGED) if allow_nonconverged else (FWI_OK,)
-        st = fwi_forward(self.handle, self._m(m), self._fields(fields, "fields", True),
-                         int(warm_start), self._data(data, "data", True), byref(rep.info))
+        args = (self._m(m), self._fields(fields, "fields", True), int(warm_start),
+                self._data(data, "data", True))
+        t0 = time.perf_counter()
+        st = fwi_forward(self.handle, *args, byref(rep.info))
+        _log_call("forward", self, st, time.perf_counter() - t0, forward=rep)
         self._check(st, ok)
         rep.code = st
         return rep
 
     def adjoint(self, m, src, lam):
         rep = SolveReport(self.n_rhs)
-        self._check(fwi_adjoint(self.handle, self._m(m), self._fields(src, "src"),
-                                self._fields(lam, "lam"), byref(rep.info)))
+        args = (self._m(m), self._fields(src, "src"), self._fields(lam, "lam"))
+        t0 = time.perf_counter()
+        st = fwi_adjoint(self.handle, *args, byref(rep.info))
+        _log_call("adjoint", self, st, time.perf_counter() - t0, adjoint=rep)
+        self._check(st)
         return rep
 
     def gradient(self, m, d_obs, grad, data=None):
         rf, ra = SolveReport(self.n_rhs), SolveReport(self.n_rhs)
         mis = c_double(0.0)
-        self._check(fwi_gradient(self.handle, self._m(m), self._data(d_obs, "d_obs"),
-                                 self._m(grad, "grad"), byref(mis),
-                                 self._data(data, "data", True), byref(rf.info),
-                                 byref(ra.info)))
+        args = (self._m(m), self._data(d_obs, "d_obs"), self._m(grad, "grad"))
+        dp = self._data(data, "data", True)
+        t0 = time.perf_counter()
+        st = fwi_gradient(self.handle, *args, byref(mis), dp, byref(rf.info), byref(ra.info))
+        _log_call("gradient", self, st, time.perf_counter() - t0, forward=rf, adjoint=ra)
+        self._check(st)
         return float(mis.value), rf, ra
 
     def admm_init(self, m0):
@@ -396,9 +445,13 @@ class Context:
         m_ref_p = self._m(m_ref, "m_ref", True)
         p.m_ref = None if m_ref_p is None else m_ref_p.value
         c128, dn = self.torch.complex128, self.dim * self.n_inv
-        self._check(fwi_admm_tv_step(self.handle, self._m(m), _dev(g, c128, dn, "g"),
-                                     _dev(u, c128, dn, "u"), self._m(grad, "grad"), byref(p),
-                                     _dev(sos, self.torch.float64, self.n_inv, "sos", True)))
+        args = (self._m(m), _dev(g, c128, dn, "g"), _dev(u, c128, dn, "u"),
+                self._m(grad, "grad"))
+        sp = _dev(sos, self.torch.float64, self.n_inv, "sos", True)
+        t0 = time.perf_counter()
+        st = fwi_admm_tv_step(self.handle, *args, byref(p), sp)
+        _log_call("admm_tv_step", self, st, time.perf_counter() - t0)
+        self._check(st)
 
     def apply(self, kind, vin, freq, m=None):
         nb = vin.shape[0]

@@ -44,3 +44,29 @@ def test_device_arguments_of_the_wrong_layout_are_rejected():
     ctx.forward(torch.full_like(m, 0.01), data=data)
     assert bool(torch.isfinite(torch.view_as_real(data)).all())
     ctx.close()
+
+
+def test_call_log_of_device_calls(tmp_path):
+    import json
+    import torch
+    from paper_2604_15796_gb300 import build, libfwi
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    w = small_workload((16, 16), n_elem=3, freqs=(2e6,))
+    ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs)
+    m = torch.full(w.shape, 0.01 + 0j, dtype=torch.complex128, device="cuda")
+    path = tmp_path / "calls.jsonl"
+    libfwi.set_call_log(str(path))
+    try:
+        data = ctx.empty_data()
+        ctx.forward(m, data=data)
+        grad = torch.empty(w.shape, dtype=torch.complex128, device="cuda")
+        ctx.gradient(m, data, grad)
+    finally:
+        libfwi.set_call_log(None)
+        ctx.close()
+    recs = [json.loads(line) for line in path.read_text().splitlines()]
+    assert [r["call"] for r in recs] == ["forward", "gradient"]
+    assert all(r["status"] == "OK" for r in recs)
+    assert recs[0]["forward"]["max_iters"] > 0 and recs[1]["adjoint"]["device_ms"] > 0
