@@ -62,7 +62,7 @@ def test_call_log_of_device_calls(tmp_path):
         data = ctx.empty_data()
         ctx.forward(m, data=data)
         grad = torch.empty(w.shape, dtype=torch.complex128, device="cuda")
-        ctx.gradient(m, data, grad)
+        ctx.gradient(m, (1.1 * data).contiguous(), grad)
     finally:
         libfwi.set_call_log(None)
         ctx.close()
