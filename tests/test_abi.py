@@ -89,3 +89,36 @@ def test_binding_rejects_tensors_that_do_not_match_the_documented_layout():
               torch.zeros(4, 2, dtype=torch.complex128).t()[0]):  # strided view
         with pytest.raises(ValueError, match="^m: expected"):
             libfwi._dev(t, torch.complex128, 4, "m")
+
+
+def test_the_boundary_is_plain_c(tmp_path):
+    """include/libfwi.h compiles as C11 with every warning an error, and a C
+    program links against the library and calls a host-only entry point."""
+    import shutil
+    import subprocess
+    from paper_2604_15796_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        import pytest
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "t.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "libfwi.h"
+int main(void) {
+  double elem[4] = {-1e-4, -1e-4, 1e-4, -1e-4}, f[1] = {1e6};
+  fwi_problem_desc d = {0};
+  d.dim = 2; d.n[0] = 16; d.n[1] = 1; d.n[2] = 16; d.h = 1e-4; d.c0 = 1540.0;
+  d.n_elem = 2; d.elem_pos = elem; d.n_freq = 1; d.freq_hz = f;
+  printf("%s %zu\n", fwi_version(), fwi_workspace_bytes(&d));
+  return 0;
+}
+''')
+    exe = tmp_path / "t"
+    libdir = os.path.dirname(lib)
+    subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-I",
+                    os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lfwi",
+                    "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert out[0] == "libfwi" and int(out[-1]) > 0
