@@ -311,7 +311,17 @@ if os.environ.get("FWI_CALL_LOG"):
 
 class Context:
     """Owns one fwi_ctx.  Tensors are torch CUDA tensors (complex64 fields for
-    FWI_MIXED, complex128 for FWI_FP64; m, grad, g, u always complex128)."""
+    FWI_MIXED, complex128 for FWI_FP64; m, grad, g, u always complex128).
+
+    shape: grid in array order ((Nz, Nx) or (Nz, Ny, Nx)); h: pixel [m];
+    c0: background SoS [m/s]; elem: element positions [N_E, d]; freqs [Hz];
+    tol, max_it: BiCGSTAB stopping rule; max_batch: RHS per Krylov launch
+    (0: all); stream: the torch stream the library enqueues on;
+    tx_angles: plane-wave transmits [rad] instead of point transmits
+    (data [n_freq][N_T][N_E]); elem_length: 3-D line elements [m];
+    inv_factor: inversion mesh of inv_factor^d pixels per cell (m, grad,
+    g, u, SoS on it: ``inv_shape``); alpha0: background attenuation
+    [Np/m/Hz]."""
 
     def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
                  max_it=1000, max_batch=0, stream=None, tx_angles=None, elem_length=0.0,
