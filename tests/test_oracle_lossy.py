@@ -2,13 +2,13 @@
 background compressibility, Sec. II): the complex wavenumber, the Green's
 functions at complex k (Helmholtz equation, decay, the closed-form cell
 integrals against quadrature over the disc / ball), the contrast <-> SoS and
-attenuation maps, and the gradient against finite differences in a lossy
-medium."""
+attenuation maps, the gradient against finite differences in a lossy
+medium, and the whole solve against the Bessel series of a lossy cylinder."""
 import numpy as np
 import pytest
 
 import oracle
-from oracle import green, inverse, model
+from oracle import green, inverse, model, operator
 from paper_2604_15796_gb300 import phantoms
 from test_oracle_green import _ball_integral, _disc_integral
 
@@ -110,3 +110,42 @@ def test_lossy_gradient_and_reciprocity():
     p.extra["alpha0"] = 0.0
     _, d0 = inverse.forward_model(1.3 * m, p, "lu")
     assert not np.allclose(d, d0, rtol=1e-2)
+
+
+def test_lossy_cylinder_converges_to_bessel_series():
+    """The whole lossy solve against an analytic solution: a cylinder with its
+    own speed and attenuation in an attenuating background, the Bessel-series
+    field with both wavenumbers complex (the addition theorem and the
+    interface conditions hold unchanged for Im k > 0).  The wavenumbers are
+    computed here from the two media, k^2 = omega^2 (1/c^2 + i alpha/(pi c)),
+    and the contrast is k1^2/k0^2 - 1; the VIE data converge to the series as
+    the pixel shrinks, and the lossless series is far from them."""
+    from test_oracle_operator import _cylinder_field
+    c0, a0, c1, a1, f = C0, 2e-4, 1480.0, 4e-4, 1.0e6
+    w = 2 * np.pi * f
+    k0 = w * np.sqrt(1 / c0 ** 2 + 1j * a0 / (np.pi * c0))
+    k1 = w * np.sqrt(1 / c1 ** 2 + 1j * a1 / (np.pi * c1))
+    assert k0.imag > 0.04 * k0.real and k1.imag > 0.08 * k1.real
+    R, width = 1.2e-3, 4.8e-3
+    errs = []
+    for npx in (48, 96, 192):
+        h = width / npx
+        elem = np.array([[-1.0e-3, -h], [0.0, -h], [1.3e-3, -h]])
+        prob = oracle.Problem((npx, npx), h, c0, elem, np.array([f]))
+        prob.extra["alpha0"] = a0
+        x = model.pixel_centres(prob.shape, h)
+        centre = np.array([0.0, width / 2.0])
+        inside = np.hypot(x[:, 0] - centre[0], x[:, 1] - centre[1]) < R
+        m = np.where(inside, k1 * k1 / (k0 * k0) - 1.0, 0.0).astype(np.complex128)
+        fields = operator.solve_forward(m.reshape(prob.shape), prob, "bicgstab", tol=1e-11)
+        data = inverse.forward_data(m, fields, prob)[0]
+        ref = np.empty_like(data)
+        lossless = np.empty_like(data)
+        for e in range(3):
+            ref[e] = _cylinder_field(k0, k1, R, elem[e] - centre, elem - centre)[1]
+            lossless[e] = _cylinder_field(k0.real, k1.real, R, elem[e] - centre,
+                                          elem - centre)[1]
+        errs.append(np.linalg.norm(data - ref) / np.linalg.norm(ref))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 0.5 * errs[1]
+    assert errs[2] < 0.05, errs
+    assert np.linalg.norm(data - lossless) > 5 * errs[2] * np.linalg.norm(ref)
