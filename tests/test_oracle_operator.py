@@ -3,7 +3,9 @@
 definition, a single-pixel scatterer whose discrete solution has a closed
 form (with the self term taken from quadrature, not from the oracle), dense
 LU against two Krylov methods, the homogeneous medium, and convergence to
-the Bessel-series solution of a penetrable cylinder as h -> 0."""
+the Bessel-series solution of a penetrable cylinder and to the
+spherical-Bessel series of a penetrable sphere (lossless and lossy) as
+h -> 0."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -156,3 +158,69 @@ def test_penetrable_cylinder_converges_to_bessel_series():
         errs.append(np.linalg.norm(data - ref) / np.linalg.norm(ref))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 0.05, errs
+
+
+def _sphere_field(k0, k1, R, xs, pts, n_terms=40):
+    """Scattered field of a unit point source exp(ik0 r)/(4 pi r) at xs by a
+    homogeneous sphere of radius R centred at the origin (wavenumber k1
+    inside): the spherical-Bessel series with continuity of the field and of
+    its radial derivative at r = R, using
+    exp(ik|x - xs|)/(4 pi |x - xs|) = (ik/4pi) sum (2n+1) j_n(kr) h_n(k rs) P_n(cos g)
+    for r < rs.  Also returns that expansion of the incident field (a check of
+    the helper against the closed form)."""
+    rs, r = np.linalg.norm(xs), np.linalg.norm(pts, axis=1)
+    cosg = (pts @ xs) / (r * rs)
+    n = np.arange(n_terms + 1)
+    jn, yn = special.spherical_jn, special.spherical_yn
+
+    def hn(nn, z, d=False):
+        return jn(nn, z, d) + 1j * yn(nn, z, d)
+    c = hn(n, k0 * rs)
+    j0, j0p = jn(n, k0 * R), jn(n, k0 * R, True)
+    j1, j1p = jn(n, k1 * R), jn(n, k1 * R, True)
+    h0, h0p = hn(n, k0 * R), hn(n, k0 * R, True)
+    a = c * (k1 * j1p * j0 - k0 * j1 * j0p) / (k0 * j1 * h0p - k1 * j1p * h0)
+    P = np.stack([special.eval_legendre(q, cosg) for q in n], axis=1)
+    w = (1j * k0 / (4 * np.pi)) * (2 * n + 1)[None] * P
+    sc = (w * a[None] * hn(n[None], k0 * r[:, None])).sum(1)
+    inc = (w * c[None] * jn(n[None], k0 * r[:, None])).sum(1)
+    return sc, inc
+
+
+@pytest.mark.parametrize("lossy", [False, True])
+def test_penetrable_sphere_converges_to_spherical_bessel_series(lossy):
+    """3-D counterpart of the cylinder: the VIE data of a sphere converge to
+    the series as the voxel shrinks, in a lossless and in an attenuating
+    background (wavenumbers computed here from the two media,
+    k^2 = omega^2 (1/c^2 + i alpha/(pi c)), contrast k1^2/k0^2 - 1)."""
+    c0, c1, f = 1540.0, 1480.0, 1.0e6
+    a0, a1 = (2e-4, 4e-4) if lossy else (0.0, 0.0)
+    w = 2 * np.pi * f
+    k0 = w * np.sqrt(1 / c0 ** 2 + 1j * a0 / (np.pi * c0))
+    k1 = w * np.sqrt(1 / c1 ** 2 + 1j * a1 / (np.pi * c1))
+    if not lossy:
+        k0, k1 = k0.real, k1.real
+    R, width = 0.9e-3, 3.2e-3
+    centre = np.array([0.0, 0.0, width / 2.0])
+    # the helper's incident expansion is the closed-form Green's function
+    xs = np.array([-0.8e-3, 0.0, -0.05e-3]) - centre
+    pts = np.array([[0.3e-3, 0.2e-3, 0.1e-3], [-0.5e-3, 0.4e-3, -0.6e-3]])
+    _, inc = _sphere_field(k0, k1, R, xs, pts)
+    dist = np.linalg.norm(pts - xs, axis=1)
+    assert np.allclose(inc, np.exp(1j * k0 * dist) / (4 * np.pi * dist), rtol=1e-10)
+    errs = []
+    for npx in (32, 48, 64):
+        h = width / npx
+        elem = np.array([[-0.8e-3, 0.0, -h], [0.0, 0.3e-3, -h], [0.9e-3, -0.2e-3, -h]])
+        prob = oracle.Problem((npx, npx, npx), h, c0, elem, np.array([f]))
+        prob.extra["alpha0"] = a0
+        x = model.pixel_centres(prob.shape, h)
+        inside = np.linalg.norm(x - centre, axis=1) < R
+        m = np.where(inside, k1 * k1 / (k0 * k0) - 1.0, 0.0).astype(np.complex128)
+        fields = operator.solve_forward(m.reshape(prob.shape), prob, "bicgstab", tol=1e-11)
+        data = inverse.forward_data(m, fields, prob)[0]
+        ref = np.array([_sphere_field(k0, k1, R, elem[e] - centre, elem - centre)[0]
+                        for e in range(3)])
+        errs.append(np.linalg.norm(data - ref) / np.linalg.norm(ref))
+    assert errs[0] > errs[1] > errs[2], errs
+    assert errs[2] < 0.04, errs
