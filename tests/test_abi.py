@@ -73,6 +73,42 @@ def test_plane_wave_descriptor_sizes_and_checks():
     del k0, k1, k2
 
 
+def test_inversion_mesh_attenuation_and_element_length_checks():
+    """The inversion-mesh factor must divide every grid size (<= 1: the
+    forward mesh); alpha0 and elem_length must be finite and >= 0; an
+    inversion mesh adds one forward-mesh vector and a lossy background one
+    data-space buffer per frequency to the workspace (0 bytes: rejected)."""
+    import numpy as np
+    from paper_2604_15796_gb300 import build, libfwi
+    build.build()
+    elem = np.stack([np.linspace(-1e-3, 1e-3, 8), np.full(8, -1e-4)], axis=1)
+    freqs = [1e6, 2e6]
+
+    def nbytes(shape, e=elem, **kw):
+        d, keep = libfwi.make_desc(shape, 1e-4, 1540.0, e, freqs, **kw)
+        n = libfwi.fwi_workspace_bytes(ctypes.byref(d))
+        del keep
+        return n
+    base = nbytes((32, 32))
+    assert base > 0
+    for r in (0, -2, 1):
+        assert nbytes((32, 32), inv_factor=r) == base
+    assert nbytes((32, 32), inv_factor=2) >= base + 32 * 32 * 16
+    assert nbytes((32, 32), inv_factor=4) == nbytes((32, 32), inv_factor=2)
+    assert nbytes((32, 32), inv_factor=3) == 0
+    assert nbytes((32, 64), inv_factor=64) == 0
+    e3 = np.stack([np.linspace(-1e-3, 1e-3, 8), np.zeros(8), np.full(8, -1e-4)], axis=1)
+    assert nbytes((32, 16, 16), e3, inv_factor=16) > 0
+    assert nbytes((32, 16, 16), e3, inv_factor=32) == 0
+    ne = elem.shape[0]
+    assert nbytes((32, 32), alpha0=1e-4) == base + len(freqs) * (ne * ne + 1) * 16
+    assert nbytes((32, 32), alpha0=0.0) == base
+    for bad in (-1e-4, float("nan"), float("inf")):
+        assert nbytes((32, 32), alpha0=bad) == 0
+        assert nbytes((32, 16, 16), e3, elem_length=bad) == 0
+    assert nbytes((32, 16, 16), e3, elem_length=1e-2) == nbytes((32, 16, 16), e3)
+
+
 def test_binding_rejects_tensors_that_do_not_match_the_documented_layout():
     """The binding checks device, dtype, element count and contiguity of a
     tensor argument before its pointer reaches the library (CPU tensors:
