@@ -158,3 +158,19 @@ int main(void) {
                     "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
     assert out[0] == "libfwi" and int(out[-1]) > 0
+
+
+def test_a_missing_library_fails_loudly(tmp_path):
+    """Without the compiled library the binding raises (no CPU fallback)."""
+    import subprocess
+    import sys
+    missing = str(tmp_path / "libfwi.so")
+    code = ("from paper_2604_15796_gb300 import libfwi\n"
+            "try:\n"
+            f"    libfwi.load({missing!r})\n"
+            "except OSError as e:\n"
+            "    print('raised:', e)\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                         check=True).stdout
+    assert out.startswith("raised: libfwi.so not built"), out
