@@ -73,13 +73,15 @@ typedef struct fwi_problem_desc {
                               2*Nx, 2*Ny (3D), 2*Nz must be a supported FFT
                               length: 16, 32, 64, 128, 192, 256, 320, 384,
                               512, 640, 768, 1024. */
-  double h;                /* pixel / voxel edge [m] */
-  double c0;               /* background speed of sound [m/s], lossless */
+  double h;                /* pixel / voxel edge [m], finite and > 0 */
+  double c0;               /* background speed of sound [m/s], finite and
+                              > 0 */
   int n_elem;              /* number of array elements (N_T = N_R) */
-  const double* elem_pos;  /* host [n_elem][dim], (x, z) or (x, y, z) [m];
-                              copied in fwi_create */
+  const double* elem_pos;  /* host [n_elem][dim], (x, z) or (x, y, z) [m],
+                              finite; read and copied in fwi_create */
   int n_freq;
-  const double* freq_hz;   /* host [n_freq]; copied in fwi_create */
+  const double* freq_hz;   /* host [n_freq], finite and > 0; copied in
+                              fwi_create */
   double krylov_tol;       /* BiCGSTAB relative residual (<= 0: 1e-6) */
   int krylov_max_it;       /* BiCGSTAB iteration cap (<= 0: 1000) */
   int precision;           /* fwi_precision */

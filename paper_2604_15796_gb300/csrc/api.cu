@@ -62,11 +62,13 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
   L.lx = 2 * L.nx; L.ly = (d->dim == 3) ? 2 * L.ny : 1; L.lz = 2 * L.nz;
   if (!fft_len_ok(L.lx) || !fft_len_ok(L.lz) || (d->dim == 3 && !fft_len_ok(L.ly)))
     return bad("2*n must be one of 16,32,64,128,192,256,320,384,512,640,768,1024");
-  if (!(d->h > 0) || !(d->c0 > 0)) return bad("h and c0 must be positive");
+  if (!(d->h > 0) || !(d->c0 > 0) || !std::isfinite(d->h) || !std::isfinite(d->c0))
+    return bad("h and c0 must be finite and positive");
   if (d->n_elem <= 0 || !d->elem_pos) return bad("n_elem must be positive with elem_pos");
   if (d->n_freq <= 0 || !d->freq_hz) return bad("n_freq must be positive with freq_hz");
   for (int l = 0; l < d->n_freq; ++l)
-    if (!(d->freq_hz[l] > 0)) return bad("frequencies must be positive");
+    if (!(d->freq_hz[l] > 0) || !std::isfinite(d->freq_hz[l]))
+      return bad("frequencies must be finite and positive");
   if (d->precision != FWI_MIXED && d->precision != FWI_FP64) return bad("unknown precision");
   if (d->n_tx < 0 || (d->n_tx > 0 && !d->tx_angle))
     return bad("n_tx must be >= 0, with tx_angle when positive");
@@ -212,6 +214,9 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   Layout L;
   std::string why;
   if (!make_layout(d, L, &why)) return fail(nullptr, FWI_ERR_INVALID_ARG, why);
+  for (size_t i = 0; i < (size_t)d->n_elem * d->dim; ++i)
+    if (!std::isfinite(d->elem_pos[i]))
+      return fail(nullptr, FWI_ERR_INVALID_ARG, "elem_pos must be finite");
   fwi_ctx* c = new fwi_ctx();
   c->dim = L.dim; c->nx = L.nx; c->ny = L.ny; c->nz = L.nz;
   c->lx = L.lx; c->ly = L.ly; c->lz = L.lz; c->N = L.N; c->rows = L.rows;

@@ -174,3 +174,38 @@ def test_a_missing_library_fails_loudly(tmp_path):
     out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
                          check=True).stdout
     assert out.startswith("raised: libfwi.so not built"), out
+
+
+def test_degenerate_descriptors_are_rejected_on_the_host():
+    """Empty arrays (no element, no frequency), non-positive or non-finite
+    h, c0 and frequencies, and grids without an FFT plan (2 N outside
+    16 ... 1024) give 0 workspace bytes; a non-finite element position makes
+    fwi_create fail with FWI_ERR_INVALID_ARG before any device call."""
+    import numpy as np
+    from paper_2604_15796_gb300 import build, libfwi
+    build.build()
+    elem = np.stack([np.linspace(-1e-3, 1e-3, 8), np.full(8, -1e-4)], axis=1)
+
+    def nbytes(shape=(32, 32), e=elem, freqs=(1e6,), h=1e-4, c0=1540.0):
+        d, keep = libfwi.make_desc(shape, h, c0, e, list(freqs))
+        n = libfwi.fwi_workspace_bytes(ctypes.byref(d))
+        del keep
+        return n
+    assert nbytes() > 0 and nbytes((8, 8)) > 0 and nbytes((512, 512)) > 0
+    assert nbytes(e=np.zeros((0, 2))) == 0
+    assert nbytes(freqs=()) == 0
+    for bad in (0.0, -1e-4, float("nan"), float("inf")):
+        assert nbytes(h=bad) == 0
+        assert nbytes(c0=bad * 1e7) == 0
+        assert nbytes(freqs=(1e6, bad * 1e10)) == 0
+    for shape in ((1, 1), (4, 32), (1024, 1024), (32, 513)):
+        assert nbytes(shape) == 0, shape
+    bad_elem = elem.copy()
+    bad_elem[5, 0] = np.nan
+    d, keep = libfwi.make_desc((32, 32), 1e-4, 1540.0, bad_elem, [1e6])
+    assert libfwi.fwi_workspace_bytes(ctypes.byref(d)) > 0  # positions are read by fwi_create
+    h = ctypes.c_void_p()
+    st = libfwi.fwi_create(ctypes.byref(d), None, ctypes.byref(h))
+    assert st == libfwi.FWI_ERR_INVALID_ARG and not h.value
+    assert b"elem_pos must be finite" in libfwi.fwi_last_error(None)
+    del keep
