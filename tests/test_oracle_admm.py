@@ -217,3 +217,97 @@ def test_algorithm_1_reconstructs_an_inclusion():
     inside = sos_true > 1540.0
     assert sos[inside].mean() > 1545.0                 # the inclusion appears, faster than c0
     assert np.abs(sos[~inside] - 1540.0).mean() < 2.0  # the background stays near c0
+
+
+def _tv_prox_objective(m, d, lam, gamma, shape):
+    """1/2 ||m - d||^2 + lam sum_n ||(nabla m)_n||_2 + gamma/2 ||m||^2: the
+    objective of Eq. 7 when the data map is the identity and m_ref = 0."""
+    gm = admm.grad_op(m.reshape(shape), shape)
+    tv = np.sqrt((np.abs(gm) ** 2).sum(axis=0)).sum()
+    r = m.ravel() - d.ravel()
+    return 0.5 * np.vdot(r, r).real + lam * tv + 0.5 * gamma * np.vdot(m, m).real
+
+
+@pytest.mark.parametrize("dual_step", [None, 1.0])
+def test_admm_with_identity_jacobian_converges_to_the_tv_prox(dual_step):
+    """With J = I (point fields p_e = delta_e and one receiver field equal
+    to 1, so J a = a and grad = m - d), rho = 1 and the dual factor rho
+    (the paper's) or 1 (they coincide at rho = 1), Algorithm 1 is scaled
+    ADMM for the TV-denoising problem min 1/2||m - d||^2 + lam TV(m) +
+    gamma/2 ||m||^2, whose minimiser is unique (the objective is
+    1-strongly convex).  The iterates must reach the minimiser that a
+    generic optimiser finds on the smoothed objective: a wrong sign or
+    factor in the u-update, the shrink threshold or the m-step right-hand
+    side converges elsewhere or not at all.  Strong convexity bounds the
+    distance: F(m) - F* >= 1/2 ||m - m*||^2."""
+    shape = (4, 4)
+    n = 16
+    rng = np.random.default_rng(5)
+    d = 0.1 * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    d[:2, :] += 0.3  # a step edge for TV to keep
+    lam, gamma = 0.02, 1e-3
+    prob = oracle.Problem(shape, 1e-4, 1540.0, model.linear_array(n, 1e-4, 1e-4, 2),
+                          np.array([1.0e6]))
+    fields = np.eye(n, dtype=np.complex128).reshape((1, n) + shape)
+    rfields = np.ones((1, 1) + shape, dtype=np.complex128)
+    a = phantoms.complex_normal(shape, 9)
+    assert np.allclose(inverse.jac_forward(a, fields, rfields, prob).ravel(), a.ravel())
+    p = admm.AdmmParams(lam=lam, rho=1.0, gamma=gamma, n_cg=n, dual_step=dual_step)
+    m = np.zeros(shape, dtype=np.complex128)
+    g = admm.grad_op(m, shape)
+    u = np.zeros_like(g)
+    for _ in range(400):
+        grad = m - d  # J^H (J m - d)
+        m, g, u, _, _ = admm.admm_tv_step(m, g, u, grad, fields, rfields, prob, p)
+    # generic optimiser on the smoothed objective (real and imaginary parts)
+    eps = 1e-10
+
+    def f(x):
+        mm = (x[:n] + 1j * x[n:]).reshape(shape)
+        gm = admm.grad_op(mm, shape)
+        tv = np.sqrt((np.abs(gm) ** 2).sum(axis=0) + eps ** 2).sum()
+        r = (mm - d).ravel()
+        return 0.5 * np.vdot(r, r).real + lam * tv + 0.5 * gamma * np.vdot(mm, mm).real
+
+    best = None
+    for x0 in (np.concatenate([d.real.ravel(), d.imag.ravel()]), np.zeros(2 * n)):
+        res = optimize.minimize(f, x0, method="BFGS", options={"gtol": 1e-12, "maxiter": 20000})
+        if best is None or res.fun < best.fun:
+            best = res
+    m_opt = (best.x[:n] + 1j * best.x[n:]).reshape(shape)
+    F_admm = _tv_prox_objective(m, d, lam, gamma, shape)
+    F_opt = _tv_prox_objective(m_opt, d, lam, gamma, shape)
+    assert F_admm <= F_opt + 1e-9
+    assert np.linalg.norm(m - m_opt) <= 1e-3 * np.linalg.norm(d)
+    # the constraint g = nabla m holds at the fixed point
+    assert np.linalg.norm(g - admm.grad_op(m, shape)) <= 1e-6 * np.linalg.norm(g)
+    # TV keeps the edge: the solution is not the plain shrunk data
+    assert np.linalg.norm(m - d / (1 + gamma)) > 1e-2 * np.linalg.norm(d)
+
+
+def test_admm_identity_jacobian_detects_a_flipped_dual_update():
+    """The same iteration with the u-update's sign flipped (planted in a copy
+    of the step, on the CPU) does not reach the TV-prox minimiser."""
+    shape = (4, 4)
+    n = 16
+    rng = np.random.default_rng(5)
+    d = 0.1 * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+    d[:2, :] += 0.3
+    lam, gamma = 0.02, 1e-3
+    prob = oracle.Problem(shape, 1e-4, 1540.0, model.linear_array(n, 1e-4, 1e-4, 2),
+                          np.array([1.0e6]))
+    fields = np.eye(n, dtype=np.complex128).reshape((1, n) + shape)
+    rfields = np.ones((1, 1) + shape, dtype=np.complex128)
+    p = admm.AdmmParams(lam=lam, rho=1.0, gamma=gamma, n_cg=n)
+    res = {}
+    for flip in (False, True):
+        m = np.zeros(shape, dtype=np.complex128)
+        g = admm.grad_op(m, shape)
+        u = np.zeros_like(g)
+        for _ in range(400):
+            u_prev = u
+            m, g, u, _, _ = admm.admm_tv_step(m, g, u, m - d, fields, rfields, prob, p)
+            if flip:
+                u = u_prev - (u - u_prev)
+        res[flip] = _tv_prox_objective(m, d, lam, gamma, shape)
+    assert res[True] > res[False] + 1e-6
