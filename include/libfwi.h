@@ -333,9 +333,13 @@ FWI_API fwi_status fwi_server_destroy(fwi_server* s);
    (the split partial sums live in one 4 MiB file-scope device array, which
    every GPU that loads the library holds until exit); larger sizes return
    FWI_ERR_INVALID_ARG with a message (fwi_last_error(NULL)).
+   cuda_stream and X, a, Q, Y must belong to the current device (a stream
+   of another device is rejected with FWI_ERR_INVALID_ARG).
    The first call on a device looks up the array's device address
-   (cudaGetSymbolAddress) and caches it; make that first call outside any
-   stream capture.  Every call shares the array, which keeps the last
+   (cudaGetSymbolAddress) and caches it for the current CUDA context; a
+   later context on that device (after cudaDeviceReset, say) looks it up
+   again on its first call.  Make each such first call outside any stream
+   capture.  Every call shares the array, which keeps the last
    call's contents (no part of it needs to start at zero: each call writes
    every partial it reads).  Calls whose work overlaps on the GPU (other
    streams, other host threads) race on the array; serialise them.

@@ -707,7 +707,14 @@ __device__ __align__(256) float2 g_noalloc_scratch[kNoallocScratchElems];
 
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-float2* g_noalloc_ptr[kNoallocMaxDevices] = {};
+// Per device: the array's device address and the id of the CUDA context it
+// was looked up in.  A __device__ symbol's address belongs to the context
+// that loaded the module: after cudaDeviceReset (or any teardown of the
+// primary context) the next context loads the module again, possibly at
+// another address, so the cached address is only reused while the current
+// context is the one it was looked up in.
+struct NoallocSlot { unsigned long long ctx_id; float2* ptr; };
+NoallocSlot g_noalloc_slot[kNoallocMaxDevices] = {};
 
 struct FreqScales { double s[FWI_NOALLOC_MAX_FREQ]; };
 
@@ -727,21 +734,52 @@ __global__ void contract_reduce_static_kernel(double2* Y, const float2* part, in
   }
 }
 
-// Device address of the scratch array for the current device, looked up
-// once per device (cudaGetSymbolAddress; no allocation).
-cudaError_t noalloc_scratch(float2** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
+// Driver entry points for the current context and its process-unique id
+// (cuCtxGetId ids are never reused, unlike context handles), taken through
+// the runtime so that the library does not link libcuda.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+
+// Unique id of the current CUDA context, or 0 if the driver cannot tell.
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)f;
+  });
+  if (!get_current || !get_id) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on device `dev` (the current
+// device), looked up with cudaGetSymbolAddress (no allocation) once per
+// device and context.  If the driver cannot name the context, the address
+// is looked up on every call instead of being cached.
+cudaError_t noalloc_scratch(int dev, float2** out) {
   if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long id = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ptr[dev]) {
+  NoallocSlot& slot = g_noalloc_slot[dev];
+  if (id == 0 || slot.ctx_id != id || !slot.ptr) {
     void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_noalloc_ptr[dev] = (float2*)p;
+    slot.ptr = (float2*)p;
+    slot.ctx_id = id;
   }
-  *out = g_noalloc_ptr[dev];
+  *out = slot.ptr;
   return cudaSuccess;
 }
 
@@ -763,11 +801,21 @@ extern "C" fwi_status fwi_contract_pixels_noalloc(const void* X, const void* a, 
     return fail(nullptr, FWI_ERR_INVALID_ARG,
                 "fwi_contract_pixels_noalloc: n_freq * n_elem^2 exceeds the 4 MiB static "
                 "scratch (at most 524288 complex partial sums)");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int dev = 0, sdev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc device");
+  // the array (and the SM count) are the current device's: a stream of
+  // another device would run the kernels against the wrong copy
+  e = cudaStreamGetDevice(s, &sdev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc stream");
+  if (sdev != dev)
+    return fail(nullptr, FWI_ERR_INVALID_ARG,
+                "fwi_contract_pixels_noalloc: cuda_stream belongs to another device than "
+                "the current one");
   float2* part = nullptr;
-  cudaError_t e = noalloc_scratch(&part);
+  e = noalloc_scratch(dev, &part);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc scratch");
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fwi_contract_pixels_noalloc");
   const int nbe = (n_elem + TB - 1) / TB;
@@ -782,7 +830,6 @@ extern "C" fwi_status fwi_contract_pixels_noalloc(const void* X, const void* a, 
   chunk = ((chunk + KC - 1) / KC) * KC;
   FreqScales sc{};
   for (int l = 0; l < n_freq; ++l) sc.s[l] = scale[l];
-  cudaStream_t s = (cudaStream_t)cuda_stream;
   dim3 grid((unsigned)split, nbe * nbe, n_freq);
   contract_kernel<float><<<grid, 256, 0, s>>>((const float2*)X, (const float2*)a,
                                               (const float2*)Q, part, n_elem, N, n_freq, chunk,
