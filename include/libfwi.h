@@ -403,6 +403,11 @@ typedef struct fwi_tuning {
                            after about 1 s and the call returns FWI_ERR_CUDA
                            ("pipeline wait timed out"); the context stays
                            usable.  Applies once; reads back as 0. */
+  int col_tma;          /* 1 (default): the FP32 column passes stage their
+                           input tiles in shared memory with TMA tensor
+                           copies, the next tile's copy overlapping the
+                           current tile's transforms; 0: plain loads.
+                           Results are bitwise the same. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

@@ -568,6 +568,7 @@ fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
   out->tuned = ctx->tuned;
   out->jac_tensor_cores = ctx->use_tc ? 1 : 0;
   out->overlap_halves = ctx->overlap ? 1 : 0;
+  out->col_tma = ctx->col_tma;
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
   return FWI_OK;
@@ -589,6 +590,9 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
     return fail(ctx, FWI_ERR_INVALID_ARG, "overlap_halves must be 0 or 1");
   if (in->debug_stall_once != 0 && in->debug_stall_once != 1)
     return fail(ctx, FWI_ERR_INVALID_ARG, "debug_stall_once must be 0 or 1");
+  if (in->col_tma != 0 && in->col_tma != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "col_tma must be 0 or 1");
+  ctx->col_tma = in->col_tma;
   ctx->tc_stall = in->debug_stall_once;
   ctx->use_tc = in->jac_tensor_cores == 1;
   ctx->overlap = in->overlap_halves == 1;

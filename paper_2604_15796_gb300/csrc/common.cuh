@@ -85,6 +85,8 @@ template <typename T> struct ColArgs {
   const int* active; const int* n_active; int nb;
   int rhs0, n_elem;         // global RHS index = rhs0 + slot; freq = idx / n_elem
   int freq_fixed;           // >= 0: every RHS uses this frequency
+  int tma;                  // FP32, zero-padded input: stage tiles with TMA
+  int* err;                 // error word of bounded waits (or NULL)
 };
 
 // Host-side launch interface, specialised per precision in the

@@ -82,6 +82,7 @@ struct fwi_ctx {
   int* tc_err = nullptr;            // error word of the tensor-core kernels
   int* h_tc_err = nullptr;          // pinned host mirror
   bool use_tc = true;               // tensor-core pixel contractions (FP32 fields)
+  int col_tma = 1;                  // column passes stage tiles with TMA (FP32)
   int tc_stall = 0;                 // next contraction withholds its first stage (test)
   double* red = nullptr;            // reduction scratch (doubles)
   double* h_red = nullptr;          // pinned host mirror

@@ -320,15 +320,17 @@ template <int L_, int R1_, int R2_, int TL_> struct Plan {
 // samples x[R2 n1 + n2] at v[i*R1 + n1] (loaded by the caller; entries with
 // n1 >= NIN1 must be zero).  Computes the R1-point DFTs, applies the
 // four-step twiddle w_L^{n2 k1} (table tw of L entries, forward sign), and
-// stores y[n2][k1] into shared memory.
-template <class P, typename T>
+// stores y[n2][k1] into shared memory.  HALF_IN: the samples n1 >= R1/2 are
+// zero (a zero-padded line) and the DFTs skip them.
+template <class P, typename T, bool HALF_IN = false>
 FWI_HD void phaseA_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                          const cplx<T>* tw) {
 #pragma unroll
   for (int i = 0; i < P::C1; ++i) {
     const int n2 = t + i * P::TL;
     if (P::C1 * P::TL == P::R2 || n2 < P::R2) {
-      Dft<P::R1, false, T>::run(v + i * P::R1);
+      if constexpr (HALF_IN) DftHalfIn<P::R1, false, T>::run(v + i * P::R1);
+      else Dft<P::R1, false, T>::run(v + i * P::R1);
 #pragma unroll
       for (int k1 = 0; k1 < P::R1; ++k1) {
         cplx<T> z = v[i * P::R1 + k1];
@@ -377,7 +379,9 @@ FWI_HD void phaseC_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
 }
 
 // Phase D (inverse): reads y[n2][k1] for each owned n2 and all k1, inverse
-// R1-point DFTs.  On return v[i*R1 + n1] = x[R2 n1 + n2] (unnormalised).
+// R1-point DFTs of which only the cropped half is formed.  On return
+// v[i*R1 + n1] = x[R2 n1 + n2] (unnormalised) for n1 < R1/2; the entries
+// n1 >= R1/2 are undefined (every caller keeps the cropped half only).
 template <class P, typename T>
 FWI_HD void phaseD_load(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
 #pragma unroll
@@ -387,7 +391,7 @@ FWI_HD void phaseD_load(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
 #pragma unroll
       for (int k1 = 0; k1 < P::R1; ++k1)
         v[i * P::R1 + k1] = sm[(n2 * (P::R1 + pad) + k1) * sj];
-      Dft<P::R1, true, T>::run(v + i * P::R1);
+      DftHalfOut<P::R1, true, T>::run(v + i * P::R1);
     }
   }
 }

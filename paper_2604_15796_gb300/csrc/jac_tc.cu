@@ -769,9 +769,10 @@ fwi_status tc_err_check(fwi_ctx* c) {
   const int code = *c->h_tc_err;
   *c->h_tc_err = 0;
   cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
+  // codes 1-4: tensor-core contractions; 5-6: TMA staging of the column passes
   return fail(c, FWI_ERR_CUDA,
-              std::string("tensor-core contraction: pipeline wait timed out (code ") +
-                  std::to_string(code) + ")");
+              std::string(code <= 4 ? "tensor-core contraction" : "column pass TMA staging") +
+                  ": pipeline wait timed out (code " + std::to_string(code) + ")");
 }
 
 }  // namespace fwi

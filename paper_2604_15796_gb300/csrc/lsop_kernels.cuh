@@ -15,10 +15,13 @@
 // (grid-stride loop over (active RHS, tile) work items).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is taken from the driver at run time)
+
 #include <atomic>
 #include <mutex>
 
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace fwi {
 
@@ -222,7 +225,7 @@ __device__ __forceinline__ void ph_A(int t, cplx<T>* v, cplx<T>* sm, int sj, int
       sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
     }
   } else {
-    phaseA_store<P, T>(t, v, sm, sj, pad, tw);
+    phaseA_store<P, T, HALF_IN>(t, v, sm, sj, pad, tw);
   }
 }
 
@@ -643,6 +646,89 @@ row_inv_kernel(const RowInvArgs<T> a) {
 }
 
 // --------------------------------------------------------------------------
+// Work item of a column pass -> (RHS slot, plane, column tile).  The
+// convolution orders the items slot-fastest: the CTAs then sweep all
+// right-hand sides of a column tile together, so each tile of the kernel
+// spectrum is read from HBM once per frequency and served from L2 for the
+// other right-hand sides (in 3-D one frequency's spectrum, lz*ly*lx*8 bytes,
+// exceeds L2).  The other passes go right-hand side by right-hand side.
+struct ColItem { int slot, plane, tile; };
+__device__ __forceinline__ ColItem col_item(unsigned item, unsigned nact, unsigned per_rhs,
+                                            unsigned ntile, int nplanes, bool slot_fast) {
+  ColItem it;
+  unsigned rem;
+  if (slot_fast) {
+    rem = item / nact;
+    it.slot = (int)(item - rem * nact);
+  } else {
+    it.slot = (int)(item / per_rhs);
+    rem = item - (unsigned)it.slot * per_rhs;
+  }
+  it.plane = (nplanes == 1) ? 0 : (int)(rem / ntile);
+  it.tile = (int)(rem - (unsigned)it.plane * ntile);
+  return it;
+}
+
+// The transforms of one column item after its samples are in registers
+// (phase-A slots for the forward and convolution modes, phase-B slots for
+// the inverse) and the exchange buffer is free: forward FFT along the
+// column, product with the kernel spectrum, inverse FFT, cropped store
+// (C_CONV); forward FFT and store of every frequency sample (C_FWD);
+// inverse FFT and cropped store (C_INV).  `out` points at the item's first
+// output sample of column j.
+template <class P, typename T, int TC>
+__device__ __forceinline__ void col_transform_store(const ColArgs<T>& a, int t, cplx<T>* smc,
+                                                    cplx<T>* v, int rhs, int j,
+                                                    cplx<T>* __restrict__ out) {
+  using V = cplx<T>;
+  constexpr int GP = 32 / TC;
+  const long long ls = a.line_stride;
+  if (a.mode != C_INV) {
+    if (a.full) ph_A<P, GP, T, false>(t, v, smc, TC, 0, a.tw);
+    else ph_A<P, GP, T, true>(t, v, smc, TC, 0, a.tw);
+    __syncthreads();
+    ph_B<P, GP, T>(t, v, smc, TC, 0);
+    if (a.mode == C_FWD) {
+#pragma unroll
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
+#pragma unroll
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2))
+            out[(long long)(k1 + P::R1 * k2) * ls] = v[i * PlanTraits<P>::MB + kp];
+        }
+      }
+      return;
+    }
+    const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs) / a.n_elem;
+    const V* __restrict__ g = a.ghat + (long long)l * a.ghat_freq_stride + j;
+#pragma unroll
+    for (int i = 0; i < PlanTraits<P>::CB; ++i) {
+#pragma unroll
+      for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+        int k1, k2;
+        if (slotB<P, GP>(t, i, kp, k1, k2)) {
+          const int r = i * PlanTraits<P>::MB + kp;
+          v[r] = cmul(v[r], FWI_LDG(g + (long long)(k1 + P::R1 * k2) * a.ncols));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  ph_C<P, GP, T>(t, v, smc, TC, 0, a.tw);
+  __syncthreads();
+  ph_D<P, GP, T>(t, v, smc, TC, 0);
+#pragma unroll
+  for (int i = 0; i < PlanTraits<P>::CA; ++i) {
+#pragma unroll
+    for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+      int n2, n1;
+      if (slotA<P, GP>(t, i, m, n2, n1) && n1 < P::H1)
+        out[(long long)(P::R2 * n1 + n2) * ls] = v[i * PlanTraits<P>::MA + m];
+    }
+  }
+}
+
 // Column pass over tiles of TC adjacent columns; thread (c, g) handles
 // column c of the tile as thread g of its line.  Shared-memory positions
 // are interleaved across the tile's columns (stride TC), which keeps the
@@ -662,12 +748,11 @@ col_kernel(const ColArgs<T> a) {
   const int nact = a.active ? *a.n_active : a.nb;
   const unsigned items = (unsigned)nact * per_rhs;  // < 2^31 (fwi_create caps the batch)
   const long long ls = a.line_stride;
+  const bool slot_fast = a.mode == C_CONV;
   for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
-    const int slot = (int)(item / per_rhs);
-    const unsigned rem = item - (unsigned)slot * per_rhs;
-    const int plane = (a.nplanes == 1) ? 0 : (int)(rem / ntile);
-    const int tile = (int)(rem - (unsigned)plane * ntile);
-    const int rhs = a.active ? a.active[slot] : slot;
+    const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
+    const int plane = it.plane, tile = it.tile;
+    const int rhs = a.active ? a.active[it.slot] : it.slot;
     const int j = tile * TC + c;
     const V* __restrict__ in = a.in + rhs * a.in_rhs_stride + plane * a.in_plane_stride + j;
     V* __restrict__ out = a.out + rhs * a.out_rhs_stride + plane * a.out_plane_stride + j;
@@ -697,51 +782,125 @@ col_kernel(const ColArgs<T> a) {
       }
     }
     __syncthreads();
-    if (a.mode != C_INV) {
-      if (a.full) ph_A<P, GP, T, false>(t, v, smc, TC, 0, a.tw);
-      else ph_A<P, GP, T, true>(t, v, smc, TC, 0, a.tw);
-      __syncthreads();
-      ph_B<P, GP, T>(t, v, smc, TC, 0);
-      if (a.mode == C_FWD) {
-#pragma unroll
-        for (int i = 0; i < PlanTraits<P>::CB; ++i) {
-#pragma unroll
-          for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
-            int k1, k2;
-            if (slotB<P, GP>(t, i, kp, k1, k2))
-              out[(long long)(k1 + P::R1 * k2) * ls] = v[i * PlanTraits<P>::MB + kp];
-          }
-        }
-        continue;
-      }
-      const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs) / a.n_elem;
-      const V* __restrict__ g = a.ghat + (long long)l * a.ghat_freq_stride + j;
+    col_transform_store<P, T, TC>(a, t, smc, v, rhs, j, out);
+  }
+}
+
+// --------------------------------------------------------------------------
+// Column pass with the input tiles staged by the tensor memory accelerator
+// (FP32, zero-padded or inverse input).  One thread of the CTA issues the
+// TMA copy of the NEXT work item's input tile (TC columns x the line's
+// nonzero rows, one 3-D box per <= 256 rows) into a staging buffer as soon
+// as every thread has moved the current tile into registers, so the HBM
+// read of item i+1 overlaps the transforms of item i.  The staging buffer
+// is a separate region of shared memory from the transform exchange.  The
+// wait on the copy's mbarrier is bounded (1 s): on a timeout the CTA
+// records the code in a.err, waits (bounded) for its copy in flight and
+// stops; the entry points report the code.
+//
+// Tensor map: 3-D, innermost the columns (as 2 floats each), then the
+// line's rows (stride line_stride), then (RHS, plane) pairs (stride
+// in_rhs_stride / nplanes); box {2 TC, rows_in / nbox, 1}.
+constexpr int kColErrWait = 5;
+constexpr int kColErrDrain = 6;
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+template <class P, int TC>
+__global__ void __launch_bounds__(TC * P::TL, (TC * P::TL >= 256) ? 2 : 4)
+col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map, int rows_in,
+               int nbox) {
+  using V = float2;
+  constexpr int GP = 32 / TC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // TMA destinations 128-byte aligned (the launch adds 128 bytes of slack)
+  const uint32_t base_pad = (128u - (tc::smem_addr(smraw) & 127u)) & 127u;
+  V* sm = reinterpret_cast<V*>(smraw + base_pad);            // exchange, L x TC
+  V* stg = sm + P::L * TC;                                   // staging, rows_in x TC
+  uint64_t* bar = reinterpret_cast<uint64_t*>(stg + rows_in * TC);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 1);
+  const uint32_t bar_a = tc::smem_addr(bar);
+  const uint32_t stg_a = tc::smem_addr(stg);
+  const int c = threadIdx.x % TC;
+  const int t = threadIdx.x / TC;
+  V* smc = sm + c;
+  const unsigned ntile = (unsigned)(a.ncols / TC);
+  const unsigned per_rhs = (unsigned)a.nplanes * ntile;
+  const int nact = a.active ? *a.n_active : a.nb;
+  const unsigned items = (unsigned)nact * per_rhs;  // < 2^31 (fwi_create caps the batch)
+  const bool slot_fast = a.mode == C_CONV;
+  const int box_rows = rows_in / nbox;
+  const uint32_t tile_bytes = (uint32_t)(rows_in * TC * sizeof(V));
+  int dummy_err = 0;
+  int* err = a.err ? a.err : &dummy_err;
+
+  auto issue = [&](unsigned item) {
+    const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
+    const int rhs = a.active ? a.active[it.slot] : it.slot;
+    tc::mbar_arrive_expect_tx(bar_a, tile_bytes);
+    for (int b = 0; b < nbox; ++b)
+      tma_load_3d(stg_a + (uint32_t)(b * box_rows * TC * sizeof(V)), &map, 2 * it.tile * TC,
+                  b * box_rows, rhs * a.nplanes + it.plane, bar_a);
+  };
+
+  if (threadIdx.x == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
+    tc::mbar_init(bar_a, 1);
+    *abort_flag = 0;
+    tc::mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && blockIdx.x < items) issue(blockIdx.x);
+  uint32_t parity = 0;
+  bool failed = false;
+  for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
+    const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
+    const int rhs = a.active ? a.active[it.slot] : it.slot;
+    const int j = it.tile * TC + c;
+    const bool ok = tc::mbar_wait(bar_a, parity, abort_flag, err, kColErrWait);
+    V v[P::E];
+    if (a.mode == C_INV) {
 #pragma unroll
       for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
         for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
           int k1, k2;
-          if (slotB<P, GP>(t, i, kp, k1, k2)) {
-            const int r = i * PlanTraits<P>::MB + kp;
-            v[r] = cmul(v[r], FWI_LDG(g + (long long)(k1 + P::R1 * k2) * a.ncols));
-          }
+          if (slotB<P, GP>(t, i, kp, k1, k2))
+            v[i * PlanTraits<P>::MB + kp] = stg[(k1 + P::R1 * k2) * TC + c];
         }
       }
-      __syncthreads();
-    }
-    ph_C<P, GP, T>(t, v, smc, TC, 0, a.tw);
-    __syncthreads();
-    ph_D<P, GP, T>(t, v, smc, TC, 0);
+    } else {
 #pragma unroll
-    for (int i = 0; i < PlanTraits<P>::CA; ++i) {
+      for (int i = 0; i < PlanTraits<P>::CA; ++i) {
 #pragma unroll
-      for (int m = 0; m < PlanTraits<P>::MA; ++m) {
-        int n2, n1;
-        if (slotA<P, GP>(t, i, m, n2, n1) && n1 < P::H1)
-          out[(long long)(P::R2 * n1 + n2) * ls] = v[i * PlanTraits<P>::MA + m];
+        for (int m = 0; m < PlanTraits<P>::MA; ++m) {
+          int n2, n1;
+          const bool in = slotA<P, GP>(t, i, m, n2, n1);
+          v[i * PlanTraits<P>::MA + m] =
+              (in && n1 < P::H1) ? stg[(P::R2 * n1 + n2) * TC + c] : mk<float>(0.f, 0.f);
+        }
       }
     }
+    // every thread holds its samples (the staging buffer is free) and is
+    // done with the previous item's exchange
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    parity ^= 1u;
+    if (threadIdx.x == 0 && item + gridDim.x < items) issue(item + gridDim.x);
+    V* __restrict__ out = a.out + rhs * a.out_rhs_stride + it.plane * a.out_plane_stride + j;
+    col_transform_store<P, float, TC>(a, t, smc, v, rhs, j, out);
   }
+  // a timed-out copy may still land in this CTA's shared memory
+  if (failed && threadIdx.x == 0) tc::mbar_wait_drain(bar_a, parity, err, kColErrDrain);
 }
 
 // --------------------------------------------------------------------------
@@ -807,13 +966,16 @@ template <int L, typename T, int KIND, int VAR> GridCache& gcache() {
   return g;
 }
 
+// attr_smem: the kernel's dynamic shared-memory limit to set (at least
+// smem; a kernel launched with several sizes gets the largest).
 template <typename K>
-inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc) {
+inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc,
+                            size_t attr_smem = 0) {
   if (gc.blocks.load(std::memory_order_acquire) > 0) return cudaSuccess;
   std::lock_guard<std::mutex> lock(grid_mutex());
   if (gc.blocks.load(std::memory_order_relaxed) > 0) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)(attr_smem > smem ? attr_smem : smem));
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
   e = cudaGetDevice(&dev);
@@ -850,10 +1012,74 @@ cudaError_t launch_row_inv(const RowInvArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (the
+// library does not link libcuda); NULL if the driver does not offer it.
+typedef CUresult (*TensorMapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                      const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                      const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+inline TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (TensorMapEncodeFn)f;
+  });
+  return fn;
+}
+
+// Tensor map of a column pass's input (see col_tma_kernel).  False when the
+// pass does not fit the TMA path (then the plain kernel runs).
+template <int L, int TC>
+bool col_tensor_map(const ColArgs<float>& a, CUtensorMap* map, int* rows_in, int* nbox) {
+  if (!a.tma || a.full) return false;
+  TensorMapEncodeFn enc = tensor_map_encoder();
+  if (!enc || a.nplanes < 1 || a.nb < 1 || a.ncols % TC) return false;
+  const int rin = (a.mode == C_INV) ? L : L / 2;
+  const int nb = (rin + 255) / 256;
+  if (rin % nb) return false;
+  if (a.in_rhs_stride % a.nplanes) return false;
+  const long long pstride = a.in_rhs_stride / a.nplanes;
+  if (a.nplanes > 1 && pstride != a.in_plane_stride) return false;
+  if (((uintptr_t)a.in & 15) || (a.line_stride * 8) % 16 || (pstride * 8) % 16) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * a.ncols, (cuuint64_t)rin,
+                              (cuuint64_t)a.nb * a.nplanes};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.line_stride * 8, (cuuint64_t)pstride * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * TC), (cuuint32_t)(rin / nb), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(a.in), dims, strides, box,
+          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return false;
+  *rows_in = rin;
+  *nbox = nb;
+  return true;
+}
+
 template <int L, typename T, int VAR>
 cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
   using P = typename PlanFor<L>::type;
   constexpr int tc = col_tc_v<L, T, VAR>();
+  if constexpr (sizeof(T) == 4) {
+    CUtensorMap map;
+    int rows_in = 0, nbox = 0;
+    if (col_tensor_map<L, tc>(a, &map, &rows_in, &nbox)) {
+      auto k = col_tma_kernel<P, tc>;
+      // exchange + staging + mbarrier and abort flag + alignment slack
+      const size_t smem = (size_t)(L + rows_in) * tc * sizeof(float2) + 16 + 128;
+      const size_t smem_max = (size_t)(2 * L) * tc * sizeof(float2) + 16 + 128;  // inverse
+      GridCache& gc = (a.mode == C_INV) ? gcache<L, T, 4, VAR>() : gcache<L, T, 3, VAR>();
+      cudaError_t e = grid_for(k, tc * P::TL, smem, gc, smem_max);
+      if (e != cudaSuccess) return e;
+      k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, rows_in, nbox);
+      return cudaGetLastError();
+    }
+  }
   auto k = col_kernel<P, T, tc>;
   GridCache& gc = gcache<L, T, 2, VAR>();
   cudaError_t e = grid_for(k, tc * P::TL, col_smem_v<L, T, VAR>(), gc);

@@ -67,7 +67,7 @@ class fwi_tuning(Structure):
     _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
                 ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
                 ("jac_tensor_cores", c_int), ("overlap_halves", c_int),
-                ("debug_stall_once", c_int)]
+                ("debug_stall_once", c_int), ("col_tma", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -513,6 +513,15 @@ class Context:
         t = fwi_tuning()
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.jac_tensor_cores = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_col_tma(self, on):
+        """Stage the FP32 column passes' input tiles with TMA copies (True)
+        or read them with plain loads (False); results are bitwise the
+        same."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.col_tma = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def debug_stall_once(self):

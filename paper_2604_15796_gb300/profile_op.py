@@ -4,6 +4,7 @@ kernel tuning and ncu captures.
 
     python -m paper_2604_15796_gb300.profile_op --grid 256 --rhs 256 --reps 3
     python -m paper_2604_15796_gb300.profile_op --jac --grid 256 --rhs 128 --nfreq 2
+    python -m paper_2604_15796_gb300.profile_op --dim3 --grid 160 --depth 128 --rhs 32
 
 Operator mode: a context with ``rhs`` array elements at one frequency (one
 operator application processes ``rhs`` right-hand sides) applies
@@ -32,10 +33,14 @@ def main():
     ap.add_argument("--jac", action="store_true")
     ap.add_argument("--nfreq", type=int, default=2)
     ap.add_argument("--cuda-core-jacobian", action="store_true")
+    ap.add_argument("--dim3", action="store_true",
+                    help="3-D grid of depth x grid x grid voxels (0.2 mm)")
+    ap.add_argument("--no-col-tma", action="store_true",
+                    help="column passes with plain loads instead of TMA staging")
     args = ap.parse_args()
     nz = args.depth or args.grid
-    shape = (nz, args.grid)
-    h = 0.1e-3
+    shape = (nz, args.grid, args.grid) if args.dim3 else (nz, args.grid)
+    h = 0.2e-3 if args.dim3 else 0.1e-3
     freqs = np.linspace(0.5e6, args.freq, args.nfreq) if args.jac else np.array([args.freq])
     w = phantoms.tissue_phantom(shape, h, args.rhs, min(0.2e-3, args.grid * h / args.rhs),
                                 freqs, 5, inclusions=[1520.0, 1580.0])
@@ -44,6 +49,8 @@ def main():
     with torch.cuda.stream(stream):
         ctx = libfwi.Context(w.shape, w.h, w.c0, w.elem, w.freqs, precision=prec,
                              stream=stream)
+        if args.no_col_tma:
+            ctx.set_col_tma(False)
         m = ctx.contrast_from_sos(torch.from_numpy(np.ascontiguousarray(w.sos)).cuda())
         if args.jac:
             if args.cuda_core_jacobian:

@@ -87,3 +87,27 @@ def test_invalid_arguments_are_rejected(lib):
     with pytest.raises(lib.FwiError) as e:
         lib.Context((16, 24), w.h, w.c0, w.elem, w.freqs)  # 2*24 has no FFT plan
     assert e.value.status == lib.FWI_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", [(32, 96), (256, 16), (8, 512), (8, 16, 256), (16, 8, 8),
+                                   (16, 96, 32), (8, 160, 16)])
+def test_tma_staged_column_passes_match_plain_loads(lib, shape):
+    """The FP32 column passes give the same bits whether their input tiles
+    are staged by TMA tensor copies or read with plain loads (the copy only
+    moves the samples; every arithmetic step is the same), and both match
+    the oracle."""
+    import torch
+    w = small_workload(shape, n_elem=3, freqs=(2.0e6,))
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs)
+    m_gpu = to_gpu(contrast(w), torch.complex128)
+    v_gpu = to_gpu(phantoms.complex_normal((3,) + tuple(shape), 21), torch.complex64)
+    out = {}
+    for tma in (True, False):
+        ctx.set_col_tma(tma)
+        out[tma] = to_np(ctx.apply("A", v_gpu, 0, m_gpu))
+    ctx.close()
+    assert np.array_equal(out[True], out[False])
+    prob = oracle_problem(w)
+    vin = to_np(v_gpu).astype(np.complex128)
+    ref = operator.apply_A(vin, contrast(w), prob, 0)
+    assert rel_l2(out[True], ref) < 1e-5
