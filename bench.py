@@ -8,7 +8,12 @@ shrink, dual update, SoS map).  Every step starts from the same iterate
 (m_k, g_k, u_k) so that all steps do the same work.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload thyroid256|large512|volume3d|disc64]
+                    [--workload volume3d|thyroid256|large512|disc64|planewave2d|elev3d|serving]
+
+The default workload is the largest single-GPU configuration, the 3-D
+single-sided volume (160 x 160 x 128 voxels, 128 elements x 4 frequencies);
+after its timed region the line also carries a short serving stream's
+p50/p99 reconstruction latency (--serving-requests, 0 for none).
 
 Prints one JSON line (rank 0).  Multi-GPU: independent replicas, one per
 rank (the solves shard by right-hand side with no exchange step).
@@ -17,7 +22,6 @@ import argparse
 import hashlib
 import json
 import os
-import re
 import statistics
 import subprocess
 import sys
@@ -62,7 +66,8 @@ def describe(w):
 
 # the sources each kernel class is compiled from: the FFT operator passes
 # (row_*, col_*) and the pixel contractions (everything else)
-KERNEL_SOURCES = {"operator": ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "lsop_f32.cu"),
+KERNEL_SOURCES = {"operator": ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "lsop_f32.cu",
+                               "tc.cuh"),
                   "contraction": ("common.cuh", "jac.cu", "jac_tc.cu", "tc.cuh")}
 
 
@@ -77,20 +82,22 @@ def kernel_source_hash(kernel="col_conv"):
     return h.hexdigest()[:12]
 
 
-def recorded_traffic(kernel, wname):
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def recorded_traffic(kernel, wname, path=None):
     """(DRAM bytes, algorithmic bytes) of one ncu-captured launch of a kernel
-    class, recorded in profiles/traffic.md, if the kernel sources have not
-    changed since (hash match); else None."""
-    path = os.path.join(ROOT, "profiles", "traffic.md")
+    class on a workload, recorded in profiles/traffic.json, if the kernel's
+    sources have not changed since the capture (hash match); else None."""
+    path = path or TRAFFIC_PATH
     if not os.path.exists(path):
         return None
-    pat = re.compile(r"^traffic\s+(\S+)\s+(\S+)\s+dram_bytes=([0-9.eE+]+)\s+"
-                     r"algorithmic_bytes=([0-9.eE+]+)\s+src=(\w+)")
-    for line in open(path):
-        m = pat.match(line.strip())
-        if m and m.group(1) == kernel and m.group(2) == wname and \
-                m.group(5) == kernel_source_hash(kernel):
-            return float(m.group(3)), float(m.group(4))
+    with open(path) as f:
+        recs = json.load(f).get("records", [])
+    for r in recs:
+        if r.get("kernel") == kernel and r.get("workload") == wname and \
+                r.get("src") == kernel_source_hash(kernel):
+            return float(r["dram_bytes"]), float(r["algorithmic_bytes"])
     return None
 
 
@@ -506,16 +513,29 @@ def cufft_matvec_comparator(ctx, w, m, stream, reps=5):
             "speedup": t_lib / t_ours}
 
 
-def peak_table(peaks, peak_kind):
-    """Denominators: measured HBM copy bandwidth; FP32 FMA peak from the SM
-    count and clock; the TF32 tensor peak from the measured bf16 GEMM peak
-    and the nominal tf32/bf16 ratio (1/2), divided by the three TF32
-    products of one FP32 product (3xTF32)."""
+def sm_count(default=152):
+    """SMs of the current CUDA device (the nominal GB300 count without one)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                       .multi_processor_count)
+    except Exception:
+        pass
+    return default
+
+
+def peak_table(peaks, peak_kind, sms=None):
+    """Denominators: measured HBM copy bandwidth; FP32 FMA peak from the
+    device's SM count and the clock; the TF32 tensor peak from the measured
+    bf16 GEMM peak and the nominal tf32/bf16 ratio (1/2), divided by the
+    three TF32 products of one FP32 product (3xTF32)."""
     mhz = peaks.get("sm_max_mhz", 2070.0)
+    sms = sm_count() if sms is None else sms
     return {
         "hbm": (peaks["hbm_gbs"], "GB/s", f"{peak_kind} hbm_gbs"),
-        "alu": (152 * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
-                f"152 SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"),
+        "alu": (sms * 128 * 2 * mhz * 1e6 / 1e12, "TFLOP/s",
+                f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"),
         "tensor": (peaks["bf16_tflops"] * 0.5 / 3.0, "TFLOP/s",
                    f"{peak_kind} bf16_tflops {peaks['bf16_tflops']:.0f} x 1/2 (tf32/bf16 nominal)"
                    " / 3 (3xTF32 products per FP32 product)"),
@@ -523,14 +543,13 @@ def peak_table(peaks, peak_kind):
 
 
 def bound_of(name, k, tensor):
-    """The resource that limits a kernel class (from its ncu counters): the
-    pixel contractions run on the tensor cores (or FP32 FMA without them),
-    the column FFT passes are instruction-issue bound, the row passes and
-    vector kernels stream HBM."""
+    """The roofline a kernel class is measured against: the pixel
+    contractions run on the tensor cores (or FP32 FMA without them); the
+    FFT operator passes (row and column) and the vector kernels stream
+    their algorithmic bytes through HBM (the column passes also report
+    their nominal FFT flop rate)."""
     if name in TENSOR_CLASSES:
         return "tensor" if tensor else "alu"
-    if name.startswith("col_") and k["flops"] > 0:
-        return "alu"
     if k["bytes"] > 0:
         return "hbm"
     return "alu" if k["flops"] > 0 else None
@@ -568,6 +587,10 @@ def roofline(name, k, peaks, peak_kind, wname, tensor):
         gbs = k["bytes"] / k["launches"] / (avg_ms * 1e6)
         out["hbm_gbs_at_algorithmic_bytes"] = gbs
         out["hbm_frac"] = gbs / peaks["hbm_gbs"]
+    if bound == "hbm" and k["flops"] > 0:
+        alu = peak_table(peaks, peak_kind)["alu"][0]
+        out["fft_tflops_nominal"] = k["flops"] / k["launches"] / (avg_ms * 1e9)
+        out["alu_frac_nominal"] = out["fft_tflops_nominal"] / alu
     out.update({"kernel": name, "launches": k["launches"], "avg_launch_ms": avg_ms,
                 "algorithmic_bytes_per_launch": k["bytes"] / k["launches"],
                 "algorithmic_flops_per_launch": k["flops"] / k["launches"],
@@ -641,16 +664,18 @@ def serving_fp64_comparator(work, results, rate, n_sample=2):
             "mean_interarrival_ms": 1e3 / rate}
 
 
-def run_serving(args):
+def run_serving(args, n_requests=None, n_burst=4, n_comparator=2):
     """Serving stream: Poisson arrivals of whole reconstructions (5 ADMM-TV
     iterations each) over grids {128^2, 256^2, 384^2, 512^2, 96^3}, 64-192
     elements, 2-12 frequencies; continuous batching with admission by HBM
-    footprint.  Arrival rate: 80 % of the capacity measured on a burst."""
+    footprint.  Arrival rate: 80 % of the capacity measured on a burst of
+    ``n_burst`` requests."""
     import threading
     import torch
     from paper_2604_15796_gb300 import libfwi, phantoms
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    specs = phantoms.serving_requests(n_req=args.requests + 4, seed=1004, rate_hz=1.0)
+    n_requests = args.requests if n_requests is None else n_requests
+    specs = phantoms.serving_requests(n_req=n_requests + n_burst, seed=1004, rate_hz=1.0)
 
     def build(sp):
         """Request inputs (untimed): observed data = forward data of the
@@ -683,8 +708,8 @@ def run_serving(args):
         return w, sos0, dh.astype(np.complex64), prm
 
     srv = libfwi.Server(max_active=args.max_active)
-    # capacity on a burst of 4 requests
-    burst = [build(sp) for sp in specs[:4]]
+    # capacity on a burst of n_burst requests
+    burst = [build(sp) for sp in specs[:n_burst]]
     print("serving: burst requests built", file=sys.stderr, flush=True)
     t0 = time.perf_counter()
     ids = [srv.submit(w.shape, w.h, w.c0, w.elem, w.freqs, s0, d, **prm)
@@ -696,9 +721,9 @@ def run_serving(args):
     cap = len(ids) / (time.perf_counter() - t0)
     rate = 0.8 * cap
     rng = np.random.default_rng(77)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=args.requests))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_requests))
     print(f"serving: burst capacity {cap:.3f} req/s", file=sys.stderr, flush=True)
-    work = [build(sp) for sp in specs[4:4 + args.requests]]
+    work = [build(sp) for sp in specs[n_burst:n_burst + n_requests]]
     results = [None] * len(work)
     lock = threading.Lock()
     start = time.perf_counter()
@@ -728,12 +753,13 @@ def run_serving(args):
             th.join()
     wall = time.perf_counter() - start
     srv.close()
-    comp = None if args.no_comparator else serving_fp64_comparator(work, results, rate)
+    comp = None if args.no_comparator else serving_fp64_comparator(work, results, rate,
+                                                                   n_sample=n_comparator)
     lat = np.array([r["latency_ms"] for r in results])
     bad = sum(1 for r in results if r["status"] != 0)
     solves = sum(r["rhs_solves"] for r in results)
     return {"metric": METRIC, "value": solves / wall, "unit": UNIT, "n_gpus": 1,
-            "steps": len(work), "warmup": 4, "ms_per_step": 1e3 * wall / len(work),
+            "steps": len(work), "warmup": n_burst, "ms_per_step": 1e3 * wall / len(work),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 fields / FP64 Krylov scalars", "data": "synthetic",
             "config": {"workload": f"serving stream: {len(work)} reconstruction requests, "
@@ -755,13 +781,40 @@ def run_serving(args):
             "clocks": clk.summary()}
 
 
+def serving_brief(args):
+    """Latency sub-record of the headline line, measured after its timed
+    region: a short serving stream (``--serving-requests`` requests of the
+    serving workload, Poisson arrivals at 80 % of the capacity of a
+    two-request burst) with its p50/p99 reconstruction latency, and the
+    plain unbatched FP64 path's latency on the smallest request of the
+    stream, alone, against the batched path's."""
+    r = run_serving(args, n_requests=args.serving_requests, n_burst=2, n_comparator=1)
+    out = {"kind": "serving stream after the timed region (not in value)",
+           "requests": r["steps"], "failed_requests": r["failed_requests"],
+           "latency_ms": r["latency_ms"], "rhs_solves_per_s": r["value"],
+           "arrival_rate_hz": r["config"]["arrival_rate_hz"],
+           "grids": sorted({q["grid"] for q in r["requests"]})}
+    comp = r.get("comparator_fp64_unbatched")
+    if comp:
+        # the FP64 path is timed on the stream's smallest request alone (its
+        # full stream would not keep up with the arrivals); the factor is the
+        # ratio of the two paths' service times for the same request
+        row = comp["requests"][0]
+        out["fp64_unbatched"] = {
+            "request": f"{row['grid']} x {row['rhs']} RHS", "alone_ms": row[
+                "fp64_unbatched_alone_ms"], "batched_alone_ms": row["batched_alone_ms"],
+            "factor_alone": row["factor_alone"],
+            "mean_interarrival_ms": comp["mean_interarrival_ms"]}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="thyroid256",
+    ap.add_argument("--workload", default="volume3d",
                     choices=["thyroid256", "large512", "volume3d", "disc64", "planewave2d",
                              "elev3d", "serving"])
     ap.add_argument("--max-batch", type=int, default=0)
@@ -777,6 +830,9 @@ def main():
     ap.add_argument("--check-samples", type=int, default=2)
     ap.add_argument("--ref-step-s", type=float, default=2.0)
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--serving-requests", type=int, default=6,
+                    help="requests of the serving sub-record after the timed region "
+                         "(0: none)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -808,6 +864,8 @@ def main():
                          f"cores" + ("; point-source right-hand sides on the line-element "
                                      "workload's operator" if line else "")}
     line = run_ours(args, rank, world, samples)
+    if rank == 0 and world == 1 and args.serving_requests > 0:
+        line["serving"] = serving_brief(args)
     if rank == 0:
         line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
