@@ -58,7 +58,8 @@ typedef enum fwi_status {
   FWI_ERR_BREAKDOWN = 5,     /* BiCGSTAB breakdown (rho or omega = 0) */
   FWI_ERR_NONFINITE = 6,     /* a non-finite value reached a reduction */
   FWI_ERR_CANCELLED = 7,     /* fwi_cancel was called during the solve */
-  FWI_ERR_UNSUPPORTED = 8    /* grid size without a compiled FFT plan */
+  FWI_ERR_UNSUPPORTED = 8,   /* grid size without a compiled FFT plan */
+  FWI_ERR_REDUCE = 9         /* the caller's reducer (fwi_set_reducer) failed */
 } fwi_status;
 
 typedef enum fwi_precision {
@@ -120,6 +121,11 @@ typedef struct fwi_problem_desc {
                               compressibilities complex (a background pixel
                               has m = 0; fwi_contrast_from_sos without an
                               alpha map gives every pixel alpha0). */
+  int hybrid_born;         /* 1: the context keeps one more field array, the
+                              receiver-field snapshot of the hybrid Born /
+                              distorted-Born Jacobian (Sec. IV-B; see
+                              fwi_freeze_receiver_fields); 0: none (the
+                              Jacobian always uses the current fields). */
 } fwi_problem_desc;
 
 /* Per-call Krylov report.  The caller sets n_rhs and the optional host
@@ -236,6 +242,51 @@ FWI_API fwi_status fwi_admm_tv_step(fwi_ctx* ctx, void* m, void* g, void* u,
                             const void* grad, const fwi_admm_params* p,
                             double* sos_out);
 
+/* Receiver fields of the Jacobian (Sec. IV-B, hybrid Born / distorted-Born
+   approximation).  The Jacobian rows are dP_{l,e,j}/dm_n =
+   ptilde_{l,j}(n) p_{l,e}(n) with the receiver fields ptilde_{l,j} =
+   A_l^{-1} R_{l,j}; with receivers at the element positions ptilde_{l,j} =
+   k_l^2 dV p_{l,j}, the element fields.  By default J and J^H (and so the
+   m-step of fwi_admm_tv_step) take ptilde from the current forward fields
+   (the strict distorted-Born Jacobian).  The paper refreshes the receiver
+   fields only every few iterations and keeps them fixed in between:
+     freeze = 1: copy the current forward fields (of the last fwi_forward or
+                 fwi_gradient) into the context's snapshot; until the next
+                 call, J and J^H take ptilde from the snapshot and p_{l,e}
+                 from the current fields;
+     freeze = 0: back to the current fields.
+   Needs a context created with hybrid_born = 1 (FWI_ERR_INVALID_ARG
+   otherwise) and, for freeze = 1, forward fields.  Enqueued on the context
+   stream (a device-to-device copy of n_freq * n_elem * N field elements). */
+FWI_API fwi_status fwi_freeze_receiver_fields(fwi_ctx* ctx, int freeze);
+
+/* ---- Sharding over GPUs by frequency (Sec. IV-D) -------------------------
+   The paper spreads its sources over workers and aggregates the partial
+   Jacobian products.  Here the work is split by frequency: each rank (one
+   process per GPU) creates its context with a subset of the frequencies and
+   the matching rows of d_obs, so its solves, data and Jacobian rows are its
+   own, and every sum the method takes over frequencies is completed by a
+   reduction the caller supplies (NCCL on the context stream, or any other
+   all-reduce).  With a reducer set the library calls it, on the host thread
+   of the library call, on
+     - fwi_gradient: the misfit's per-block partial sums (before the host
+       adds them) and the assembled gradient (2 N_inv doubles), so that
+       every rank returns the misfit and gradient of all frequencies;
+     - fwi_admm_tv_step: each CG iteration's J^H J d (2 N_inv doubles), so
+       that every rank runs the same CG iterates and returns the same m, g,
+       u and SoS (given the same inputs on every rank);
+     - fwi_jac_adjoint: its output z.
+   fn must replace the `count` doubles at device address buf by their sum
+   over all ranks.  Work the library enqueued on cuda_stream (the context's
+   stream) before the call produces buf; work it enqueues after the call
+   reads the result, so fn must order its writes before that work (a
+   collective on cuda_stream, or a synchronise and a blocking copy back).
+   Every rank must make the same sequence of library calls.  fn returns 0
+   on success; anything else makes the library call return FWI_ERR_REDUCE.
+   fn = NULL removes the reducer.  The library itself never communicates. */
+typedef int (*fwi_reduce_fn)(void* buf, size_t count, void* cuda_stream, void* user);
+FWI_API fwi_status fwi_set_reducer(fwi_ctx* ctx, fwi_reduce_fn fn, void* user);
+
 /* ADMM initialisation (Algorithm 1): g = nabla m0, u = 0.
    m0: dev c128 [N]; g, u: dev c128 [dim][N] (out). */
 FWI_API fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u);
@@ -264,7 +315,7 @@ FWI_API fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z);
 /* ---- Serving: continuous batching of reconstructions -------------------
    A server runs whole reconstructions (Algorithm 1: contrast from the
    starting SoS, g0 = nabla m0, u0 = 0, then n_iter x [fwi_gradient,
-   fwi_admm_tv_step]) for requests of different grids, arrays and frequency
+   (receiver-field refresh), fwi_admm_tv_step]) for requests of different grids, arrays and frequency
    sets.  Requests wait in FIFO order and are admitted, first fit, as soon as
    a worker slot is free and their device footprint (fwi_workspace_bytes of
    the request plus its vectors) fits in the remaining HBM budget.  Each
@@ -280,6 +331,12 @@ typedef struct fwi_request {
   const void* d_obs;         /* host cF [n_freq][N_T][n_elem]: observed data */
   fwi_admm_params admm;      /* m_ref must be NULL */
   int n_iter;                /* ADMM-TV iterations (>= 1) */
+  int refresh_every;         /* hybrid Born schedule (Sec. IV-B): <= 1 uses
+                                the current receiver fields in every m-step;
+                                K > 1 refreshes them on iterations 0, K,
+                                2K, ... (fwi_freeze_receiver_fields right
+                                after that iteration's gradient) and keeps
+                                them fixed in between */
 } fwi_request;
 typedef struct fwi_request_result {
   int status;                /* fwi_status of the reconstruction */

@@ -319,6 +319,9 @@ fwi_status admm_step(fwi_ctx* c, void* mv, void* gv, void* uv, const void* gradv
     }
     st = jac_adjoint(c, y, z);
     if (st != FWI_OK) return st;
+    // frequency sharding: J^H J d summed over every rank's frequencies
+    st = reduce_sum(c, z, 2 * (size_t)c->Ninv);
+    if (st != FWI_OK) return st;
     {
       Prof pf(c, KC_ADMM);
       q_kernel<<<nb, 256, 0, s>>>(q, z, d, rho, gamma, G, dim, part);

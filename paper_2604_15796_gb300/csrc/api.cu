@@ -47,6 +47,7 @@ struct Layout {
   long long N;
   size_t csz;
   size_t b_ghat, b_field, b_kv, b_plane1, b_plane2, b_small, b_jsplit, b_zpart, b_vec, b_tc;
+  size_t b_rfield;  // receiver-field snapshot (hybrid_born), else 0
   size_t total;
 };
 
@@ -131,8 +132,10 @@ bool make_layout(const fwi_problem_desc* d, Layout& L, std::string* why) {
             (L.rf > 1 ? (size_t)L.N * 16 : 0) +
             sizeof(double) * (L.n_freq + 256 + 512 + 16);
   L.b_tc = (d->precision == FWI_FP64) ? 0 : tc_bops_bytes(L.n_elem, L.n_freq);
+  if (d->hybrid_born != 0 && d->hybrid_born != 1) return bad("hybrid_born must be 0 or 1");
+  L.b_rfield = d->hybrid_born ? L.b_field : 0;
   L.total = L.b_ghat + 4 * L.b_field + 5 * L.b_kv + L.b_plane1 + L.b_plane2 + L.b_small +
-            L.b_jsplit + L.b_zpart + L.b_vec + L.b_tc + 256;
+            L.b_jsplit + L.b_zpart + L.b_vec + L.b_tc + L.b_rfield + 256;
   return true;
 }
 
@@ -142,6 +145,14 @@ size_t workspace_bytes(const fwi_problem_desc* d, std::string* why) {
   Layout L;
   if (!make_layout(d, L, why)) return 0;
   return L.total;
+}
+
+fwi_status reduce_sum(fwi_ctx* c, void* buf, size_t count) {
+  if (!c->reduce_fn) return FWI_OK;
+  const int rc = c->reduce_fn(buf, count, (void*)c->stream, c->reduce_user);
+  if (rc != 0)
+    return fail(c, FWI_ERR_REDUCE, "reducer returned " + std::to_string(rc));
+  return FWI_OK;
 }
 
 }  // namespace fwi
@@ -156,7 +167,8 @@ static void release(fwi_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   prof_flush(c);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-  void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->lam, c->asrc,
+  void* bufs[] = {c->ghat, c->tw_x, c->tw_y, c->tw_z, c->p0, c->fields, c->rfields, c->lam,
+                  c->asrc,
                   c->kv[0], c->kv[1], c->kv[2], c->kv[3], c->kv[4], c->plane1, c->plane2,
                   c->mF, c->scal, c->partial, c->active, c->n_active, c->dres, c->dF,
                   c->W, c->WhW, c->dpw, c->dsyn, c->vfwd, c->sdat, c->dlossy,
@@ -270,6 +282,7 @@ fwi_status fwi_create(const fwi_problem_desc* d, void* stream, fwi_ctx** out) {
   alloc(&c->ghat, L.b_ghat);
   alloc(&c->p0, L.b_field);
   alloc(&c->fields, L.b_field);
+  alloc(&c->rfields, L.b_rfield);
   alloc(&c->lam, L.b_field);
   alloc(&c->asrc, L.b_field);
   for (int i = 0; i < 5; ++i) alloc(&c->kv[i], L.b_kv);
@@ -476,6 +489,9 @@ fwi_status fwi_gradient(fwi_ctx* ctx, const void* m, const void* d_obs, void* gr
   if (st != FWI_OK) worst = st;
   st = assemble_gradient(ctx, grad);
   if (st != FWI_OK) return st;
+  // frequency sharding: the gradient of all frequencies (Sec. IV-D)
+  st = reduce_sum(ctx, grad, 2 * (size_t)ctx->Ninv);
+  if (st != FWI_OK) return st;
   tc_err_fetch(ctx);
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "fwi_gradient");
@@ -505,6 +521,32 @@ fwi_status fwi_admm_init(fwi_ctx* ctx, const void* m0, void* g, void* u) {
   if (!m0 || !g || !u) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   ctx->err.clear();
   return admm_init(ctx, m0, g, u);
+}
+
+fwi_status fwi_set_reducer(fwi_ctx* ctx, fwi_reduce_fn fn, void* user) {
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  ctx->reduce_fn = fn;
+  ctx->reduce_user = fn ? user : nullptr;
+  return FWI_OK;
+}
+
+fwi_status fwi_freeze_receiver_fields(fwi_ctx* ctx, int freeze) {
+  CallRange nvtx_range("fwi_freeze_receiver_fields");
+  if (!ctx) return FWI_ERR_INVALID_ARG;
+  if (!ctx->rfields)
+    return fail(ctx, FWI_ERR_INVALID_ARG,
+                "the context has no receiver-field snapshot (create it with hybrid_born = 1)");
+  if (freeze != 0 && freeze != 1) return fail(ctx, FWI_ERR_INVALID_ARG, "freeze must be 0 or 1");
+  ctx->err.clear();
+  if (freeze) {
+    if (!ctx->fields_valid)
+      return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields: call fwi_forward or fwi_gradient first");
+    FWI_CUDA(ctx, cudaMemcpyAsync(ctx->rfields, ctx->fields,
+                                  (size_t)ctx->n_rhs * ctx->N * ctx->csz,
+                                  cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  ctx->rfields_frozen = freeze == 1;
+  return FWI_OK;
 }
 
 static fwi_status apply_common(fwi_ctx* ctx, int kind, const void* m, int freq, int n_rhs,
@@ -550,12 +592,16 @@ fwi_status fwi_jac_adjoint(fwi_ctx* ctx, const void* y, void* z) {
   if (!y || !z) return fail(ctx, FWI_ERR_INVALID_ARG, "missing pointer");
   if (!ctx->fields_valid) return fail(ctx, FWI_ERR_INVALID_ARG, "no forward fields");
   ctx->err.clear();
-  if (ctx->n_tx == 0) return jac_adjoint(ctx, (const double2*)y, (double2*)z);
-  // J^H = J_point^H W^H
-  fwi_status st = synth(ctx, ctx->W, 1, ctx->n_elem, ctx->n_tx, (const double2*)y, ctx->dsyn,
-                        nullptr);
+  fwi_status st;
+  if (ctx->n_tx == 0) {
+    st = jac_adjoint(ctx, (const double2*)y, (double2*)z);
+  } else {
+    // J^H = J_point^H W^H
+    st = synth(ctx, ctx->W, 1, ctx->n_elem, ctx->n_tx, (const double2*)y, ctx->dsyn, nullptr);
+    if (st == FWI_OK) st = jac_adjoint(ctx, ctx->dsyn, (double2*)z);
+  }
   if (st != FWI_OK) return st;
-  return jac_adjoint(ctx, ctx->dsyn, (double2*)z);
+  return reduce_sum(ctx, z, 2 * (size_t)ctx->Ninv);  // frequency sharding
 }
 
 fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {

@@ -51,6 +51,8 @@ struct fwi_ctx {
   void* tw_z = nullptr;
   void* p0 = nullptr;               // [n_rhs][N] incident fields
   void* fields = nullptr;           // [n_rhs][N] forward solution
+  void* rfields = nullptr;          // [n_rhs][N] receiver-field snapshot (hybrid_born)
+  bool rfields_frozen = false;      // J / J^H take ptilde from rfields
   void* lam = nullptr;              // [n_rhs][N] adjoint work / solution
   void* asrc = nullptr;             // [n_rhs][N] adjoint right-hand sides
   void* kv[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // R, RH, P, V, T
@@ -107,6 +109,9 @@ struct fwi_ctx {
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // caller-supplied sum over ranks (frequency sharding), or none
+  fwi_reduce_fn reduce_fn = nullptr;
+  void* reduce_user = nullptr;
   std::atomic<bool> cancel{false};
   std::string err;
   size_t bytes = 0;
@@ -132,6 +137,13 @@ fwi_status adjoint_sources_conj(fwi_ctx* c, void* out);
 fwi_status assemble_gradient(fwi_ctx* c, void* grad);
 fwi_status jac_forward(fwi_ctx* c, const void* a_c128, double2* y);
 fwi_status jac_adjoint(fwi_ctx* c, const double2* y, double2* z);
+// Sum of `count` doubles at device address buf over the ranks of a
+// frequency-sharded run (the caller's reducer; a no-op without one).
+fwi_status reduce_sum(fwi_ctx* c, void* buf, size_t count);
+// the fields the Jacobian's receiver side (ptilde) is taken from
+inline const void* receiver_fields(const fwi_ctx* c) {
+  return c->rfields_frozen ? c->rfields : c->fields;
+}
 // plane-wave synthesis out[l] = op(A[l]) in[l] (op: A, or A^H when herm),
 // op(A[l]) of R x K, in[l] of K x n_elem; conj_out (field precision) or NULL
 fwi_status synth(fwi_ctx* c, const double2* A, int herm, int R, int K, const double2* in,
@@ -146,7 +158,8 @@ bool tc_usable(const fwi_ctx* c);
 size_t tc_bops_bytes(int n_elem, int n_freq);
 int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const float2* Q,
                          float2* part);
-int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart);
+int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* Q, const float2* X,
+                   float2* zpart);
 int tc_adjoint_sources(fwi_ctx* c, const float2* B, const float2* Q, float2* out);
 void tc_err_fetch(fwi_ctx* c);
 fwi_status tc_err_check(fwi_ctx* c);

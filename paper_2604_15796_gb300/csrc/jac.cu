@@ -548,6 +548,13 @@ template <typename T> static fwi_status residual_t(fwi_ctx* c, const void* d_obs
     fwi_status st = data_scale(c, (cplx<T>*)c->dF, (const cplx<T>*)c->dF, 0);
     if (st != FWI_OK) return st;
   }
+  {
+    // frequency sharding: the partial sums of every rank's frequencies
+    // (reduced whether or not this caller reads the misfit, so that every
+    // rank makes the same reductions)
+    fwi_status st = reduce_sum(c, misfit_parts(c), kMisfitBlocks);
+    if (st != FWI_OK) return st;
+  }
   if (misfit) {
     FWI_CUDA(c, cudaMemcpyAsync(c->h_red, misfit_parts(c), sizeof(double) * kMisfitBlocks,
                                 cudaMemcpyDeviceToHost, c->stream));
@@ -613,7 +620,8 @@ fwi_status assemble_gradient(fwi_ctx* c, void* grad) {
   return c->fp64 ? gradient_t<double>(c, grad) : gradient_t<float>(c, grad);
 }
 
-// (J a)_{l,e,j} = k_l^2 dV sum_n p_e(n) p_j(n) a_n
+// (J a)_{l,e,j} = k_l^2 dV sum_n p_e(n) p_j(n) a_n, p_j from the receiver
+// fields (the current fields, or their frozen snapshot: Sec. IV-B)
 template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a, double2* y) {
   fwi_status st = Jac<T>::upload_scales(c);
   if (st != FWI_OK) return st;
@@ -628,7 +636,7 @@ template <typename T> static fwi_status jac_forward_t(fwi_ctx* c, const void* a,
   }
   FWI_CUDA(c, cudaGetLastError());
   st = Jac<T>::contract(c, (const cplx<T>*)c->fields, (const cplx<T>*)c->aF,
-                        (const cplx<T>*)c->fields, y);
+                        (const cplx<T>*)receiver_fields(c), y);
   if (st != FWI_OK) return st;
   return data_scale(c, y, (const double2*)y, 0);  // lossy background: k_l^2 dV
 }
@@ -637,7 +645,8 @@ fwi_status jac_forward(fwi_ctx* c, const void* a, double2* y) {
   return c->fp64 ? jac_forward_t<double>(c, a, y) : jac_forward_t<float>(c, a, y);
 }
 
-// (J^H b)_n = sum_l k_l^2 dV sum_e conj(p_e(n)) sum_j conj(p_j(n)) b_ej
+// (J^H b)_n = sum_l k_l^2 dV sum_e conj(p_e(n)) sum_j conj(p_j(n)) b_ej, p_j
+// from the receiver fields
 template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2* y,
                                                       double2* z_out) {
   fwi_status st = Jac<T>::upload_scales(c);
@@ -652,7 +661,8 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
   }
   if constexpr (std::is_same<T, float>::value) {
     if (tc_usable(c)) {
-      const int np = tc_jh_partials(c, y, (const float2*)c->fields, (float2*)c->zpart);
+      const int np = tc_jh_partials(c, y, (const float2*)receiver_fields(c),
+                                    (const float2*)c->fields, (float2*)c->zpart);
       if (np < 0) return FWI_ERR_CUDA;
       Prof p(c, KC_MISC);
       sum_parts_kernel<T><<<blocks_for(c->N, 256, c->n_sm * 8), 256, 0, c->stream>>>(
@@ -674,8 +684,8 @@ template <typename T> static fwi_status jac_adjoint_t(fwi_ctx* c, const double2*
     const double fe = (double)c->n_freq * c->n_elem * c->N;
     Prof p(c, KC_MIX_JH, 2.0 * fe * sizeof(cplx<T>), 8.0 * fe * c->n_elem + 8.0 * fe);
     mix_kernel<T, true><<<grid, 256, 0, c->stream>>>(
-        (const cplx<T>*)c->dF, (const cplx<T>*)c->fields, 1, (const cplx<T>*)c->fields,
-        (cplx<T>*)c->zpart, c->red, c->n_elem, c->N);
+        (const cplx<T>*)c->dF, (const cplx<T>*)receiver_fields(c), 1,
+        (const cplx<T>*)c->fields, (cplx<T>*)c->zpart, c->red, c->n_elem, c->N);
   }
   FWI_CUDA(c, cudaGetLastError());
   Prof p(c, KC_MISC);

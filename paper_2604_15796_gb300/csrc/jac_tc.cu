@@ -384,7 +384,8 @@ constexpr int M_CONV_BYTES = M_A_BYTES + M_B_BYTES;
 constexpr int M_SMEM = M_CONV * M_CONV_BYTES + M_RAW * M_RAW_BYTES;
 
 struct JhArgs {
-  const float2* X;     // [n_freq][NE][N]
+  const float2* X;     // [n_freq][NE][N] mixed operand (rows j)
+  const float2* Xe;    // [n_freq][NE][N] FUSED: epilogue operand (rows e)
   const float* bops;   // [n_freq][nbe][nks] k-step blocks of the B stack (hi, lo)
   const double* scale; // [n_freq]
   float2* zpart;       // FUSED: [n_freq][nbe][N]; else W itself, [n_freq][NE][N]
@@ -451,7 +452,7 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
       const bool ok = mbar_wait(smem_addr(&bar_done[b]), (k >> 1) & 1, &abort_flag, p.err,
                                 kErrWaitDone);
       fence_after_sync();
-      const float2* Xl = p.X + (long long)l * p.NE * p.N;
+      const float2* Xl = p.Xe + (long long)l * p.NE * p.N;
       const float sc = (float)p.scale[l];
       const uint32_t lane_addr = tmem + ((uint32_t)(32 * q) << 16) + 256u * b;
       const long long n = (long long)pb * ROWS + r;
@@ -706,8 +707,8 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
 namespace {
 
 template <bool FUSED, typename V>
-int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int kclass,
-           double bytes, double flops) {
+int tc_mix(fwi_ctx* c, const V* B, const float2* X, const float2* Xe, int conj_x, float2* out,
+           int kclass, double bytes, double flops) {
   cudaError_t e = set_attrs();
   if (e != cudaSuccess) {
     cuda_fail(c, e, "tc_mix attributes");
@@ -729,7 +730,7 @@ int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int
   const int npb = (int)((c->N + ROWS - 1) / ROWS);
   const int units = c->n_freq * nbe * npb;
   const int grid = units < c->n_sm ? units : c->n_sm;
-  JhArgs args{X, (const float*)c->tc_bops, c->red, out, c->tc_err, c->N,
+  JhArgs args{X, Xe, (const float*)c->tc_bops, c->red, out, c->tc_err, c->N,
               c->n_elem, c->n_freq, nbe, nks, npb, units, conj_x};
   {
     Prof pf(c, kclass, bytes, flops);
@@ -745,15 +746,18 @@ int tc_mix(fwi_ctx* c, const V* B, const float2* X, int conj_x, float2* out, int
 
 }  // namespace
 
-int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* X, float2* zpart) {
+// z_l[n] = s_l sum_e conj(X[e][n]) sum_j y[e][j] conj(Q[j][n]): Q the
+// receiver fields (mixed by the MMAs), X the transmit fields (epilogue).
+int tc_jh_partials(fwi_ctx* c, const double2* y, const float2* Q, const float2* X,
+                   float2* zpart) {
   const double fe = (double)c->n_freq * c->n_elem * c->N;
-  return tc_mix<true>(c, y, X, 1, zpart, KC_MIX_JH, 2.0 * fe * sizeof(float2),
+  return tc_mix<true>(c, y, Q, X, 1, zpart, KC_MIX_JH, 2.0 * fe * sizeof(float2),
                       8.0 * fe * c->n_elem + 8.0 * fe);
 }
 
 int tc_adjoint_sources(fwi_ctx* c, const float2* B, const float2* Q, float2* out) {
   const double fe = (double)c->n_freq * c->n_elem * c->N;
-  return tc_mix<false>(c, B, Q, 0, out, KC_MIX_SOURCES, 2.0 * fe * sizeof(float2),
+  return tc_mix<false>(c, B, Q, nullptr, 0, out, KC_MIX_SOURCES, 2.0 * fe * sizeof(float2),
                        8.0 * fe * c->n_elem);
 }
 

@@ -32,6 +32,7 @@ struct Request {
   std::vector<char> d_obs;
   fwi_admm_params admm{};
   int n_iter = 1;
+  int refresh_every = 1;
   long long n = 0;       // voxels
   size_t csz = 8;        // field element bytes
   size_t bytes = 0;      // admitted footprint
@@ -129,6 +130,12 @@ void run_request(fwi_server* srv, Request& r) {
       res.krylov_iters_mean = iters_n ? iters_sum / iters_n : 0.0;
       if (k == 0) res.misfit_first = mis;
       res.misfit_last = mis;
+      // hybrid Born schedule (Sec. IV-B): receiver fields of this
+      // iteration's forward solve on iterations 0, K, 2K, ..., frozen between
+      if (r.refresh_every > 1 && k % r.refresh_every == 0) {
+        const fwi_status s3 = fwi_freeze_receiver_fields(ctx, 1);
+        if (s3 != FWI_OK) { status = s3; break; }
+      }
       fwi_status s2 = fwi_admm_tv_step(ctx, m, g, u, grad, &r.admm,
                                        k == r.n_iter - 1 ? (double*)sos : nullptr);
       if (s2 != FWI_OK) { status = s2; break; }
@@ -248,6 +255,9 @@ fwi_status fwi_server_submit(fwi_server* s, const fwi_request* r, long long* id)
   q->d_obs.assign((const char*)r->d_obs, (const char*)r->d_obs + nd);
   q->admm = r->admm;
   q->n_iter = r->n_iter;
+  q->refresh_every = r->refresh_every > 1 ? r->refresh_every : 1;
+  // the hybrid Born schedule needs the context's receiver-field snapshot
+  q->desc.hybrid_born = q->refresh_every > 1 ? 1 : 0;
   size_t ws = 0;
   q->bytes = request_bytes(q->desc, q->n, q->csz, ws);
   if (q->bytes == 0) return fail(nullptr, FWI_ERR_INVALID_ARG, "unsupported request problem");

@@ -28,11 +28,12 @@ FWI_ERR_BREAKDOWN = 5
 FWI_ERR_NONFINITE = 6
 FWI_ERR_CANCELLED = 7
 FWI_ERR_UNSUPPORTED = 8
+FWI_ERR_REDUCE = 9
 FWI_MIXED = 0
 FWI_FP64 = 1
 
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "NOMEM", 3: "CUDA", 4: "NOT_CONVERGED",
-                5: "BREAKDOWN", 6: "NONFINITE", 7: "CANCELLED", 8: "UNSUPPORTED"}
+                5: "BREAKDOWN", 6: "NONFINITE", 7: "CANCELLED", 8: "UNSUPPORTED", 9: "REDUCE"}
 
 
 class fwi_problem_desc(Structure):
@@ -41,7 +42,7 @@ class fwi_problem_desc(Structure):
                 ("freq_hz", POINTER(c_double)), ("krylov_tol", c_double),
                 ("krylov_max_it", c_int), ("precision", c_int), ("max_batch", c_int),
                 ("n_tx", c_int), ("tx_angle", POINTER(c_double)), ("elem_length", c_double),
-                ("inv_factor", c_int), ("alpha0", c_double)]
+                ("inv_factor", c_int), ("alpha0", c_double), ("hybrid_born", c_int)]
 
 
 class fwi_solve_info(Structure):
@@ -77,7 +78,8 @@ class fwi_admm_params(Structure):
 
 class fwi_request(Structure):
     _fields_ = [("problem", fwi_problem_desc), ("sos0", POINTER(c_double)),
-                ("d_obs", c_void_p), ("admm", fwi_admm_params), ("n_iter", c_int)]
+                ("d_obs", c_void_p), ("admm", fwi_admm_params), ("n_iter", c_int),
+                ("refresh_every", c_int)]
 
 
 class fwi_request_result(Structure):
@@ -104,6 +106,8 @@ EXPORTS = {
     "fwi_admm_tv_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                  POINTER(fwi_admm_params), c_void_p]),
     "fwi_admm_init": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "fwi_freeze_receiver_fields": (c_int, [c_void_p, c_int]),
+    "fwi_set_reducer": (c_int, [c_void_p, c_void_p, c_void_p]),
     "fwi_apply_K": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_apply_A": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "fwi_apply_AH": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
@@ -164,6 +168,11 @@ fwi_adjoint = _bind("fwi_adjoint")
 fwi_gradient = _bind("fwi_gradient")
 fwi_admm_tv_step = _bind("fwi_admm_tv_step")
 fwi_admm_init = _bind("fwi_admm_init")
+fwi_freeze_receiver_fields = _bind("fwi_freeze_receiver_fields")
+fwi_set_reducer = _bind("fwi_set_reducer")
+
+# int (*fwi_reduce_fn)(void* buf, size_t count, void* cuda_stream, void* user)
+REDUCE_FN = ctypes.CFUNCTYPE(c_int, c_void_p, c_size_t, c_void_p, c_void_p)
 fwi_apply_K = _bind("fwi_apply_K")
 fwi_apply_A = _bind("fwi_apply_A")
 fwi_apply_AH = _bind("fwi_apply_AH")
@@ -184,6 +193,20 @@ fwi_reset_stats = _bind("fwi_reset_stats")
 fwi_version = _bind("fwi_version")
 
 
+def reduce_callback(fn):
+    """C reducer (REDUCE_FN) that calls ``fn(ptr, count, stream)`` and
+    returns 0, or 1 after printing the exception it raised."""
+    def cb(buf, count, stream, user):
+        try:
+            fn(int(buf or 0), int(count), int(stream or 0))
+            return 0
+        except Exception:  # reported to the library as a failed reduction
+            import traceback
+            traceback.print_exc()
+            return 1
+    return REDUCE_FN(cb)
+
+
 class FwiError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libfwi {STATUS_NAMES.get(status, status)}: {msg}")
@@ -191,7 +214,8 @@ class FwiError(RuntimeError):
 
 
 def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-              max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0):
+              max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0,
+              hybrid_born=False):
     """fwi_problem_desc from array-order ``shape`` ((Nz, Nx) or (Nz, Ny, Nx)).
     ``tx_angles``: steering angles [rad] of plane-wave transmits, or None for
     point transmits at every element.  ``elem_length``: 3-D line elements of
@@ -218,6 +242,7 @@ def make_desc(shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6, max_it=1
     d.elem_length = float(elem_length)
     d.inv_factor = int(inv_factor)
     d.alpha0 = float(alpha0)
+    d.hybrid_born = int(bool(hybrid_born))
     tx = None
     if tx_angles is not None and len(tx_angles) > 0:
         tx = np.ascontiguousarray(tx_angles, dtype=np.float64)
@@ -321,11 +346,12 @@ class Context:
     (data [n_freq][N_T][N_E]); elem_length: 3-D line elements [m];
     inv_factor: inversion mesh of inv_factor^d pixels per cell (m, grad,
     g, u, SoS on it: ``inv_shape``); alpha0: background attenuation
-    [Np/m/Hz]."""
+    [Np/m/Hz]; hybrid_born: keep a receiver-field snapshot for
+    ``freeze_receiver_fields``."""
 
     def __init__(self, shape, h, c0, elem, freqs, precision=FWI_MIXED, tol=1e-6,
                  max_it=1000, max_batch=0, stream=None, tx_angles=None, elem_length=0.0,
-                 inv_factor=1, alpha0=0.0):
+                 inv_factor=1, alpha0=0.0, hybrid_born=False):
         import torch
         self.torch = torch
         self.shape = tuple(shape)
@@ -344,7 +370,7 @@ class Context:
         self.field_dtype = torch.complex128 if precision == FWI_FP64 else torch.complex64
         self.desc, self._keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it,
                                           max_batch, tx_angles, elem_length, inv_factor,
-                                          alpha0)
+                                          alpha0, hybrid_born)
         self.workspace_bytes = int(fwi_workspace_bytes(byref(self.desc)))
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -462,6 +488,21 @@ class Context:
         st = fwi_admm_tv_step(self.handle, *args, byref(p), sp)
         _log_call("admm_tv_step", self, st, time.perf_counter() - t0)
         self._check(st)
+
+    def set_reducer(self, fn):
+        """Frequency sharding (fwi_set_reducer): ``fn(ptr, count, stream)``
+        replaces the ``count`` doubles at device address ``ptr`` by their
+        sum over all ranks, ordered on the CUDA stream handle ``stream``
+        (see ``sharding``); None removes it.  An exception in fn makes the
+        library call fail with FWI_ERR_REDUCE."""
+        self._reducer = None if fn is None else reduce_callback(fn)
+        self._check(fwi_set_reducer(self.handle, self._reducer, None))
+
+    def freeze_receiver_fields(self, freeze=True):
+        """Hybrid Born schedule (Sec. IV-B): True snapshots the current
+        forward fields as the Jacobian's receiver fields until the next call;
+        False returns to the current fields."""
+        self._check(fwi_freeze_receiver_fields(self.handle, int(bool(freeze))))
 
     def apply(self, kind, vin, freq, m=None):
         nb = vin.shape[0]
@@ -583,17 +624,21 @@ class Server:
 
     def submit(self, shape, h, c0, elem, freqs, sos0, d_obs, n_iter=5, lam=1e-4, rho=1e-3,
                gamma=1e-5, n_cg=10, dual_step=0.0, precision=FWI_MIXED, tol=1e-6, max_it=1000,
-               max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0):
+               max_batch=0, tx_angles=None, elem_length=0.0, inv_factor=1, alpha0=0.0,
+               refresh_every=1):
         """Queue a reconstruction; host numpy inputs (sos0 float64 of the inversion mesh,
         d_obs [n_freq][N_T][n_elem], complex64 for FWI_MIXED and complex128
         for FWI_FP64).  max_batch limits the right-hand sides per Krylov launch
         (0: all); tx_angles selects plane-wave transmits, elem_length 3-D line
         elements, inv_factor an inversion mesh (sos0 and the result on it),
-        alpha0 an attenuating background.
+        alpha0 an attenuating background, refresh_every > 1 the hybrid Born
+        schedule of the receiver fields (refreshed every refresh_every
+        iterations).
         Returns the request id."""
         req = fwi_request()
         desc, keep = make_desc(shape, h, c0, elem, freqs, precision, tol, max_it, max_batch,
-                               tx_angles, elem_length, inv_factor, alpha0)
+                               tx_angles, elem_length, inv_factor, alpha0,
+                               hybrid_born=refresh_every > 1)
         req.problem = desc
         sos0 = np.ascontiguousarray(sos0, dtype=np.float64)
         cdt = np.complex128 if precision == FWI_FP64 else np.complex64
@@ -611,6 +656,7 @@ class Server:
         req.admm.lambda_, req.admm.rho, req.admm.gamma = lam, rho, gamma
         req.admm.dual_step, req.admm.n_cg, req.admm.m_ref = dual_step, n_cg, None
         req.n_iter = n_iter
+        req.refresh_every = int(refresh_every)
         rid = ctypes.c_longlong()
         st = fwi_server_submit(self.handle, byref(req), byref(rid))
         if st != FWI_OK:
