@@ -275,6 +275,14 @@ def run_ours(args, rank, world, samples):
             ctx.set_jac_tensor_cores(False)
         if args.one_chain:
             ctx.set_overlap(False)
+        if args.no_col_tma:
+            ctx.set_col_tma(False)
+        if args.no_row_l2_prefetch:
+            ctx.set_row_l2_prefetch(False)
+        if args.no_spectrum_stage:
+            ctx.set_col_spectrum_stage(False)
+        if args.no_jac_tma:
+            ctx.set_jac_tma(False)
         tuning = ctx.tuning()
         c128 = torch.complex128
         sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
@@ -427,7 +435,10 @@ def run_ours(args, rank, world, samples):
                    "krylov_tol": 1e-6, "admm": {k: v for k, v in params.items()},
                    "jacobian": "tensor cores (tcgen05, 3xTF32)" if tensor
                    else "CUDA cores (FP32 FMA)",
-                   "krylov_chains": 2 if tuning.get("overlap_halves") else 1},
+                   "krylov_chains": 2 if tuning.get("overlap_halves") else 1,
+                   "tuning": {k: tuning.get(k) for k in ("row_fwd", "row_inv", "col", "col_y",
+                                                         "col_tma", "col_spectrum_stage",
+                                                         "jac_tma", "row_l2_prefetch")}},
         "gradient_evals_per_s": args.steps * world / (ms / 1e3),
         "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
                            "fwd_mean": float(its[:, 2].mean()),
@@ -825,6 +836,14 @@ def main():
                     help="iterate each batch as one chain (no two-stream overlap)")
     ap.add_argument("--cuda-core-jacobian", action="store_true",
                     help="run the pixel contractions on CUDA cores instead of tensor cores")
+    ap.add_argument("--no-col-tma", action="store_true",
+                    help="column passes read their tiles with plain loads instead of TMA")
+    ap.add_argument("--no-row-l2-prefetch", action="store_true",
+                    help="row passes without the L2 prefetch of their next work item")
+    ap.add_argument("--no-spectrum-stage", action="store_true",
+                    help="the convolution reads the kernel spectrum from global memory")
+    ap.add_argument("--no-jac-tma", action="store_true",
+                    help="tensor-core contractions load their operand tiles with cp.async")
     ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--check-samples", type=int, default=2)

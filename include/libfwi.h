@@ -461,9 +461,28 @@ typedef struct fwi_tuning {
                            ("pipeline wait timed out"); the context stays
                            usable.  Applies once; reads back as 0. */
   int col_tma;          /* 1 (default): the FP32 column passes stage their
-                           input tiles in shared memory with TMA tensor
-                           copies, the next tile's copy overlapping the
-                           current tile's transforms; 0: plain loads.
+                           input tiles (and, for the 3-D and smaller 2-D
+                           convolutions, their kernel-spectrum tiles) in
+                           shared memory with TMA tensor copies, the next
+                           tile's copy overlapping the current tile's
+                           transforms, and read their twiddles from shared
+                           memory; 0: plain loads from global memory.  The
+                           same arithmetic on the same values: results agree
+                           to FP32 rounding. */
+  int col_spectrum_stage; /* 1 (default): with col_tma, the convolution also
+                           stages its kernel-spectrum tiles with TMA where
+                           they fit (half the column's rows, the spectrum
+                           being even; at most 256 rows); 0: the spectrum
+                           is read from global memory.  Results agree to
+                           FP32 rounding. */
+  int jac_tma;          /* 1 (default): the tensor-core pixel contractions
+                           receive their raw FP32 operand tiles by TMA
+                           tensor copies issued by one producer thread;
+                           0: every producer copies its rows with cp.async.
+                           Results are bitwise the same. */
+  int row_l2_prefetch;  /* 1 (default): the row passes prefetch the HBM rows
+                           of their next work item into L2 while the
+                           current item transforms; 0: no prefetch.
                            Results are bitwise the same. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);

@@ -53,6 +53,7 @@ template <typename T> struct RowFwdArgs {
   int rows;            // lines per RHS
   int ntiles;
   long long N;         // elements per RHS vector
+  int l2pf;            // prefetch the next item's rows into L2
 };
 
 template <typename T> struct RowInvArgs {
@@ -69,6 +70,7 @@ template <typename T> struct RowInvArgs {
   double2* partial;
   int nx, rows, ntiles;
   long long N;
+  int l2pf;              // prefetch the next item's rows into L2
 };
 
 template <typename T> struct ColArgs {
@@ -81,11 +83,13 @@ template <typename T> struct ColArgs {
   int ncols, nplanes;
   const cplx<T>* ghat;      // CONV: [freq][L][ncols], scaled
   long long ghat_freq_stride;
+  int n_freq;               // frequencies held in ghat
   const cplx<T>* tw;
   const int* active; const int* n_active; int nb;
   int rhs0, n_elem;         // global RHS index = rhs0 + slot; freq = idx / n_elem
   int freq_fixed;           // >= 0: every RHS uses this frequency
   int tma;                  // FP32, zero-padded input: stage tiles with TMA
+  int gstage;               // with tma: also stage the kernel-spectrum tiles
   int* err;                 // error word of bounded waits (or NULL)
 };
 

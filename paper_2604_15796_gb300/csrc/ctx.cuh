@@ -85,6 +85,9 @@ struct fwi_ctx {
   int* h_tc_err = nullptr;          // pinned host mirror
   bool use_tc = true;               // tensor-core pixel contractions (FP32 fields)
   int col_tma = 1;                  // column passes stage tiles with TMA (FP32)
+  int col_gstage = 1;               // ... and the convolution's kernel-spectrum tiles
+  int row_l2pf = 1;                 // row passes prefetch their next item into L2
+  int jac_tma = 1;                  // tensor-core contractions take raw tiles by TMA
   int tc_stall = 0;                 // next contraction withholds its first stage (test)
   double* red = nullptr;            // reduction scratch (doubles)
   double* h_red = nullptr;          // pinned host mirror

@@ -80,6 +80,12 @@ template <typename V> FWI_HD V cmulc(V a, V b) {
   V z; z.x = a.x * b.x + a.y * b.y; z.y = a.y * b.x - a.x * b.y; return z;
 }
 template <typename V> FWI_HD V cconj(V a) { a.y = -a.y; return a; }
+// Twiddle-table element: from shared memory (TWS) or through the read-only
+// path from global memory.
+template <bool TWS, typename V> FWI_HD V tw_at(const V* p) {
+  if constexpr (TWS) return *p;
+  else return FWI_LDG(p);
+}
 template <typename V, typename S> FWI_HD V cscale(V a, S s) { a.x *= s; a.y *= s; return a; }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV, typename V> FWI_HD V mul_mi(V a) {
@@ -322,7 +328,7 @@ template <int L_, int R1_, int R2_, int TL_> struct Plan {
 // four-step twiddle w_L^{n2 k1} (table tw of L entries, forward sign), and
 // stores y[n2][k1] into shared memory.  HALF_IN: the samples n1 >= R1/2 are
 // zero (a zero-padded line) and the DFTs skip them.
-template <class P, typename T, bool HALF_IN = false>
+template <class P, typename T, bool HALF_IN = false, bool TWS = false>
 FWI_HD void phaseA_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                          const cplx<T>* tw) {
 #pragma unroll
@@ -334,7 +340,7 @@ FWI_HD void phaseA_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
 #pragma unroll
       for (int k1 = 0; k1 < P::R1; ++k1) {
         cplx<T> z = v[i * P::R1 + k1];
-        if (k1 > 0 && n2 > 0) z = cmul(z, FWI_LDG(tw + n2 * k1));
+        if (k1 > 0 && n2 > 0) z = cmul(z, tw_at<TWS>(tw + n2 * k1));
         sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
       }
     }
@@ -360,7 +366,7 @@ FWI_HD void phaseB_load(int t, cplx<T>* v, const cplx<T>* sm, int sj, int pad) {
 // Phase C (inverse): v[i*R2 + k2] holds X[k1 + R1 k2] for each owned k1.
 // Inverse R2-point DFTs over k2, conjugate twiddle w_L^{-n2 k1}, store
 // y[n2][k1] to shared memory.
-template <class P, typename T>
+template <class P, typename T, bool TWS = false>
 FWI_HD void phaseC_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                          const cplx<T>* tw) {
 #pragma unroll
@@ -371,7 +377,7 @@ FWI_HD void phaseC_store(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
 #pragma unroll
       for (int n2 = 0; n2 < P::R2; ++n2) {
         cplx<T> z = v[i * P::R2 + n2];
-        if (k1 > 0 && n2 > 0) z = cmulc(z, FWI_LDG(tw + n2 * k1));
+        if (k1 > 0 && n2 > 0) z = cmulc(z, tw_at<TWS>(tw + n2 * k1));
         sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
       }
     }

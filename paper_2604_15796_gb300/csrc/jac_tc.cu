@@ -17,14 +17,18 @@
 // accuracy; accumulation is FP32 in TMEM and partial sums over CTAs are
 // combined in FP64 by the callers' reduction kernels.
 //
-// Pipelines: four producer warps stream raw FP32 tiles with cp.async
-// (several stages ahead), split them into the TF32 operand planes of a
-// shared-memory stage and signal an mbarrier; one warp issues the MMAs and
+// Pipelines: raw FP32 operand tiles arrive several stages ahead, by TMA
+// tensor copies that one producer thread issues (or, without TMA, by the
+// producers' own cp.async); four producer warps split them into the TF32
+// operand planes of a shared-memory stage and signal an mbarrier; one warp
+// issues the MMAs and
 // releases the stage with tcgen05.commit; two TMEM accumulators alternate so
 // that four more warps read one out while the MMAs fill the other.  Every
 // wait is bounded (tc.cuh).
+#include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "ctx.cuh"
 #include "prof.cuh"
@@ -134,6 +138,24 @@ template <bool SHARED> struct CRaw {
   static constexpr int TILES = C_CONV * C_CONV_BYTES + N * BYTES;
   static constexpr int SMEM = TILES + 4 * C_TILE_BYTES;
 };
+// Raw stages filled by TMA: rows of 64 bytes without padding, written with
+// the 64-byte swizzle (16-byte chunk q of row r lands at chunk q ^ ((r / 2)
+// mod 4)), which keeps the producers' 16-byte row reads free of bank
+// conflicts; stages 1024-byte aligned for the swizzle pattern.
+template <bool SHARED> struct CRawT {
+  static constexpr int N = SHARED ? 8 : 4;
+  static constexpr int TILE = ROWS * 64;  // one operand's box
+  static constexpr int X = 0, Q = TILE;
+  static constexpr int A = (SHARED ? 1 : 2) * TILE;
+  static constexpr int BYTES = ((A + 64 + 1023) / 1024) * 1024;
+  static constexpr int TX = (SHARED ? 1 : 2) * TILE;  // bytes the TMA copies deliver
+  static constexpr int TILES = C_CONV * C_CONV_BYTES + N * BYTES;
+  static constexpr int SMEM = TILES + 4 * C_TILE_BYTES;
+};
+// Byte offset of 16-byte chunk q of row r in a swizzled 64-byte-row tile.
+__device__ __forceinline__ uint32_t swz64(int r, int q) {
+  return (uint32_t)(r * 64 + ((q ^ ((r >> 1) & 3)) << 4));
+}
 
 struct ContractArgs {
   const float2* X;
@@ -153,15 +175,21 @@ struct ContractArgs {
 // drain warp owns the 32 TMEM lanes of its quadrant (32 rows e) and moves
 // 16 columns at a time through a shared transpose tile, so that its global
 // read-modify-write covers two 128-byte row segments per instruction.
-template <bool SHARED>
-__global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs p) {
+// XTMA: the raw X (and Q) tiles arrive by TMA tensor copies (64-byte
+// swizzle) issued by one producer thread and completing on bar_raw; the
+// weights a still come by cp.async.  Otherwise every producer copies its
+// rows with cp.async.
+template <bool SHARED, bool XTMA>
+__global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(
+    ContractArgs p, const __grid_constant__ CUtensorMap xmap,
+    const __grid_constant__ CUtensorMap qmap) {
   using namespace tc;
-  using RW = CRaw<SHARED>;
+  using RW = typename std::conditional<XTMA, CRawT<SHARED>, CRaw<SHARED>>::type;
   constexpr int C_RAW = RW::N, C_RAW_BYTES = RW::BYTES;
   constexpr int C_RAW_X = RW::X, C_RAW_Q = RW::Q, C_RAW_A = RW::A;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[C_CONV], bar_empty[C_CONV], bar_done[2],
-      bar_freed[2], bar_final;
+      bar_freed[2], bar_final, bar_raw[C_RAW];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -186,8 +214,17 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
       mbar_init(smem_addr(&bar_freed[b]), 128);
     }
     mbar_init(smem_addr(&bar_final), 1);
+    if (XTMA)
+      for (int i = 0; i < C_RAW; ++i) mbar_init(smem_addr(&bar_raw[i]), 1);
     abort_flag = 0;
     mbar_init_fence();
+    if (XTMA) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap))
+                   : "memory");
+      if (!same_rows)
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&qmap))
+                     : "memory");
+    }
   }
   if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 512);
   fence_before_sync();
@@ -261,18 +298,29 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
       if (g < nch) {
         const long long n0 = n_begin + (long long)g * KS;
         const uint32_t rb = raw0 + (uint32_t)((g % C_RAW) * C_RAW_BYTES);
-        const long long n = n0 + 2 * fq;
-        const bool okn = n < n_end;
+        if (XTMA) {
+          // k-steps never straddle a chunk end (chunks are whole k-steps);
+          // rows e >= NE and pixels n >= N are outside the tensor: zero fill
+          if (r == 0) {
+            const uint32_t bar = smem_addr(&bar_raw[g % C_RAW]);
+            mbar_arrive_expect_tx(bar, (uint32_t)CRawT<SHARED>::TX);
+            tma_load_3d(rb + C_RAW_X, &xmap, (int)(2 * n0), eb * ROWS, l, bar);
+            if (!same_rows) tma_load_3d(rb + C_RAW_Q, &qmap, (int)(2 * n0), jb * ROWS, l, bar);
+          }
+        } else {
+          const long long n = n0 + 2 * fq;
+          const bool okn = n < n_end;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int rr = fr + 32 * k;
-          const int er = eb * ROWS + rr, jr = jb * ROWS + rr;
-          const bool okx = okn && er < p.NE, okq = okn && jr < p.NE;
-          cp_async16(rb + C_RAW_X + rr * C_RAWROW + 16 * fq,
-                     okx ? Xl + (long long)er * p.N + n : Xl, okx ? 16u : 0u);
-          if (!same_rows)
-            cp_async16(rb + C_RAW_Q + rr * C_RAWROW + 16 * fq,
-                       okq ? Ql + (long long)jr * p.N + n : Ql, okq ? 16u : 0u);
+          for (int k = 0; k < 4; ++k) {
+            const int rr = fr + 32 * k;
+            const int er = eb * ROWS + rr, jr = jb * ROWS + rr;
+            const bool okx = okn && er < p.NE, okq = okn && jr < p.NE;
+            cp_async16(rb + C_RAW_X + rr * C_RAWROW + 16 * fq,
+                       okx ? Xl + (long long)er * p.N + n : Xl, okx ? 16u : 0u);
+            if (!same_rows)
+              cp_async16(rb + C_RAW_Q + rr * C_RAWROW + 16 * fq,
+                         okq ? Ql + (long long)jr * p.N + n : Ql, okq ? 16u : 0u);
+          }
         }
         if (has_a && r < 4) {
           const long long n = n0 + 2 * r;
@@ -285,6 +333,9 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
 #pragma unroll
     for (int g = 0; g < C_RAW - 1; ++g) issue(g);
     for (int g = 0; g < nch; ++g) {
+      if (XTMA)
+        mbar_wait(smem_addr(&bar_raw[g % C_RAW]), (g / C_RAW) & 1, &abort_flag, p.err,
+                  kErrWaitFull);
       cp_async_wait<C_RAW - 2>();
       bar_sync(1, 128);  // chunk g visible to all; everyone done with chunk g-1
       issue(g + C_RAW - 1);
@@ -297,9 +348,12 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
         float2 x[4], q[4];
+        // chunks 2 half and 2 half + 1 of row r (swizzled when TMA filled)
+        const uint32_t o0 = XTMA ? swz64(r, 2 * half) : (uint32_t)(r * C_RAWROW + 32 * half);
+        const uint32_t o1 = XTMA ? swz64(r, 2 * half + 1) : o0 + 16;
         {
-          const float4 u0 = lds128(rb + C_RAW_X + r * C_RAWROW + 32 * half);
-          const float4 u1 = lds128(rb + C_RAW_X + r * C_RAWROW + 32 * half + 16);
+          const float4 u0 = lds128(rb + C_RAW_X + o0);
+          const float4 u1 = lds128(rb + C_RAW_X + o1);
           x[0] = make_float2(u0.x, u0.y); x[1] = make_float2(u0.z, u0.w);
           x[2] = make_float2(u1.x, u1.y); x[3] = make_float2(u1.z, u1.w);
         }
@@ -307,8 +361,8 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
 #pragma unroll
           for (int i = 0; i < 4; ++i) q[i] = x[i];
         } else {
-          const float4 u0 = lds128(rb + C_RAW_Q + r * C_RAWROW + 32 * half);
-          const float4 u1 = lds128(rb + C_RAW_Q + r * C_RAWROW + 32 * half + 16);
+          const float4 u0 = lds128(rb + C_RAW_Q + o0);
+          const float4 u1 = lds128(rb + C_RAW_Q + o1);
           q[0] = make_float2(u0.x, u0.y); q[1] = make_float2(u0.z, u0.w);
           q[2] = make_float2(u1.x, u1.y); q[3] = make_float2(u1.z, u1.w);
         }
@@ -334,6 +388,14 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_contract_kernel(ContractArgs 
       if (!(p.stall && g == 0)) mbar_arrive(smem_addr(&bar_full[cs]));
     }
     cp_async_wait<0>();
+    if (XTMA && r == 0 && abort_flag) {
+      // copies issued before a wait gave up may still land in this CTA's
+      // shared memory: wait (bounded) for the last one of every raw stage
+      for (int i = 0; i < C_RAW && i < nch; ++i) {
+        const int g = nch - 1 - ((nch - 1 - i) % C_RAW);
+        mbar_wait_drain(smem_addr(&bar_raw[g % C_RAW]), (g / C_RAW) & 1, p.err, kErrWaitDrain);
+      }
+    }
   } else {
     for (int g = 0; g < nch; ++g) {
       const int cs = g % C_CONV;
@@ -398,12 +460,16 @@ struct JhArgs {
 // FUSED: z_l[n] = s_l sum_e conj(X[e][n]) W[e][n] (J^H b); otherwise the
 // mix W_l[e][n] = s_l sum_j B[e][j] X'[j][n] itself is written (adjoint
 // sources conj(s_e) = k^2 dV sum_j p0_j conj(r_ej)).
-template <bool FUSED>
-__global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
+// XTMA: the raw tiles of the mixed operand (8 rows j x 128 pixels, one box)
+// arrive by TMA tensor copies issued by one producer thread and completing
+// on bar_raw; otherwise every producer copies its part with cp.async.
+template <bool FUSED, bool XTMA>
+__global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p,
+                                                             const __grid_constant__ CUtensorMap xmap) {
   using namespace tc;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar_full[M_CONV], bar_empty[M_CONV], bar_done[2],
-      bar_freed[2], bar_final;
+      bar_freed[2], bar_final, bar_raw[M_RAW];
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -422,8 +488,13 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
       mbar_init(smem_addr(&bar_freed[b]), 128);
     }
     mbar_init(smem_addr(&bar_final), 1);
+    if (XTMA)
+      for (int i = 0; i < M_RAW; ++i) mbar_init(smem_addr(&bar_raw[i]), 1);
     abort_flag = 0;
     mbar_init_fence();
+    if (XTMA)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap))
+                   : "memory");
   }
   if (warp == 0) tmem_alloc(smem_addr(&tmem_base), 512);
   fence_before_sync();
@@ -502,24 +573,37 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
         unit_of(g / p.nks, l, eb, pb);
         const int ks = g % p.nks;
         const uint32_t rb = raw0 + (uint32_t)((g % M_RAW) * M_RAW_BYTES);
-        const float2* Xl = p.X + (long long)l * p.NE * p.N;
+        if (XTMA) {
+          // rows j >= NE and pixels n >= N are outside the tensor: zero fill
+          if (r == 0) {
+            const uint32_t bar = smem_addr(&bar_raw[g % M_RAW]);
+            mbar_arrive_expect_tx(bar, M_RAW_BYTES);
+            tma_load_3d(rb, &xmap, 2 * pb * ROWS, ks * KS, l, bar);
+          }
+        } else {
+          const float2* Xl = p.X + (long long)l * p.NE * p.N;
 #pragma unroll
-        for (int k = 0; k < (KS * ROWS / 2) / 128; ++k) {
-          const int i = r + 128 * k;
-          const int jj = i / (ROWS / 2), pr = i % (ROWS / 2);
-          const int jrow = ks * KS + jj;
-          const long long n = (long long)pb * ROWS + 2 * pr;
-          const bool ok = (jrow < p.NE) && (n < p.N);
-          cp_async16(rb + (uint32_t)(jj * ROWS * 8 + 16 * pr),
-                     ok ? Xl + (long long)jrow * p.N + n : p.X, ok ? 16u : 0u);
+          for (int k = 0; k < (KS * ROWS / 2) / 128; ++k) {
+            const int i = r + 128 * k;
+            const int jj = i / (ROWS / 2), pr = i % (ROWS / 2);
+            const int jrow = ks * KS + jj;
+            const long long n = (long long)pb * ROWS + 2 * pr;
+            const bool ok = (jrow < p.NE) && (n < p.N);
+            cp_async16(rb + (uint32_t)(jj * ROWS * 8 + 16 * pr),
+                       ok ? Xl + (long long)jrow * p.N + n : p.X, ok ? 16u : 0u);
+          }
         }
       }
-      cp_async_commit();
+      if (!XTMA) cp_async_commit();
     };
 #pragma unroll
     for (int g = 0; g < M_RAW - 1; ++g) issue(g);
     for (int g = 0; g < nchunks; ++g) {
-      cp_async_wait<M_RAW - 2>();
+      if (XTMA)
+        mbar_wait(smem_addr(&bar_raw[g % M_RAW]), (g / M_RAW) & 1, &abort_flag, p.err,
+                  kErrWaitFull);
+      else
+        cp_async_wait<M_RAW - 2>();
       bar_sync(1, 128);
       issue(g + M_RAW - 1);
       const int kunit = g / p.nks, ks = g % p.nks;
@@ -552,7 +636,16 @@ __global__ void __launch_bounds__(C_THREADS, 1) tc_jh_kernel(JhArgs p) {
       fence_proxy_async();
       mbar_arrive(smem_addr(&bar_full[cs]));
     }
-    cp_async_wait<0>();
+    if (!XTMA) {
+      cp_async_wait<0>();
+    } else if (r == 0 && abort_flag) {
+      // copies issued before a wait gave up may still land in this CTA's
+      // shared memory: wait (bounded) for the last one of every raw stage
+      for (int i = 0; i < M_RAW && i < nchunks; ++i) {
+        const int g = nchunks - 1 - ((nchunks - 1 - i) % M_RAW);
+        mbar_wait_drain(smem_addr(&bar_raw[g % M_RAW]), (g / M_RAW) & 1, p.err, kErrWaitDrain);
+      }
+    }
   } else {
     for (int g = 0; g < nchunks; ++g) {
       const int cs = g % M_CONV, ks = g % p.nks, kunit = g / p.nks, b = kunit & 1;
@@ -622,23 +715,56 @@ int blocks_for(long long n, int threads, int cap) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// A field array [n_freq][NE][N] (complex FP32) as a 3-D tensor of floats
+// (innermost the 2 N floats of a row) with boxes of box_x floats x box_rows
+// rows of one frequency; swz64: 64-byte swizzle (box rows of 64 bytes).
+bool field_tensor_map(const fwi_ctx* c, const float2* base, int box_x, int box_rows,
+                      bool swz64, CUtensorMap* map) {
+  tc::TensorMapEncodeFn enc = tc::tensor_map_encoder();
+  if (!enc || ((uintptr_t)base & 15) || (c->N * 8) % 16) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * c->N, (cuuint64_t)c->n_elem,
+                              (cuuint64_t)c->n_freq};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->N * 8, (cuuint64_t)c->n_elem * c->N * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swz64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 std::once_flag g_attr_once;
 cudaError_t g_attr_err = cudaSuccess;
 
 cudaError_t set_attrs() {
   std::call_once(g_attr_once, [] {
-    g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<true>,
+    g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<true, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       CRaw<true>::SMEM);
     if (g_attr_err == cudaSuccess)
-      g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<false>,
+      g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<false, false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         CRaw<false>::SMEM);
     if (g_attr_err == cudaSuccess)
-      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<true>,
+      g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<true, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        CRawT<true>::SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_contract_kernel<false, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        CRawT<false>::SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<true, true>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
     if (g_attr_err == cudaSuccess)
-      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<false>,
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<false, true>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<true, false>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
+    if (g_attr_err == cudaSuccess)
+      g_attr_err = cudaFuncSetAttribute(tc_jh_kernel<false, false>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, M_SMEM);
   });
   return g_attr_err;
@@ -688,13 +814,27 @@ int tc_contract_partials(fwi_ctx* c, const float2* X, const float2* a, const flo
   c->tc_stall = 0;  // one launch
   dim3 grid(split, nbe * nbe, c->n_freq);
   const double fe = (double)c->n_freq * c->n_elem * c->N;
+  const bool shared_rows = X == Q && nbe == 1;
+  CUtensorMap xmap, qmap;
+  const bool xtma = c->jac_tma && field_tensor_map(c, X, 2 * KS, ROWS, true, &xmap) &&
+                    (shared_rows || field_tensor_map(c, Q, 2 * KS, ROWS, true, &qmap));
+  if (!xtma) std::memset(&xmap, 0, sizeof(xmap));
+  if (!xtma || shared_rows) std::memset(&qmap, 0, sizeof(qmap));
   {
     Prof pf(c, KC_CONTRACT, (2.0 * fe + (a ? c->N : 0)) * sizeof(float2),
             8.0 * fe * c->n_elem);
-    if (X == Q && nbe == 1)
-      tc_contract_kernel<true><<<grid, C_THREADS, CRaw<true>::SMEM, c->stream>>>(args);
+    if (shared_rows && xtma)
+      tc_contract_kernel<true, true><<<grid, C_THREADS, CRawT<true>::SMEM, c->stream>>>(
+          args, xmap, qmap);
+    else if (xtma)
+      tc_contract_kernel<false, true><<<grid, C_THREADS, CRawT<false>::SMEM, c->stream>>>(
+          args, xmap, qmap);
+    else if (shared_rows)
+      tc_contract_kernel<true, false><<<grid, C_THREADS, CRaw<true>::SMEM, c->stream>>>(
+          args, xmap, qmap);
     else
-      tc_contract_kernel<false><<<grid, C_THREADS, CRaw<false>::SMEM, c->stream>>>(args);
+      tc_contract_kernel<false, false><<<grid, C_THREADS, CRaw<false>::SMEM, c->stream>>>(
+          args, xmap, qmap);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -732,9 +872,17 @@ int tc_mix(fwi_ctx* c, const V* B, const float2* X, const float2* Xe, int conj_x
   const int grid = units < c->n_sm ? units : c->n_sm;
   JhArgs args{X, Xe, (const float*)c->tc_bops, c->red, out, c->tc_err, c->N,
               c->n_elem, c->n_freq, nbe, nks, npb, units, conj_x};
+  // the mixed operand [n_freq][NE][N] as a 3-D tensor of floats, box 8 rows
+  // (one k-step of j) x 128 pixels
+  CUtensorMap xmap;
+  const bool xtma = c->jac_tma && field_tensor_map(c, X, 2 * ROWS, KS, false, &xmap);
+  if (!xtma) std::memset(&xmap, 0, sizeof(xmap));
   {
     Prof pf(c, kclass, bytes, flops);
-    tc_jh_kernel<FUSED><<<grid, C_THREADS, M_SMEM, c->stream>>>(args);
+    if (xtma)
+      tc_jh_kernel<FUSED, true><<<grid, C_THREADS, M_SMEM, c->stream>>>(args, xmap);
+    else
+      tc_jh_kernel<FUSED, false><<<grid, C_THREADS, M_SMEM, c->stream>>>(args, xmap);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {

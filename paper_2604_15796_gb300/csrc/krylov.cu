@@ -272,7 +272,7 @@ Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int h
   r.plane = plane1; r.tw = (const cplx<T>*)c->tw_x;
   r.active = b.active; r.n_active = b.n_active; r.nb = nb;
   r.scal = b.scal; r.partial = b.partial;
-  r.nx = c->nx; r.rows = c->rows; r.N = c->N;
+  r.nx = c->nx; r.rows = c->rows; r.N = c->N; r.l2pf = c->row_l2pf;
   {
     const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_rf);
     r.ntiles = (c->rows + lpc - 1) / lpc;
@@ -282,7 +282,7 @@ Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int h
   q.X = X; q.R = R; q.RH = RH; q.P = P; q.V = V; q.Tt = Tt;
   q.tw = (const cplx<T>*)c->tw_x;
   q.active = b.active; q.n_active = b.n_active; q.nb = nb;
-  q.partial = b.partial; q.nx = c->nx; q.rows = c->rows; q.N = c->N;
+  q.partial = b.partial; q.nx = c->nx; q.rows = c->rows; q.N = c->N; q.l2pf = c->row_l2pf;
   {
     const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_ri);
     q.ntiles = (c->rows + lpc - 1) / lpc;
@@ -314,11 +314,12 @@ Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int h
   for (ColArgs<T>* a : {&b.cz, &b.cy_fwd, &b.cy_inv}) {
     a->active = b.active; a->n_active = b.n_active; a->nb = nb;
     a->rhs0 = rhs0; a->n_elem = c->n_elem; a->freq_fixed = -1;
-    a->tma = c->col_tma; a->err = c->tc_err;
+    a->tma = c->col_tma; a->gstage = c->col_gstage; a->err = c->tc_err;
   }
   b.cz.tw = (const cplx<T>*)c->tw_z;
   b.cz.ghat = (const cplx<T>*)c->ghat;
   b.cz.ghat_freq_stride = (long long)c->lz * lyx;
+  b.cz.n_freq = c->n_freq;
   return b;
 }
 

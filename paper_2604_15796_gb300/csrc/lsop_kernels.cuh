@@ -15,15 +15,22 @@
 // (grid-stride loop over (active RHS, tile) work items).
 #pragma once
 
-#include <cuda.h>  // CUtensorMap (the encoder is taken from the driver at run time)
 
+#include <algorithm>
 #include <atomic>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
 #include "tc.cuh"
 
 namespace fwi {
+
+// Resident CTAs per SM a kernel is compiled for (its register budget per
+// thread is then 65536 / (threads x blocks)).
+constexpr int blocks_for_regs(int threads, int regs) {
+  return (65536 / (threads * regs)) < 1 ? 1 : 65536 / (threads * regs);
+}
 
 // FP64 sum of NV (a power of two, <= 32) values over the 32 lanes of a
 // warp, reduce-scatter style: at each of the first log2(NV) levels a lane
@@ -105,22 +112,26 @@ __device__ __forceinline__ void line_sum(const A (&acc)[NV], int line, int t,
       for (int k = 0; k < NV; ++k) out[k] = red[2 * line][k] + red[2 * line + 1][k];
     __syncthreads();
   } else {
-    constexpr int P2 = (TL <= 32) ? 32 : 64;
+    // lines that are not whole warps (TL = 12, 20, 24, ...): thread k of
+    // each line adds value k of its TL threads in thread order, and thread 0
+    // collects the NV sums; two barriers instead of a log2(TL)-level tree.
+    // The caller's next barrier precedes any rewrite of these arrays.
+    static_assert(NV <= TL, "one summing thread per value");
     __shared__ double red[NTHREADS][NV];
+    __shared__ double sums[NTHREADS / TL + 1][NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) red[threadIdx.x][k] = d[k];
     __syncthreads();
-#pragma unroll
-    for (int s = P2 / 2; s >= 1; s >>= 1) {
-      if (t < s && t + s < TL)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[threadIdx.x][k] += red[threadIdx.x + s][k];
-      __syncthreads();
+    if (t < NV) {
+      const int base = threadIdx.x - t;
+      double acc = 0.0;
+      for (int i = 0; i < TL; ++i) acc += red[base + i][t];
+      sums[line][t] = acc;
     }
+    __syncthreads();
     if (t == 0)
 #pragma unroll
-      for (int k = 0; k < NV; ++k) out[k] = red[threadIdx.x][k];
-    __syncthreads();
+      for (int k = 0; k < NV; ++k) out[k] = sums[line][k];
   }
   (void)line;
 }
@@ -208,7 +219,7 @@ __device__ __forceinline__ bool slotB(int t, int i, int kp, int& k1, int& k2) {
 
 // HALF_IN: the line's samples n1 >= R1/2 are zero (zero-padded rows and
 // columns of the doubled lattice), so single-thread first DFTs skip them.
-template <class P, int GP, typename T, bool HALF_IN = false>
+template <class P, int GP, typename T, bool HALF_IN = false, bool TWS = false>
 __device__ __forceinline__ void ph_A(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                                      const cplx<T>* tw) {
   if constexpr (PlanTraits<P>::split) {
@@ -221,11 +232,11 @@ __device__ __forceinline__ void ph_A(int t, cplx<T>* v, cplx<T>* sm, int sj, int
     for (int kp = 0; kp < P::Q1; ++kp) {
       const int k1 = (P::S1 == 1) ? kp : kp + P::Q1 * s;
       cplx<T> z = v[kp];
-      if (k1 > 0 && n2 > 0) z = cmul(z, FWI_LDG(tw + n2 * k1));
+      if (k1 > 0 && n2 > 0) z = cmul(z, tw_at<TWS>(tw + n2 * k1));
       sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
     }
   } else {
-    phaseA_store<P, T, HALF_IN>(t, v, sm, sj, pad, tw);
+    phaseA_store<P, T, HALF_IN, TWS>(t, v, sm, sj, pad, tw);
   }
 }
 
@@ -246,7 +257,7 @@ __device__ __forceinline__ void ph_B(int t, cplx<T>* v, const cplx<T>* sm, int s
   }
 }
 
-template <class P, int GP, typename T>
+template <class P, int GP, typename T, bool TWS = false>
 __device__ __forceinline__ void ph_C(int t, cplx<T>* v, cplx<T>* sm, int sj, int pad,
                                      const cplx<T>* tw) {
   if constexpr (PlanTraits<P>::split) {
@@ -258,11 +269,11 @@ __device__ __forceinline__ void ph_C(int t, cplx<T>* v, cplx<T>* sm, int sj, int
     for (int m = 0; m < P::Q2; ++m) {
       const int n2 = (P::S2 == 1) ? m : 2 * m + s;
       cplx<T> z = v[m];
-      if (k1 > 0 && n2 > 0) z = cmulc(z, FWI_LDG(tw + n2 * k1));
+      if (k1 > 0 && n2 > 0) z = cmulc(z, tw_at<TWS>(tw + n2 * k1));
       sm[(n2 * (P::R1 + pad) + k1) * sj] = z;
     }
   } else {
-    phaseC_store<P, T>(t, v, sm, sj, pad, tw);
+    phaseC_store<P, T, TWS>(t, v, sm, sj, pad, tw);
   }
 }
 
@@ -356,11 +367,47 @@ __device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, 
   }
 }
 
+// Prefetch of `bytes` at p into L2 (no registers, no completion to wait
+// for; p 16-byte aligned, bytes a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The HBM rows a row pass's work item reads (its LPC lines of one
+// right-hand side: contiguous in every [rhs][row][x] array), prefetched
+// into L2 by one thread while the CTA transforms the previous item, so that
+// the item's loads wait on L2 rather than on HBM.  Row lengths nx and
+// starts row*nx are even, so every range is 16-byte aligned.
+template <class P, typename T, int LPC>
+__device__ __forceinline__ void rf_prefetch(const RowFwdArgs<T>& a, unsigned item,
+                                            unsigned ntiles) {
+  using V = cplx<T>;
+  const int slot = (int)(item / ntiles);
+  const int tile = (int)(item - (unsigned)slot * ntiles);
+  const int rhs = a.active ? a.active[slot] : slot;
+  const int row0 = tile * LPC;
+  const int nr = (a.rows - row0 < LPC) ? a.rows - row0 : LPC;
+  const long long off = (long long)rhs * a.N + (long long)row0 * a.nx;
+  const unsigned bytes = (unsigned)(nr * a.nx * (int)sizeof(V));
+  switch (a.mode) {
+    case RF_PLAIN:
+    case RF_INIT: l2_prefetch(a.in + off, bytes); break;
+    case RF_START: l2_prefetch(a.P + off, bytes); break;
+    case RF_S: l2_prefetch(a.R + off, bytes); l2_prefetch(a.V + off, bytes); break;
+    default: break;
+  }
+  if (a.use_m) l2_prefetch(a.m + (long long)row0 * a.nx, bytes);
+}
+
 // The forward row pass is latency-bound on its loads: the minimum-blocks
 // bound keeps it at <= 72 registers (no spills) so that more warps are
-// resident (10-14 % faster than the unconstrained 80-95 registers).
+// resident (10-14 % faster than the unconstrained 80-95 registers).  Lines
+// that do not tile a warp (TL = 20, 24: the 3-D x lines) hold more samples
+// per thread and get 88 (72 spilled 168 bytes per thread).
 template <class P, typename T, int LPC>
-__global__ void __launch_bounds__(LPC * P::TL, (LPC * P::TL <= 256) ? 896 / (LPC * P::TL) : 1)
+__global__ void __launch_bounds__(LPC * P::TL,
+                                  blocks_for_regs(LPC * P::TL,
+                                                  (32 % P::TL && P::TL % 32) ? 88 : 72))
 row_fwd_kernel(const RowFwdArgs<T> a) {
   using V = cplx<T>;
   constexpr int GP = row_gp<P>();
@@ -381,6 +428,10 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
     const int rhs = a.active ? a.active[slot] : slot;
     const int row = tile * LPC + line;
     const bool valid = row < a.rows;
+    // (not in the BiCGSTAB update mode: its six input streams already keep
+    // enough loads in flight, and the prefetch slowed it by 13 %)
+    if (a.l2pf && a.mode != RF_ITER && threadIdx.x == 0 && item + gridDim.x < items)
+      rf_prefetch<P, T, LPC>(a, item + gridDim.x, ntiles);
     V v[P::E];
     T acc = T(0);
     if (valid) {
@@ -542,6 +593,26 @@ __device__ __forceinline__ void ri_store(const RowInvArgs<T>& a, int t, int rhs,
 }
 
 template <class P, typename T, int LPC, int MODE>
+__device__ __forceinline__ void ri_prefetch_l2(const RowInvArgs<T>& a, unsigned item,
+                                               unsigned ntiles) {
+  using V = cplx<T>;
+  const int slot = (int)(item / ntiles);
+  const int tile = (int)(item - (unsigned)slot * ntiles);
+  const int rhs = a.active ? a.active[slot] : slot;
+  const int row0 = tile * LPC;
+  const int nr = (a.rows - row0 < LPC) ? a.rows - row0 : LPC;
+  l2_prefetch(a.plane + ((long long)rhs * a.rows + row0) * P::L,
+              (unsigned)(nr * P::L * (int)sizeof(V)));
+  const long long off = (long long)rhs * a.N + (long long)row0 * a.nx;
+  const unsigned bytes = (unsigned)(nr * a.nx * (int)sizeof(V));
+  if (MODE == RI_A || MODE == RI_AH) l2_prefetch(a.in + off, bytes);
+  if (MODE == RI_AH) l2_prefetch(a.m + (long long)row0 * a.nx, bytes);
+  if (MODE == RI_V) { l2_prefetch(a.P + off, bytes); l2_prefetch(a.RH + off, bytes); }
+  if (MODE == RI_T) { l2_prefetch(a.R + off, bytes); l2_prefetch(a.RH + off, bytes); }
+  if (MODE == RI_R0) { l2_prefetch(a.X + off, bytes); l2_prefetch(a.B + off, bytes); }
+}
+
+template <class P, typename T, int LPC, int MODE>
 __device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* sml, int line,
                                               int t) {
   using V = cplx<T>;
@@ -559,6 +630,8 @@ __device__ __forceinline__ void row_inv_items(const RowInvArgs<T>& a, cplx<T>* s
     const int rhs = a.active ? a.active[slot] : slot;
     const int row = tile * LPC + line;
     const bool valid = row < a.rows;
+    if (a.l2pf && threadIdx.x == 0 && item + gridDim.x < items)
+      ri_prefetch_l2<P, T, LPC, MODE>(a, item + gridDim.x, ntiles);
     V v[P::E];
     V q0[NS], q1[NS];
     if (valid) {
@@ -675,17 +748,34 @@ __device__ __forceinline__ ColItem col_item(unsigned item, unsigned nact, unsign
 // column, product with the kernel spectrum, inverse FFT, cropped store
 // (C_CONV); forward FFT and store of every frequency sample (C_FWD);
 // inverse FFT and cropped store (C_INV).  `out` points at the item's first
-// output sample of column j.
-template <class P, typename T, int TC>
-__device__ __forceinline__ void col_transform_store(const ColArgs<T>& a, int t, cplx<T>* smc,
+// output sample of column j.  TWS: the twiddle table `tw` is in shared
+// memory.  gs: the item's kernel-spectrum tile staged in shared memory,
+// offset to this thread's column (rows 0..L/2 of the TC columns, row
+// stride TC; row k > L/2 is row L - k: the spectrum of the lattice kernel,
+// even in each offset, is even in the frequency index), or NULL to read the
+// spectrum from global memory.  hook.wait_spectrum() is called before gs is
+// read (and returns false if the staging failed), hook.spectrum_done()
+// after the barrier that follows the product (every thread is then done
+// with gs).
+struct NoColHook {
+  __device__ bool wait_spectrum() const { return true; }
+  __device__ void spectrum_done() const {}
+};
+
+template <class P, typename T, int TC, bool TWS = false, class Hook = NoColHook>
+__device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, cplx<T>* smc,
                                                     cplx<T>* v, int rhs, int j,
-                                                    cplx<T>* __restrict__ out) {
+                                                    cplx<T>* __restrict__ out,
+                                                    const cplx<T>* tw,
+                                                    const cplx<T>* gs = nullptr,
+                                                    const Hook& hook = Hook()) {
   using V = cplx<T>;
   constexpr int GP = 32 / TC;
   const long long ls = a.line_stride;
+  bool ok = true;
   if (a.mode != C_INV) {
-    if (a.full) ph_A<P, GP, T, false>(t, v, smc, TC, 0, a.tw);
-    else ph_A<P, GP, T, true>(t, v, smc, TC, 0, a.tw);
+    if (a.full) ph_A<P, GP, T, false, TWS>(t, v, smc, TC, 0, tw);
+    else ph_A<P, GP, T, true, TWS>(t, v, smc, TC, 0, tw);
     __syncthreads();
     ph_B<P, GP, T>(t, v, smc, TC, 0);
     if (a.mode == C_FWD) {
@@ -698,24 +788,44 @@ __device__ __forceinline__ void col_transform_store(const ColArgs<T>& a, int t, 
             out[(long long)(k1 + P::R1 * k2) * ls] = v[i * PlanTraits<P>::MB + kp];
         }
       }
-      return;
+      return ok;
     }
-    const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs) / a.n_elem;
-    const V* __restrict__ g = a.ghat + (long long)l * a.ghat_freq_stride + j;
+    if (gs) {
+      ok = hook.wait_spectrum();
 #pragma unroll
-    for (int i = 0; i < PlanTraits<P>::CB; ++i) {
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll
-      for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
-        int k1, k2;
-        if (slotB<P, GP>(t, i, kp, k1, k2)) {
-          const int r = i * PlanTraits<P>::MB + kp;
-          v[r] = cmul(v[r], FWI_LDG(g + (long long)(k1 + P::R1 * k2) * a.ncols));
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2)) {
+            const int r = i * PlanTraits<P>::MB + kp;
+            const int k = k1 + P::R1 * k2;
+            const int kk = (k <= P::L / 2) ? k : P::L - k;
+            v[r] = cmul(v[r], gs[kk * TC]);
+          }
+        }
+      }
+    } else {
+      const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs) / a.n_elem;
+      const V* __restrict__ g = a.ghat + (long long)l * a.ghat_freq_stride + j;
+#pragma unroll
+      for (int i = 0; i < PlanTraits<P>::CB; ++i) {
+#pragma unroll
+        for (int kp = 0; kp < PlanTraits<P>::MB; ++kp) {
+          int k1, k2;
+          if (slotB<P, GP>(t, i, kp, k1, k2)) {
+            const int r = i * PlanTraits<P>::MB + kp;
+            const int k = k1 + P::R1 * k2;
+            const int kk = (k <= P::L / 2) ? k : P::L - k;  // same rows as the staged tile
+            v[r] = cmul(v[r], FWI_LDG(g + (long long)kk * a.ncols));
+          }
         }
       }
     }
     __syncthreads();
+    if (gs) hook.spectrum_done();
   }
-  ph_C<P, GP, T>(t, v, smc, TC, 0, a.tw);
+  ph_C<P, GP, T, TWS>(t, v, smc, TC, 0, tw);
   __syncthreads();
   ph_D<P, GP, T>(t, v, smc, TC, 0);
 #pragma unroll
@@ -727,14 +837,17 @@ __device__ __forceinline__ void col_transform_store(const ColArgs<T>& a, int t, 
         out[(long long)(P::R2 * n1 + n2) * ls] = v[i * PlanTraits<P>::MA + m];
     }
   }
+  return ok;
 }
 
-// Column pass over tiles of TC adjacent columns; thread (c, g) handles
-// column c of the tile as thread g of its line.  Shared-memory positions
-// are interleaved across the tile's columns (stride TC), which keeps the
-// exchange free of bank conflicts.
+// Column passes: 512-thread tiles at 64 registers (two CTAs per SM), the
+// smaller tiles at 80 (three 256-thread CTAs per SM: more warps to hide
+// the staging and kernel-spectrum loads; measured on the 160 x 160 x 128
+// volume, 1.94 -> 1.88 s per step against two CTAs at 128 registers).
+constexpr int col_regs(int threads) { return threads >= 512 ? 64 : 80; }
+
 template <class P, typename T, int TC>
-__global__ void __launch_bounds__(TC * P::TL, (TC * P::TL >= 256) ? 2 : 4)
+__global__ void __launch_bounds__(TC * P::TL, blocks_for_regs(TC * P::TL, col_regs(TC * P::TL)))
 col_kernel(const ColArgs<T> a) {
   using V = cplx<T>;
   constexpr int GP = 32 / TC;
@@ -782,7 +895,7 @@ col_kernel(const ColArgs<T> a) {
       }
     }
     __syncthreads();
-    col_transform_store<P, T, TC>(a, t, smc, v, rhs, j, out);
+    col_transform_store<P, T, TC>(a, t, smc, v, rhs, j, out, a.tw);
   }
 }
 
@@ -804,30 +917,36 @@ col_kernel(const ColArgs<T> a) {
 constexpr int kColErrWait = 5;
 constexpr int kColErrDrain = 6;
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
+// Shared-memory layout of col_tma_kernel (offsets in float2 from the
+// 128-byte aligned base): exchange L x TC | input staging rows_in x TC |
+// kernel-spectrum staging (L/2 + 1) x TC (convolution with gmap only) |
+// twiddle table L | two mbarriers and the abort flag.
+template <int L, int TC> struct ColTmaSmem {
+  static constexpr int G_ROWS = L / 2 + 1;
+  static constexpr size_t bytes(int rows_in, bool gstage) {
+    return ((size_t)L * TC + (size_t)rows_in * TC + (gstage ? (size_t)G_ROWS * TC : 0) +
+            (size_t)L) * sizeof(float2) + 32 + 128;
+  }
+};
 
-template <class P, int TC>
-__global__ void __launch_bounds__(TC * P::TL, (TC * P::TL >= 256) ? 2 : 4)
-col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map, int rows_in,
-               int nbox) {
+template <class P, int TC, bool GSTAGE>
+__global__ void __launch_bounds__(TC * P::TL, blocks_for_regs(TC * P::TL, col_regs(TC * P::TL)))
+col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
+               const __grid_constant__ CUtensorMap gmap, int rows_in, int nbox) {
   using V = float2;
   constexpr int GP = 32 / TC;
+  constexpr int G_ROWS = ColTmaSmem<P::L, TC>::G_ROWS;
   extern __shared__ __align__(16) unsigned char smraw[];
   // TMA destinations 128-byte aligned (the launch adds 128 bytes of slack)
   const uint32_t base_pad = (128u - (tc::smem_addr(smraw) & 127u)) & 127u;
   V* sm = reinterpret_cast<V*>(smraw + base_pad);            // exchange, L x TC
-  V* stg = sm + P::L * TC;                                   // staging, rows_in x TC
-  uint64_t* bar = reinterpret_cast<uint64_t*>(stg + rows_in * TC);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 1);
-  const uint32_t bar_a = tc::smem_addr(bar);
-  const uint32_t stg_a = tc::smem_addr(stg);
+  V* stg = sm + P::L * TC;                                   // input staging, rows_in x TC
+  V* gst = stg + rows_in * TC;                               // spectrum staging
+  V* tws = gst + (GSTAGE ? G_ROWS * TC : 0);                 // twiddles, L
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tws + P::L);   // [0] input, [1] spectrum
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 2);
+  const uint32_t bar_in = tc::smem_addr(bar), bar_g = tc::smem_addr(bar + 1);
+  const uint32_t stg_a = tc::smem_addr(stg), gst_a = tc::smem_addr(gst);
   const int c = threadIdx.x % TC;
   const int t = threadIdx.x / TC;
   V* smc = sm + c;
@@ -836,35 +955,63 @@ col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map, 
   const int nact = a.active ? *a.n_active : a.nb;
   const unsigned items = (unsigned)nact * per_rhs;  // < 2^31 (fwi_create caps the batch)
   const bool slot_fast = a.mode == C_CONV;
+  const bool use_g = GSTAGE && a.mode == C_CONV;
   const int box_rows = rows_in / nbox;
   const uint32_t tile_bytes = (uint32_t)(rows_in * TC * sizeof(V));
+  const uint32_t g_bytes = (uint32_t)(G_ROWS * TC * sizeof(V));
   int dummy_err = 0;
   int* err = a.err ? a.err : &dummy_err;
 
-  auto issue = [&](unsigned item) {
+  auto rhs_of = [&](const ColItem& it) { return a.active ? a.active[it.slot] : it.slot; };
+  auto issue_input = [&](unsigned item) {
     const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
-    const int rhs = a.active ? a.active[it.slot] : it.slot;
-    tc::mbar_arrive_expect_tx(bar_a, tile_bytes);
+    tc::mbar_arrive_expect_tx(bar_in, tile_bytes);
     for (int b = 0; b < nbox; ++b)
-      tma_load_3d(stg_a + (uint32_t)(b * box_rows * TC * sizeof(V)), &map, 2 * it.tile * TC,
-                  b * box_rows, rhs * a.nplanes + it.plane, bar_a);
+      tc::tma_load_3d(stg_a + (uint32_t)(b * box_rows * TC * sizeof(V)), &map, 2 * it.tile * TC,
+                  b * box_rows, rhs_of(it) * a.nplanes + it.plane, bar_in);
+  };
+  auto issue_spectrum = [&](unsigned item) {
+    const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
+    const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs_of(it)) / a.n_elem;
+    tc::mbar_arrive_expect_tx(bar_g, g_bytes);
+    tc::tma_load_3d(gst_a, &gmap, 2 * it.tile * TC, 0, l, bar_g);
   };
 
   if (threadIdx.x == 0) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map)) : "memory");
-    tc::mbar_init(bar_a, 1);
+    tc::mbar_init(bar_in, 1);
+    tc::mbar_init(bar_g, 1);
     *abort_flag = 0;
     tc::mbar_init_fence();
   }
+  for (int i = threadIdx.x; i < P::L; i += blockDim.x) tws[i] = a.tw[i];
   __syncthreads();
-  if (threadIdx.x == 0 && blockIdx.x < items) issue(blockIdx.x);
-  uint32_t parity = 0;
-  bool failed = false;
+  if (threadIdx.x == 0 && blockIdx.x < items) {
+    issue_input(blockIdx.x);
+    if (use_g) issue_spectrum(blockIdx.x);
+  }
+  uint32_t par_in = 0, par_g = 0;
+  bool failed = false, bad = false;
+  // the spectrum wait and the issue of the next item's spectrum, called
+  // from the transforms around their use of the staged tile
+  struct Hook {
+    uint32_t bar; uint32_t* par; volatile int* abort; int* err; bool* bad;
+    unsigned next, items; const decltype(issue_spectrum)* issue;
+    __device__ bool wait_spectrum() const {
+      const bool ok = tc::mbar_wait(bar, *par, abort, err, kColErrWait);
+      if (!ok) *bad = true;
+      return ok;
+    }
+    __device__ void spectrum_done() const {
+      *par ^= 1u;
+      if (threadIdx.x == 0 && next < items && !*abort) (*issue)(next);
+    }
+  };
   for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
     const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, slot_fast);
-    const int rhs = a.active ? a.active[it.slot] : it.slot;
+    const int rhs = rhs_of(it);
     const int j = it.tile * TC + c;
-    const bool ok = tc::mbar_wait(bar_a, parity, abort_flag, err, kColErrWait);
+    const bool ok = tc::mbar_wait(bar_in, par_in, abort_flag, err, kColErrWait);
     V v[P::E];
     if (a.mode == C_INV) {
 #pragma unroll
@@ -888,19 +1035,30 @@ col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map, 
         }
       }
     }
-    // every thread holds its samples (the staging buffer is free) and is
-    // done with the previous item's exchange
-    if (__syncthreads_or(!ok)) {
+    // every thread holds its samples (the input staging is free) and is
+    // done with the previous item's exchange; a failed wait (this item's
+    // input, or the previous item's spectrum) stops the CTA
+    if (__syncthreads_or(!ok || bad)) {
       failed = true;
       break;
     }
-    parity ^= 1u;
-    if (threadIdx.x == 0 && item + gridDim.x < items) issue(item + gridDim.x);
+    par_in ^= 1u;
+    const unsigned next = item + gridDim.x;
+    if (threadIdx.x == 0 && next < items) issue_input(next);
     V* __restrict__ out = a.out + rhs * a.out_rhs_stride + it.plane * a.out_plane_stride + j;
-    col_transform_store<P, float, TC>(a, t, smc, v, rhs, j, out);
+    if constexpr (GSTAGE) {
+      const Hook hook{bar_g, &par_g, abort_flag, err, &bad, next, items, &issue_spectrum};
+      col_transform_store<P, float, TC, true, Hook>(a, t, smc, v, rhs, j, out, tws,
+                                                    use_g ? gst + c : nullptr, hook);
+    } else {
+      col_transform_store<P, float, TC, true>(a, t, smc, v, rhs, j, out, tws);
+    }
   }
-  // a timed-out copy may still land in this CTA's shared memory
-  if (failed && threadIdx.x == 0) tc::mbar_wait_drain(bar_a, parity, err, kColErrDrain);
+  // copies of a CTA that stopped early may still land in its shared memory
+  if (failed && threadIdx.x == 0) {
+    tc::mbar_wait_drain(bar_in, par_in, err, kColErrDrain);
+    if (use_g) tc::mbar_wait_drain(bar_g, par_g, err, kColErrDrain);
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1012,25 +1170,24 @@ cudaError_t launch_row_inv(const RowInvArgs<T>& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// cuTensorMapEncodeTiled, taken from the driver through the runtime (the
-// library does not link libcuda); NULL if the driver does not offer it.
-typedef CUresult (*TensorMapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                      const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                      const cuuint32_t*, CUtensorMapInterleave,
-                                      CUtensorMapSwizzle, CUtensorMapL2promotion,
-                                      CUtensorMapFloatOOBfill);
-inline TensorMapEncodeFn tensor_map_encoder() {
-  static TensorMapEncodeFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = (TensorMapEncodeFn)f;
-  });
-  return fn;
+// Tensor map of the kernel spectrum for the convolution's staging: rows
+// 0..L/2 of TC columns of one frequency per box.  False when the box does
+// not fit (L/2 + 1 > 256 rows) or the staging would cost occupancy.
+template <int L, int TC>
+bool col_spectrum_map(const ColArgs<float>& a, int rows_in, CUtensorMap* map) {
+  if (!a.gstage || a.mode != C_CONV || !a.ghat || a.n_freq < 1) return false;
+  if (L / 2 + 1 > 256 || ColTmaSmem<L, TC>::bytes(rows_in, true) > 76 * 1024) return false;
+  tc::TensorMapEncodeFn enc = tc::tensor_map_encoder();
+  if (!enc || ((uintptr_t)a.ghat & 15) || (a.ncols * 8) % 16 || (a.ghat_freq_stride * 8) % 16)
+    return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)2 * a.ncols, (cuuint64_t)L, (cuuint64_t)a.n_freq};
+  const cuuint64_t strides[2] = {(cuuint64_t)a.ncols * 8, (cuuint64_t)a.ghat_freq_stride * 8};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * TC), (cuuint32_t)(L / 2 + 1), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(a.ghat), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
 }
 
 // Tensor map of a column pass's input (see col_tma_kernel).  False when the
@@ -1038,7 +1195,7 @@ inline TensorMapEncodeFn tensor_map_encoder() {
 template <int L, int TC>
 bool col_tensor_map(const ColArgs<float>& a, CUtensorMap* map, int* rows_in, int* nbox) {
   if (!a.tma || a.full) return false;
-  TensorMapEncodeFn enc = tensor_map_encoder();
+  tc::TensorMapEncodeFn enc = tc::tensor_map_encoder();
   if (!enc || a.nplanes < 1 || a.nb < 1 || a.ncols % TC) return false;
   const int rin = (a.mode == C_INV) ? L : L / 2;
   const int nb = (rin + 255) / 256;
@@ -1066,17 +1223,29 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
   using P = typename PlanFor<L>::type;
   constexpr int tc = col_tc_v<L, T, VAR>();
   if constexpr (sizeof(T) == 4) {
-    CUtensorMap map;
+    CUtensorMap map, gmap;
     int rows_in = 0, nbox = 0;
     if (col_tensor_map<L, tc>(a, &map, &rows_in, &nbox)) {
-      auto k = col_tma_kernel<P, tc>;
-      // exchange + staging + mbarrier and abort flag + alignment slack
-      const size_t smem = (size_t)(L + rows_in) * tc * sizeof(float2) + 16 + 128;
-      const size_t smem_max = (size_t)(2 * L) * tc * sizeof(float2) + 16 + 128;  // inverse
+      using SM = ColTmaSmem<L, tc>;
+      if constexpr (L / 2 + 1 <= 256) {
+        if (col_spectrum_map<L, tc>(a, rows_in, &gmap)) {
+          auto k = col_tma_kernel<P, tc, true>;
+          const size_t smem = SM::bytes(rows_in, true);
+          GridCache& gc = gcache<L, T, 5, VAR>();
+          cudaError_t e = grid_for(k, tc * P::TL, smem, gc);
+          if (e != cudaSuccess) return e;
+          k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
+          return cudaGetLastError();
+        }
+      }
+      std::memset(&gmap, 0, sizeof(gmap));
+      auto k = col_tma_kernel<P, tc, false>;
+      const size_t smem = SM::bytes(rows_in, false);
+      const size_t smem_max = SM::bytes(L, false);  // inverse mode: all L rows staged
       GridCache& gc = (a.mode == C_INV) ? gcache<L, T, 4, VAR>() : gcache<L, T, 3, VAR>();
       cudaError_t e = grid_for(k, tc * P::TL, smem, gc, smem_max);
       if (e != cudaSuccess) return e;
-      k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, rows_in, nbox);
+      k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
       return cudaGetLastError();
     }
   }

@@ -10,9 +10,11 @@
 // apart along M/N (SBO = 128) and 16 R bytes apart along K (LBO = 16 R).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (the encoder is taken from the driver at run time)
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 namespace fwi {
 namespace tc {
@@ -177,6 +179,39 @@ __device__ __forceinline__ void mbar_wait_drain(uint32_t bar, uint32_t parity, i
 }
 
 // ---- copies ----
+// cuTensorMapEncodeTiled, taken from the driver through the runtime (the
+// library does not link libcuda); NULL if the driver does not offer it.
+typedef CUresult (*TensorMapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                      const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                      const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+inline TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (TensorMapEncodeFn)f;
+  });
+  return fn;
+}
+
+// 3-D tiled TMA load of one box into shared memory, completing its bytes
+// on the mbarrier at `bar` (the caller arms it with expect_tx).
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+
 // 16-byte global -> shared copy; src_bytes 0 fills zeros.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),

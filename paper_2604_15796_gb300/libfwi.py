@@ -68,7 +68,8 @@ class fwi_tuning(Structure):
     _fields_ = [("row_fwd_variant", c_int), ("row_inv_variant", c_int), ("col_variant", c_int),
                 ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
                 ("jac_tensor_cores", c_int), ("overlap_halves", c_int),
-                ("debug_stall_once", c_int), ("col_tma", c_int)]
+                ("debug_stall_once", c_int), ("col_tma", c_int),
+                ("col_spectrum_stage", c_int), ("jac_tma", c_int), ("row_l2_prefetch", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -523,7 +524,9 @@ class Context:
         return {"row_fwd": t.row_fwd_variant, "row_inv": t.row_inv_variant,
                 "col": t.col_variant, "col_y": t.col_y_variant, "tuned": t.tuned,
                 "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)],
-                "jac_tensor_cores": t.jac_tensor_cores, "overlap_halves": t.overlap_halves}
+                "jac_tensor_cores": t.jac_tensor_cores, "overlap_halves": t.overlap_halves,
+                "col_tma": t.col_tma, "col_spectrum_stage": t.col_spectrum_stage,
+                "jac_tma": t.jac_tma, "row_l2_prefetch": t.row_l2_prefetch}
 
     def set_tuning(self, row_fwd=None, row_inv=None, col=None, col_y=None,
                    jac_tensor_cores=None, overlap_halves=None):
@@ -557,12 +560,36 @@ class Context:
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def set_col_tma(self, on):
-        """Stage the FP32 column passes' input tiles with TMA copies (True)
-        or read them with plain loads (False); results are bitwise the
-        same."""
+        """Stage the FP32 column passes' tiles in shared memory with TMA
+        copies (True) or read them with plain loads (False); results agree
+        to FP32 rounding."""
         t = fwi_tuning()
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.col_tma = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_col_spectrum_stage(self, on):
+        """With TMA staging, also stage the convolution's kernel-spectrum
+        tiles (True) or read the spectrum from global memory (False)."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.col_spectrum_stage = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_jac_tma(self, on):
+        """Tensor-core contractions take their raw operand tiles by TMA
+        (True) or by the producers' cp.async (False); same bits."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.jac_tma = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_row_l2_prefetch(self, on):
+        """Row passes prefetch their next work item's rows into L2 (True)
+        or not (False); results are bitwise the same."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.row_l2_prefetch = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def debug_stall_once(self):

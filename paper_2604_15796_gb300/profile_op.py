@@ -37,6 +37,10 @@ def main():
                     help="3-D grid of depth x grid x grid voxels (0.2 mm)")
     ap.add_argument("--no-col-tma", action="store_true",
                     help="column passes with plain loads instead of TMA staging")
+    ap.add_argument("--no-row-l2-prefetch", action="store_true",
+                    help="row passes without the L2 prefetch of their next work item")
+    ap.add_argument("--no-jac-tma", action="store_true",
+                    help="tensor-core contractions load their operand tiles with cp.async")
     args = ap.parse_args()
     nz = args.depth or args.grid
     shape = (nz, args.grid, args.grid) if args.dim3 else (nz, args.grid)
@@ -51,10 +55,14 @@ def main():
                              stream=stream)
         if args.no_col_tma:
             ctx.set_col_tma(False)
+        if args.no_row_l2_prefetch:
+            ctx.set_row_l2_prefetch(False)
         m = ctx.contrast_from_sos(torch.from_numpy(np.ascontiguousarray(w.sos)).cuda())
         if args.jac:
             if args.cuda_core_jacobian:
                 ctx.set_jac_tensor_cores(False)
+            if args.no_jac_tma:
+                ctx.set_jac_tma(False)
             ctx.forward(m)
             a = torch.from_numpy(phantoms.complex_normal(shape, 3)).cuda()
             y = ctx.jac_forward(a)
