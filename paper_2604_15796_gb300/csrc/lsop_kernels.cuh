@@ -753,10 +753,10 @@ __device__ __forceinline__ ColItem col_item(unsigned item, unsigned nact, unsign
 // offset to this thread's column (rows 0..L/2 of the TC columns, row
 // stride TC; row k > L/2 is row L - k: the spectrum of the lattice kernel,
 // even in each offset, is even in the frequency index), or NULL to read the
-// spectrum from global memory.  hook.wait_spectrum() is called before gs is
-// read (and returns false if the staging failed), hook.spectrum_done()
-// after the barrier that follows the product (every thread is then done
-// with gs).
+// spectrum from global memory.  hook.wait_spectrum() is called by thread 0
+// before the barrier that precedes the product (and returns false if the
+// staging failed), hook.spectrum_done() by every thread after the barrier
+// that follows it (every thread is then done with gs).
 struct NoColHook {
   __device__ bool wait_spectrum() const { return true; }
   __device__ void spectrum_done() const {}
@@ -776,6 +776,9 @@ __device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, 
   if (a.mode != C_INV) {
     if (a.full) ph_A<P, GP, T, false, TWS>(t, v, smc, TC, 0, tw);
     else ph_A<P, GP, T, true, TWS>(t, v, smc, TC, 0, tw);
+    // one thread waits for the staged spectrum; the barrier hands its
+    // completion (and the copied data) to the others
+    if (gs && a.mode == C_CONV && threadIdx.x == 0) ok = hook.wait_spectrum();
     __syncthreads();
     ph_B<P, GP, T>(t, v, smc, TC, 0);
     if (a.mode == C_FWD) {
@@ -791,7 +794,6 @@ __device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, 
       return ok;
     }
     if (gs) {
-      ok = hook.wait_spectrum();
 #pragma unroll
       for (int i = 0; i < PlanTraits<P>::CB; ++i) {
 #pragma unroll

@@ -5,6 +5,10 @@ kernel tuning and ncu captures.
     python -m paper_2604_15796_gb300.profile_op --grid 256 --rhs 256 --reps 3
     python -m paper_2604_15796_gb300.profile_op --jac --grid 256 --rhs 128 --nfreq 2
     python -m paper_2604_15796_gb300.profile_op --dim3 --grid 160 --depth 128 --rhs 32
+    python -m paper_2604_15796_gb300.profile_op --solve --dim3 --grid 160 --depth 128 --rhs 16
+
+Solve mode (--solve): ``reps`` forward solves of the ``rhs`` right-hand sides
+(every BiCGSTAB pass mode: INIT, ITER, S, V, T).
 
 Operator mode: a context with ``rhs`` array elements at one frequency (one
 operator application processes ``rhs`` right-hand sides) applies
@@ -31,6 +35,8 @@ def main():
     ap.add_argument("--freq", type=float, default=3e6)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--jac", action="store_true")
+    ap.add_argument("--solve", action="store_true",
+                    help="time forward solves (every BiCGSTAB pass mode) instead of A v")
     ap.add_argument("--nfreq", type=int, default=2)
     ap.add_argument("--cuda-core-jacobian", action="store_true")
     ap.add_argument("--dim3", action="store_true",
@@ -78,6 +84,19 @@ def main():
             ctx.set_profiling(False)
             ctx.close()
             report(shape, args.rhs * args.nfreq, ks)
+            return
+        if args.solve:
+            ctx.forward(m)  # warm-up
+            torch.cuda.synchronize()
+            ctx.reset_stats()
+            ctx.set_profiling(True)
+            for _ in range(args.reps):
+                ctx.forward(m)
+            torch.cuda.synchronize()
+            _, ks = ctx.stats()
+            ctx.set_profiling(False)
+            ctx.close()
+            report(shape, args.rhs, ks)
             return
         dt = torch.complex128 if args.fp64 else torch.complex64
         v = torch.from_numpy(phantoms.complex_normal((args.rhs,) + shape, 3)).to(
