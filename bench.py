@@ -283,6 +283,8 @@ def run_ours(args, rank, world, samples):
             ctx.set_col_spectrum_stage(False)
         if args.no_jac_tma:
             ctx.set_jac_tma(False)
+        if args.no_row_stage:
+            ctx.set_row_stage(False)
         tuning = ctx.tuning()
         c128 = torch.complex128
         sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
@@ -438,7 +440,8 @@ def run_ours(args, rank, world, samples):
                    "krylov_chains": 2 if tuning.get("overlap_halves") else 1,
                    "tuning": {k: tuning.get(k) for k in ("row_fwd", "row_inv", "col", "col_y",
                                                          "col_tma", "col_spectrum_stage",
-                                                         "jac_tma", "row_l2_prefetch")}},
+                                                         "jac_tma", "row_l2_prefetch",
+                                                         "row_stage")}},
         "gradient_evals_per_s": args.steps * world / (ms / 1e3),
         "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
                            "fwd_mean": float(its[:, 2].mean()),
@@ -844,6 +847,9 @@ def main():
                     help="the convolution reads the kernel spectrum from global memory")
     ap.add_argument("--no-jac-tma", action="store_true",
                     help="tensor-core contractions load their operand tiles with cp.async")
+    ap.add_argument("--no-row-stage", action="store_true",
+                    help="the forward row pass loads its rows from global memory instead "
+                         "of staging them in shared memory")
     ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--check-samples", type=int, default=2)

@@ -484,6 +484,13 @@ typedef struct fwi_tuning {
                            of their next work item into L2 while the
                            current item transforms; 0: no prefetch.
                            Results are bitwise the same. */
+  int row_stage;        /* 1 (default): the FP32 forward row pass copies the
+                           rows of its next work item (every array it
+                           reads) into shared memory with bulk copies while
+                           the current item transforms, and reads its
+                           samples there; 0: loads from global memory (with
+                           row_l2_prefetch).  Results agree to FP32
+                           rounding. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

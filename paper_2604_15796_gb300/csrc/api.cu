@@ -618,6 +618,7 @@ fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
   out->col_spectrum_stage = ctx->col_gstage;
   out->jac_tma = ctx->jac_tma;
   out->row_l2_prefetch = ctx->row_l2pf;
+  out->row_stage = ctx->row_stage;
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
   return FWI_OK;
@@ -647,10 +648,13 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
     return fail(ctx, FWI_ERR_INVALID_ARG, "col_spectrum_stage must be 0 or 1");
   if (in->jac_tma != 0 && in->jac_tma != 1)
     return fail(ctx, FWI_ERR_INVALID_ARG, "jac_tma must be 0 or 1");
+  if (in->row_stage != 0 && in->row_stage != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "row_stage must be 0 or 1");
   ctx->col_tma = in->col_tma;
   ctx->col_gstage = in->col_spectrum_stage;
   ctx->jac_tma = in->jac_tma;
   ctx->row_l2pf = in->row_l2_prefetch;
+  ctx->row_stage = in->row_stage;
   ctx->tc_stall = in->debug_stall_once;
   ctx->use_tc = in->jac_tensor_cores == 1;
   ctx->overlap = in->overlap_halves == 1;

@@ -54,6 +54,8 @@ template <typename T> struct RowFwdArgs {
   int ntiles;
   long long N;         // elements per RHS vector
   int l2pf;            // prefetch the next item's rows into L2
+  int stage;           // FP32, zero-padded rows: stage the rows with bulk copies
+  int* err;            // error word of bounded waits (or NULL)
 };
 
 template <typename T> struct RowInvArgs {

@@ -921,10 +921,13 @@ fwi_status tc_err_check(fwi_ctx* c) {
   const int code = *c->h_tc_err;
   *c->h_tc_err = 0;
   cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->stream);
-  // codes 1-4: tensor-core contractions; 5-6: TMA staging of the column passes
-  return fail(c, FWI_ERR_CUDA,
-              std::string(code <= 4 ? "tensor-core contraction" : "column pass TMA staging") +
-                  ": pipeline wait timed out (code " + std::to_string(code) + ")");
+  // codes 1-4: tensor-core contractions; 5-6: TMA staging of the column
+  // passes; 7-8: bulk-copy staging of the row passes
+  const char* where = code <= 4   ? "tensor-core contraction"
+                      : code <= 6 ? "column pass TMA staging"
+                                  : "row pass bulk-copy staging";
+  return fail(c, FWI_ERR_CUDA, std::string(where) + ": pipeline wait timed out (code " +
+                                   std::to_string(code) + ")");
 }
 
 }  // namespace fwi

@@ -273,6 +273,7 @@ Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int h
   r.active = b.active; r.n_active = b.n_active; r.nb = nb;
   r.scal = b.scal; r.partial = b.partial;
   r.nx = c->nx; r.rows = c->rows; r.N = c->N; r.l2pf = c->row_l2pf;
+  r.stage = c->row_stage; r.err = c->tc_err;
   {
     const int lpc = Lsop<T>::row_lines_per_cta(c->lx, c->var_rf);
     r.ntiles = (c->rows + lpc - 1) / lpc;

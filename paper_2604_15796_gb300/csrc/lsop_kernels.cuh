@@ -302,11 +302,27 @@ template <class P> constexpr int row_gp() { return 32; }
 // --------------------------------------------------------------------------
 // Row forward pass.  Phase-A slot (i, m) of thread t holds the sample
 // x = R2*n1 + n2 of the row in v[i*MA + m].
-template <class P, typename T, int MODE>
+//
+// Staging slot of each array the pass reads, per mode, when a work item's
+// rows are staged in shared memory (the contrast m after the mode's arrays).
+template <int MODE> struct RfSlots {
+  static constexpr int N = MODE == RF_ITER ? 5 : MODE == RF_S ? 2 : 1;
+  static constexpr int X = 0, P = MODE == RF_ITER ? 1 : 0;
+  static constexpr int R = MODE == RF_ITER ? 2 : 0, T = 3;
+  static constexpr int V = MODE == RF_ITER ? 4 : 1, IN = 0, M = N;
+};
+
+// Loads of one line's samples into phase-A slots, with the mode's update
+// written back to global memory.  STG: the samples come from the line's
+// rows staged in shared memory (sl = the line's first sample in staging
+// slot 0; slots LPC*L/2 samples apart); otherwise from the global arrays.
+template <class P, typename T, int MODE, bool STG = false, int LPC = 1>
 __device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, int row,
-                                        cplx<T>* v, T& acc) {
+                                        cplx<T>* v, T& acc, const cplx<T>* sl = nullptr) {
   using V = cplx<T>;
+  using S = RfSlots<MODE>;
   constexpr int GP = row_gp<P>();
+  constexpr int SS = LPC * (P::L / 2);  // staging slot stride
   const V* __restrict__ in = a.in;
   const V* __restrict__ mm = a.m;
   V* __restrict__ X = a.X;
@@ -330,12 +346,14 @@ __device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, 
       if (ok && n1 < nin1) {
         const int x = P::R2 * n1 + n2;
         const long long idx = vb + x;
+        // sample x of the array in staging slot k: staged, or in global memory
+        auto ld = [&](const V* g, int k) { return STG ? sl[k * SS + x] : g[idx]; };
         V u;
         if (MODE == RF_PLAIN) {
-          u = in[idx];
+          u = ld(in, S::IN);
           if (a.conj_in) u = cconj(u);
         } else if (MODE == RF_INIT) {
-          u = in[idx];
+          u = ld(in, S::IN);
           if (a.conj_in) u = cconj(u);
           X[idx] = mk<T>(T(0), T(0));
           R[idx] = u;
@@ -343,10 +361,11 @@ __device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, 
           Pp[idx] = u;
           acc += u.x * u.x + u.y * u.y;
         } else if (MODE == RF_START) {
-          u = Pp[idx];
+          u = ld(Pp, S::P);
         } else if (MODE == RF_ITER) {
           // x += alpha p + omega s ; r = s - omega t ; p = r + beta (p - omega v)
-          V xx = X[idx], p = Pp[idx], s = R[idx], tt = Tt[idx], vv = Vv[idx];
+          V xx = ld(X, S::X), p = ld(Pp, S::P), s = ld(R, S::R), tt = ld(Tt, S::T),
+            vv = ld(Vv, S::V);
           xx = cadd(xx, cadd(cmul(c.alpha, p), cmul(c.omega, s)));
           const V r = csub(s, cmul(c.omega, tt));
           p = cadd(r, cmul(c.beta, csub(p, cmul(c.omega, vv))));
@@ -355,11 +374,11 @@ __device__ __forceinline__ void rf_load(const RowFwdArgs<T>& a, int t, int rhs, 
           Pp[idx] = p;
           u = p;
         } else {  // RF_S: s = r - alpha v, stored over r
-          const V s = csub(R[idx], cmul(c.alpha, Vv[idx]));
+          const V s = csub(ld(R, S::R), cmul(c.alpha, ld(Vv, S::V)));
           R[idx] = s;
           u = s;
         }
-        if (a.use_m) u = cmul(mm[mb + x], u);
+        if (a.use_m) u = cmul(STG ? sl[S::M * SS + x] : mm[mb + x], u);
         w = u;
       }
       v[i * PlanTraits<P>::MA + m] = w;
@@ -399,12 +418,44 @@ __device__ __forceinline__ void rf_prefetch(const RowFwdArgs<T>& a, unsigned ite
   if (a.use_m) l2_prefetch(a.m + (long long)row0 * a.nx, bytes);
 }
 
+// ---- Rows staged in shared memory by bulk copies (FP32 forward pass) ----
+// A work item reads LPC consecutive lines of one right-hand side, which are
+// contiguous in every [rhs][row][x] array.  One thread copies the NEXT
+// item's rows of every array the pass reads into a staging area with
+// cp.async.bulk (one copy per array, completing on an mbarrier) as soon as
+// the current item's samples are in registers, so that the HBM reads of
+// item i+1 overlap the transforms of item i without holding registers; the
+// threads then read their samples from shared memory.  (Staging the
+// inverse pass's plane and operand rows the same way made that pass 9 %
+// slower in the 3-D solve: it is held at 4 CTAs per SM by its registers,
+// and it already issues its operand loads before the transforms.)
+constexpr int kRowErrWait = 7;
+constexpr int kRowErrDrain = 8;
+
+// Array in staging slot k of the forward row pass (the RfSlots order; the
+// contrast m after the mode's arrays), and the number of staged arrays.
+template <typename T>
+__device__ __forceinline__ const cplx<T>* rf_stage_src(const RowFwdArgs<T>& a, int k) {
+  switch (a.mode) {
+    case RF_PLAIN:
+    case RF_INIT: return k == 0 ? a.in : a.m;
+    case RF_START: return k == 0 ? a.P : a.m;
+    case RF_ITER:
+      return k == 0 ? a.X : k == 1 ? a.P : k == 2 ? a.R : k == 3 ? a.Tt : k == 4 ? a.V : a.m;
+    default: return k == 0 ? a.R : k == 1 ? a.V : a.m;
+  }
+}
+__host__ __device__ inline int rf_stage_count(int mode, int use_m) {
+  const int n = mode == RF_ITER ? 5 : mode == RF_S ? 2 : 1;
+  return n + (use_m ? 1 : 0);
+}
+
 // The forward row pass is latency-bound on its loads: the minimum-blocks
 // bound keeps it at <= 72 registers (no spills) so that more warps are
 // resident (10-14 % faster than the unconstrained 80-95 registers).  Lines
 // that do not tile a warp (TL = 20, 24: the 3-D x lines) hold more samples
 // per thread and get 88 (72 spilled 168 bytes per thread).
-template <class P, typename T, int LPC>
+template <class P, typename T, int LPC, bool STG = false>
 __global__ void __launch_bounds__(LPC * P::TL,
                                   blocks_for_regs(LPC * P::TL,
                                                   (32 % P::TL && P::TL % 32) ? 88 : 72))
@@ -414,6 +465,7 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   constexpr int LSTR = P::span(1) + 1;
+  constexpr int NXH = P::L / 2;  // samples per staged line (the half lattice)
   const int line = threadIdx.x / P::TL;
   const int t = threadIdx.x - line * P::TL;
   V* sml = sm + line * LSTR;
@@ -422,6 +474,52 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
   // count fits (fwi_create)
   const unsigned ntiles = (unsigned)a.ntiles;
   const unsigned items = (unsigned)nact * ntiles;
+  // staging (STG): after the exchange, 128-byte aligned; then the mbarrier
+  // and the abort flag
+  V* stg = nullptr;
+  uint64_t* bar = nullptr;
+  volatile int* abort_flag = nullptr;
+  int nsrc = 0;
+  uint32_t parity = 0;
+  bool failed = false;
+  int dummy_err = 0;
+  int* err = nullptr;
+  if constexpr (STG) {
+    const uint32_t base = tc::smem_addr(smraw);
+    const uint32_t ex_end = base + (uint32_t)(LPC * LSTR * sizeof(V));
+    const uint32_t st0 = (ex_end + 127u) & ~127u;
+    stg = reinterpret_cast<V*>(smraw + (st0 - base));
+    nsrc = rf_stage_count(a.mode, a.use_m);
+    bar = reinterpret_cast<uint64_t*>(stg + nsrc * LPC * NXH);
+    abort_flag = reinterpret_cast<volatile int*>(bar + 1);
+    err = a.err ? a.err : &dummy_err;
+    if (threadIdx.x == 0) {
+      tc::mbar_init(tc::smem_addr(bar), 1);
+      *abort_flag = 0;
+      tc::mbar_init_fence();
+    }
+    __syncthreads();
+  }
+  // bulk copies of an item's rows of every staged array (thread 0)
+  auto issue = [&](unsigned it) {
+    const int sl = (int)(it / ntiles);
+    const int tl = (int)(it - (unsigned)sl * ntiles);
+    const int rh = a.active ? a.active[sl] : sl;
+    const int row0 = tl * LPC;
+    const int nr = (a.rows - row0 < LPC) ? a.rows - row0 : LPC;
+    const uint32_t bytes = (uint32_t)(nr * NXH * (int)sizeof(V));
+    const uint32_t b = tc::smem_addr(bar);
+    tc::mbar_arrive_expect_tx(b, bytes * (uint32_t)nsrc);
+    for (int k = 0; k < nsrc; ++k) {
+      const bool is_m = a.use_m && k == nsrc - 1;  // m: one row set for every RHS
+      const long long off = is_m ? (long long)row0 * NXH
+                                 : (long long)rh * a.N + (long long)row0 * NXH;
+      tc::bulk_g2s(tc::smem_addr(stg + k * LPC * NXH), rf_stage_src(a, k) + off, bytes, b);
+    }
+  };
+  if constexpr (STG) {
+    if (threadIdx.x == 0 && blockIdx.x < items) issue(blockIdx.x);
+  }
   for (unsigned item = blockIdx.x; item < items; item += gridDim.x) {
     const int slot = (int)(item / ntiles);
     const int tile = (int)(item - (unsigned)slot * ntiles);
@@ -430,20 +528,34 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
     const bool valid = row < a.rows;
     // (not in the BiCGSTAB update mode: its six input streams already keep
     // enough loads in flight, and the prefetch slowed it by 13 %)
-    if (a.l2pf && a.mode != RF_ITER && threadIdx.x == 0 && item + gridDim.x < items)
+    if (!STG && a.l2pf && a.mode != RF_ITER && threadIdx.x == 0 && item + gridDim.x < items)
       rf_prefetch<P, T, LPC>(a, item + gridDim.x, ntiles);
     V v[P::E];
     T acc = T(0);
+    bool ok = true;
+    if constexpr (STG) ok = tc::mbar_wait(tc::smem_addr(bar), parity, abort_flag, err, kRowErrWait);
     if (valid) {
+      const V* sl = STG ? stg + line * NXH : nullptr;  // the line in staging slot 0
       switch (a.mode) {
-        case RF_PLAIN: rf_load<P, T, RF_PLAIN>(a, t, rhs, row, v, acc); break;
-        case RF_INIT: rf_load<P, T, RF_INIT>(a, t, rhs, row, v, acc); break;
-        case RF_START: rf_load<P, T, RF_START>(a, t, rhs, row, v, acc); break;
-        case RF_ITER: rf_load<P, T, RF_ITER>(a, t, rhs, row, v, acc); break;
-        default: rf_load<P, T, RF_S>(a, t, rhs, row, v, acc); break;
+        case RF_PLAIN: rf_load<P, T, RF_PLAIN, STG, LPC>(a, t, rhs, row, v, acc, sl); break;
+        case RF_INIT: rf_load<P, T, RF_INIT, STG, LPC>(a, t, rhs, row, v, acc, sl); break;
+        case RF_START: rf_load<P, T, RF_START, STG, LPC>(a, t, rhs, row, v, acc, sl); break;
+        case RF_ITER: rf_load<P, T, RF_ITER, STG, LPC>(a, t, rhs, row, v, acc, sl); break;
+        default: rf_load<P, T, RF_S, STG, LPC>(a, t, rhs, row, v, acc, sl); break;
       }
     }
-    __syncthreads();  // shared memory of the previous item fully consumed
+    // shared memory of the previous item fully consumed (and, staged, this
+    // item's rows are in registers: the staging area is free)
+    if constexpr (STG) {
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        break;
+      }
+      parity ^= 1u;
+      if (threadIdx.x == 0 && item + gridDim.x < items) issue(item + gridDim.x);
+    } else {
+      __syncthreads();
+    }
     // (the half-input DFT measured slower in this pass than the full one)
     if (valid) ph_A<P, GP, T, false>(t, v, sml, 1, 1, a.tw);
     __syncthreads();
@@ -467,6 +579,10 @@ row_fwd_kernel(const RowFwdArgs<T> a) {
       if (t == 0 && valid)
         a.partial[((long long)rhs * NSLOT + 0) * a.rows + row] = make_double2(tot[0], 0.0);
     }
+  }
+  // copies of a CTA that stopped early may still land in its shared memory
+  if constexpr (STG) {
+    if (failed && threadIdx.x == 0) tc::mbar_wait_drain(tc::smem_addr(bar), parity, err, kRowErrDrain);
   }
 }
 
@@ -1148,10 +1264,50 @@ inline cudaError_t grid_for(K kernel, int threads, size_t smem, GridCache& gc,
   return cudaSuccess;
 }
 
+// Bulk copies start on 16-byte boundaries: every array the staged pass
+// copies from must be 16-byte aligned (row starts row*nx and right-hand-side
+// starts rhs*N are, since nx is even); otherwise the plain pass runs, as it
+// does when the rows are not the half lattice (nx = L/2) the staging holds.
+inline bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+template <typename T> bool rf_stage_aligned(const RowFwdArgs<T>& a) {
+  const bool ok = (a.N * (long long)sizeof(cplx<T>)) % 16 == 0 && (!a.use_m || al16(a.m));
+  switch (a.mode) {
+    case RF_PLAIN: case RF_INIT: return ok && al16(a.in);
+    case RF_START: return ok && al16(a.P);
+    case RF_ITER: return ok && al16(a.X) && al16(a.P) && al16(a.R) && al16(a.Tt) && al16(a.V);
+    default: return ok && al16(a.R) && al16(a.V);
+  }
+}
+
+// Dynamic shared memory of the staged forward row pass: exchange, 128-byte
+// alignment slack, nsrc staged arrays of lpc lines of L/2 samples, mbarrier
+// and abort flag.
+template <int L, typename T, int VAR> constexpr size_t row_fwd_stage_smem(int nsrc) {
+  return row_smem_v<L, T, VAR>() + 128 +
+         (size_t)nsrc * row_lpc_v<L, VAR>() * (L / 2) * sizeof(cplx<T>) + 16;
+}
+
 template <int L, typename T, int VAR>
 cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s) {
   using P = typename PlanFor<L>::type;
   constexpr int lpc = row_lpc_v<L, VAR>();
+  if constexpr (sizeof(T) == 4) {
+    if (a.stage && !a.full && 2 * a.nx == L && rf_stage_aligned(a)) {
+      auto k = row_fwd_kernel<P, T, lpc, true>;
+      const int nsrc = rf_stage_count(a.mode, a.use_m);
+      const size_t smem = row_fwd_stage_smem<L, T, VAR>(nsrc);
+      // one occupancy per staged-array count (the modes differ in smem)
+      GridCache& gc = nsrc <= 1 ? gcache<L, T, 11, VAR>()
+                    : nsrc == 2 ? gcache<L, T, 12, VAR>()
+                    : nsrc == 3 ? gcache<L, T, 13, VAR>()
+                    : nsrc == 5 ? gcache<L, T, 15, VAR>()
+                                : gcache<L, T, 16, VAR>();
+      cudaError_t e = grid_for(k, lpc * P::TL, smem, gc, row_fwd_stage_smem<L, T, VAR>(6));
+      if (e != cudaSuccess) return e;
+      k<<<gc.blocks.load(), lpc * P::TL, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
   auto k = row_fwd_kernel<P, T, lpc>;
   GridCache& gc = gcache<L, T, 0, VAR>();
   cudaError_t e = grid_for(k, lpc * P::TL, row_smem_v<L, T, VAR>(), gc);

@@ -69,7 +69,8 @@ class fwi_tuning(Structure):
                 ("col_y_variant", c_int), ("tuned", c_int), ("ms", (c_float * 4) * 4),
                 ("jac_tensor_cores", c_int), ("overlap_halves", c_int),
                 ("debug_stall_once", c_int), ("col_tma", c_int),
-                ("col_spectrum_stage", c_int), ("jac_tma", c_int), ("row_l2_prefetch", c_int)]
+                ("col_spectrum_stage", c_int), ("jac_tma", c_int), ("row_l2_prefetch", c_int),
+                ("row_stage", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -526,7 +527,8 @@ class Context:
                 "ms": [[t.ms[k][v] for v in range(4)] for k in range(4)],
                 "jac_tensor_cores": t.jac_tensor_cores, "overlap_halves": t.overlap_halves,
                 "col_tma": t.col_tma, "col_spectrum_stage": t.col_spectrum_stage,
-                "jac_tma": t.jac_tma, "row_l2_prefetch": t.row_l2_prefetch}
+                "jac_tma": t.jac_tma, "row_l2_prefetch": t.row_l2_prefetch,
+                "row_stage": t.row_stage}
 
     def set_tuning(self, row_fwd=None, row_inv=None, col=None, col_y=None,
                    jac_tensor_cores=None, overlap_halves=None):
@@ -590,6 +592,15 @@ class Context:
         t = fwi_tuning()
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.row_l2_prefetch = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_row_stage(self, on):
+        """The FP32 forward row pass stages its rows in shared memory with
+        bulk copies (True) or loads them from global memory (False); results
+        agree to FP32 rounding."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.row_stage = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def debug_stall_once(self):

@@ -47,6 +47,9 @@ def main():
                     help="row passes without the L2 prefetch of their next work item")
     ap.add_argument("--no-jac-tma", action="store_true",
                     help="tensor-core contractions load their operand tiles with cp.async")
+    ap.add_argument("--no-row-stage", action="store_true",
+                    help="the forward row pass loads its rows from global memory instead "
+                         "of staging them in shared memory")
     args = ap.parse_args()
     nz = args.depth or args.grid
     shape = (nz, args.grid, args.grid) if args.dim3 else (nz, args.grid)
@@ -63,6 +66,8 @@ def main():
             ctx.set_col_tma(False)
         if args.no_row_l2_prefetch:
             ctx.set_row_l2_prefetch(False)
+        if args.no_row_stage:
+            ctx.set_row_stage(False)
         m = ctx.contrast_from_sos(torch.from_numpy(np.ascontiguousarray(w.sos)).cuda())
         if args.jac:
             if args.cuda_core_jacobian:
@@ -119,7 +124,7 @@ def report(shape, rhs, ks):
     for name, k in ks.items():
         if k["launches"]:
             ms = k["ms"] / k["launches"]
-            out[name] = {"ms_per_launch": ms,
+            out[name] = {"ms_per_launch": ms, "bytes_per_launch": k["bytes"] / k["launches"],
                          "gbs": k["bytes"] / k["launches"] / (ms * 1e6) if k["bytes"] else None,
                          "tflops": k["flops"] / k["launches"] / (ms * 1e9) if k["flops"] else None}
     print(json.dumps({"grid": list(shape), "rhs": rhs, "passes": out}))

@@ -114,3 +114,40 @@ def test_tma_staged_column_passes_match_plain_loads(lib, shape):
     vin = to_np(v_gpu).astype(np.complex128)
     ref = operator.apply_A(vin, contrast(w), prob, 0)
     assert rel_l2(out[True], ref) < 1e-5
+
+
+@pytest.mark.parametrize("shape", [(32, 96), (96, 32), (8, 512), (16, 8, 8), (8, 16, 160),
+                                   (8, 8, 160)])
+def test_staged_row_passes_match_plain_loads(lib, shape):
+    """The FP32 forward row pass gives the same result, to FP32 rounding,
+    whether each work item's rows are staged in shared memory by bulk copies
+    or read with plain loads: single applications of K, A and A^H, and a
+    whole forward solve (every BiCGSTAB update mode of the fused row pass),
+    with ragged row tiles; both match the oracle."""
+    import torch
+    w = small_workload(shape, n_elem=3, freqs=(2.0e6,))
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6)
+    m = contrast(w)
+    m_gpu = to_gpu(m, torch.complex128)
+    v = phantoms.complex_normal((3,) + tuple(shape), 23)
+    v_gpu = to_gpu(v, torch.complex64)
+    out = {}
+    for stage in (True, False):
+        ctx.set_row_stage(stage)
+        assert ctx.tuning()["row_stage"] == int(stage)
+        ops = [to_np(ctx.apply(k, v_gpu, 0, None if k == "K" else m_gpu))
+               for k in ("K", "A", "AH")]
+        f = ctx.empty_fields()
+        ctx.forward(m_gpu, fields=f)
+        out[stage] = (ops, to_np(f))
+    ctx.close()
+    for a, b in zip(out[True][0], out[False][0]):
+        assert rel_l2(a, b) < 3e-7, rel_l2(a, b)
+    # the solve stops at tol = 1e-6: rounding differences stay below it
+    assert rel_l2(out[True][1], out[False][1]) < 1e-5
+    prob = oracle_problem(w)
+    vin = v.astype(np.complex64).astype(np.complex128)
+    assert rel_l2(out[True][0][1], operator.apply_A(vin, m, prob, 0)) < 1e-5
+    assert rel_l2(out[True][0][2], inverse.apply_AH(vin, m, prob, 0)) < 1e-5
+    ref_f = operator.solve_forward(m, prob, "bicgstab", tol=1e-10)
+    assert rel_l2(out[True][1], ref_f) < 1e-4
