@@ -273,8 +273,8 @@ def run_ours(args, rank, world, samples):
                              max_batch=args.max_batch)
         if args.cuda_core_jacobian:
             ctx.set_jac_tensor_cores(False)
-        if args.one_chain:
-            ctx.set_overlap(False)
+        if args.chains is not None:
+            ctx.set_overlap(args.chains == 2)
         if args.no_col_tma:
             ctx.set_col_tma(False)
         if args.no_row_l2_prefetch:
@@ -835,8 +835,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-comparator", action="store_true")
-    ap.add_argument("--one-chain", action="store_true",
-                    help="iterate each batch as one chain (no two-stream overlap)")
+    ap.add_argument("--chains", type=int, choices=[1, 2], default=None,
+                    help="iterate each batch as one chain or as two halves on two streams "
+                         "(default: two on 2-D lattices, one on 3-D)")
     ap.add_argument("--cuda-core-jacobian", action="store_true",
                     help="run the pixel contractions on CUDA cores instead of tensor cores")
     ap.add_argument("--no-col-tma", action="store_true",

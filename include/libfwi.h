@@ -448,12 +448,13 @@ typedef struct fwi_tuning {
                            (tcgen05, 3xTF32 products, FP32 accumulation);
                            0: CUDA-core FP32 kernels.  FP64 contexts and odd
                            pixel counts always use the CUDA-core kernels. */
-  int overlap_halves;   /* 1 (default): batches of >= 32 right-hand sides
-                           iterate as two independent halves on two streams
-                           of one CUDA graph, so that the passes of one half
-                           fill the SMs the other half's passes leave idle;
-                           results are bitwise the same as with 0 (one
-                           chain). */
+  int overlap_halves;   /* 1 (default on 2-D lattices): batches of >= 32
+                           right-hand sides iterate as two independent
+                           halves on two streams of one CUDA graph, so that
+                           the passes of one half fill the SMs the other
+                           half's passes leave idle; 0 (default on 3-D
+                           lattices, whose passes already fill the GPU):
+                           one chain.  Results are bitwise the same. */
   int debug_stall_once; /* test of the failure path: 1 makes the next
                            tensor-core contraction withhold its first
                            pipeline stage, so that its bounded waits give up

@@ -42,7 +42,7 @@ struct fwi_ctx {
   cudaStream_t own_stream = nullptr;  // created when the caller passes NULL
   cudaStream_t stream2 = nullptr;     // second chain of the Krylov iteration graph
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  bool overlap = true;                // iterate large batches as two chains
+  bool overlap = true;                // iterate large batches as two chains (2-D default)
   int device = 0, n_sm = 0;
   // workspace (field precision unless noted)
   void* ghat = nullptr;             // [n_freq][lz][ly][lx], scaled k^2/(lx ly lz)

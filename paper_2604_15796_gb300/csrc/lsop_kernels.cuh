@@ -836,23 +836,38 @@ row_inv_kernel(const RowInvArgs<T> a) {
 
 // --------------------------------------------------------------------------
 // Work item of a column pass -> (RHS slot, plane, column tile).  The
-// convolution orders the items slot-fastest: the CTAs then sweep all
-// right-hand sides of a column tile together, so each tile of the kernel
-// spectrum is read from HBM once per frequency and served from L2 for the
-// other right-hand sides (in 3-D one frequency's spectrum, lz*ly*lx*8 bytes,
-// exceeds L2).  The other passes go right-hand side by right-hand side.
+// convolution sweeps all right-hand sides of a group of kConvTileGroup
+// adjacent column tiles together (tile fastest within the group, then the
+// slot), so that each tile of the kernel spectrum is read from HBM once per
+// frequency and served from L2 for the other right-hand sides (in 3-D one
+// frequency's spectrum, lz*ly*lx*8 bytes, exceeds L2), while each right-
+// hand side's rows are read as kConvTileGroup * 128-byte runs rather than
+// single 128-byte segments of as many different volumes as there are CTAs.
+// The other passes go right-hand side by right-hand side.
+constexpr int kConvTileGroup = 8;
 struct ColItem { int slot, plane, tile; };
 __device__ __forceinline__ ColItem col_item(unsigned item, unsigned nact, unsigned per_rhs,
                                             unsigned ntile, int nplanes, bool slot_fast) {
   ColItem it;
   unsigned rem;
   if (slot_fast) {
-    rem = item / nact;
-    it.slot = (int)(item - rem * nact);
-  } else {
-    it.slot = (int)(item / per_rhs);
-    rem = item - (unsigned)it.slot * per_rhs;
+    // plane, then tile group, then slot, then tile; the last group of a
+    // plane may be short
+    const unsigned per_plane = nact * ntile;
+    const unsigned pl = (nplanes == 1) ? 0u : item / per_plane;
+    const unsigned ri = item - pl * per_plane;
+    const unsigned gsz = nact * (unsigned)kConvTileGroup;
+    const unsigned g0 = ri / gsz * (unsigned)kConvTileGroup;  // first tile of the group
+    const unsigned r = ri - g0 * nact;
+    const unsigned k = (ntile - g0 < (unsigned)kConvTileGroup) ? ntile - g0
+                                                               : (unsigned)kConvTileGroup;
+    it.slot = (int)(r / k);
+    it.plane = (int)pl;
+    it.tile = (int)(g0 + (r - (unsigned)it.slot * k));
+    return it;
   }
+  it.slot = (int)(item / per_rhs);
+  rem = item - (unsigned)it.slot * per_rhs;
   it.plane = (nplanes == 1) ? 0 : (int)(rem / ntile);
   it.tile = (int)(rem - (unsigned)it.plane * ntile);
   return it;
