@@ -66,8 +66,8 @@ def describe(w):
 
 # the sources each kernel class is compiled from: the FFT operator passes
 # (row_*, col_*) and the pixel contractions (everything else)
-KERNEL_SOURCES = {"operator": ("fft_core.cuh", "lsop_kernels.cuh", "common.cuh", "lsop_f32.cu",
-                               "tc.cuh"),
+KERNEL_SOURCES = {"operator": ("fft_core.cuh", "lsop_kernels.cuh", "col_pair.cuh", "common.cuh",
+                               "lsop_f32.cu", "tc.cuh"),
                   "contraction": ("common.cuh", "jac.cu", "jac_tc.cu", "tc.cuh")}
 
 
@@ -285,6 +285,8 @@ def run_ours(args, rank, world, samples):
             ctx.set_jac_tma(False)
         if args.no_row_stage:
             ctx.set_row_stage(False)
+        if args.no_col_pairs:
+            ctx.set_col_pairs(False)
         tuning = ctx.tuning()
         c128 = torch.complex128
         sos_true = torch.from_numpy(np.ascontiguousarray(w.sos)).cuda()
@@ -441,7 +443,7 @@ def run_ours(args, rank, world, samples):
                    "tuning": {k: tuning.get(k) for k in ("row_fwd", "row_inv", "col", "col_y",
                                                          "col_tma", "col_spectrum_stage",
                                                          "jac_tma", "row_l2_prefetch",
-                                                         "row_stage")}},
+                                                         "row_stage", "col_pairs")}},
         "gradient_evals_per_s": args.steps * world / (ms / 1e3),
         "bicgstab_iters": {"fwd_max": int(its[:, 0].max()), "adj_max": int(its[:, 1].max()),
                            "fwd_mean": float(its[:, 2].mean()),
@@ -848,6 +850,8 @@ def main():
                     help="the convolution reads the kernel spectrum from global memory")
     ap.add_argument("--no-jac-tma", action="store_true",
                     help="tensor-core contractions load their operand tiles with cp.async")
+    ap.add_argument("--no-col-pairs", action="store_true",
+                    help="the convolution computes one column per thread instead of two")
     ap.add_argument("--no-row-stage", action="store_true",
                     help="the forward row pass loads its rows from global memory instead "
                          "of staging them in shared memory")

@@ -492,6 +492,12 @@ typedef struct fwi_tuning {
                            samples there; 0: loads from global memory (with
                            row_l2_prefetch).  Results agree to FP32
                            rounding. */
+  int col_pairs;        /* 1 (default): the FP32 convolution pass, where its
+                           transform length is 16, 64 or 256 and its kernel
+                           spectrum is staged, computes two columns per
+                           thread with packed f32x2 arithmetic on column
+                           pairs; 0: one column per thread.  Results agree
+                           to FP32 rounding. */
 } fwi_tuning;
 FWI_API fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out);
 FWI_API fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in);

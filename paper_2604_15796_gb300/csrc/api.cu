@@ -625,6 +625,7 @@ fwi_status fwi_get_tuning(const fwi_ctx* ctx, fwi_tuning* out) {
   out->jac_tma = ctx->jac_tma;
   out->row_l2_prefetch = ctx->row_l2pf;
   out->row_stage = ctx->row_stage;
+  out->col_pairs = ctx->col_pairs;
   for (int k = 0; k < 4; ++k)
     for (int v = 0; v < 4; ++v) out->ms[k][v] = ctx->tune_ms[k][v];
   return FWI_OK;
@@ -656,11 +657,14 @@ fwi_status fwi_set_tuning(fwi_ctx* ctx, const fwi_tuning* in) {
     return fail(ctx, FWI_ERR_INVALID_ARG, "jac_tma must be 0 or 1");
   if (in->row_stage != 0 && in->row_stage != 1)
     return fail(ctx, FWI_ERR_INVALID_ARG, "row_stage must be 0 or 1");
+  if (in->col_pairs != 0 && in->col_pairs != 1)
+    return fail(ctx, FWI_ERR_INVALID_ARG, "col_pairs must be 0 or 1");
   ctx->col_tma = in->col_tma;
   ctx->col_gstage = in->col_spectrum_stage;
   ctx->jac_tma = in->jac_tma;
   ctx->row_l2pf = in->row_l2_prefetch;
   ctx->row_stage = in->row_stage;
+  ctx->col_pairs = in->col_pairs;
   ctx->tc_stall = in->debug_stall_once;
   ctx->use_tc = in->jac_tensor_cores == 1;
   ctx->overlap = in->overlap_halves == 1;

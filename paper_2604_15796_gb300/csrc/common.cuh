@@ -92,6 +92,7 @@ template <typename T> struct ColArgs {
   int freq_fixed;           // >= 0: every RHS uses this frequency
   int tma;                  // FP32, zero-padded input: stage tiles with TMA
   int gstage;               // with tma: also stage the kernel-spectrum tiles
+  int pairs;                // with gstage: two columns per thread where the plan allows
   int* err;                 // error word of bounded waits (or NULL)
 };
 

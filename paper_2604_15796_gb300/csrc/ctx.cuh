@@ -89,6 +89,7 @@ struct fwi_ctx {
   int row_l2pf = 1;                 // row passes prefetch their next item into L2
   int jac_tma = 1;                  // tensor-core contractions take raw tiles by TMA
   int row_stage = 1;                // forward row pass stages its rows (FP32)
+  int col_pairs = 1;                // convolution: two columns per thread (FP32)
   int tc_stall = 0;                 // next contraction withholds its first stage (test)
   double* red = nullptr;            // reduction scratch (doubles)
   double* h_red = nullptr;          // pinned host mirror

@@ -315,7 +315,8 @@ Batch<T> make_batch(fwi_ctx* c, cplx<T>* X, int rhs0, int nb, int off = 0, int h
   for (ColArgs<T>* a : {&b.cz, &b.cy_fwd, &b.cy_inv}) {
     a->active = b.active; a->n_active = b.n_active; a->nb = nb;
     a->rhs0 = rhs0; a->n_elem = c->n_elem; a->freq_fixed = -1;
-    a->tma = c->col_tma; a->gstage = c->col_gstage; a->err = c->tc_err;
+    a->tma = c->col_tma; a->gstage = c->col_gstage; a->pairs = c->col_pairs;
+    a->err = c->tc_err;
   }
   b.cz.tw = (const cplx<T>*)c->tw_z;
   b.cz.ghat = (const cplx<T>*)c->ghat;

@@ -893,6 +893,20 @@ struct NoColHook {
   __device__ void spectrum_done() const {}
 };
 
+// Spectrum row of frequency k = k1 + R1 k2 (k1 < R1), folded onto 0..L/2
+// (the spectrum is even in k).  For unsplit plans with R1 | L/2 the fold is
+// known from the slot alone: k <= L/2 exactly when k2 < L/(2 R1) (k = L/2
+// at k2 = L/(2 R1), k1 = 0 folds onto itself), so no per-element compare.
+template <class P>
+__device__ __forceinline__ int spectrum_row(int k1, int k2, int kp) {
+  const int k = k1 + P::R1 * k2;
+  if constexpr (!PlanTraits<P>::split && (P::L / 2) % P::R1 == 0) {
+    return (kp < P::L / (2 * P::R1)) ? k : P::L - k;
+  } else {
+    return (k <= P::L / 2) ? k : P::L - k;
+  }
+}
+
 template <class P, typename T, int TC, bool TWS = false, class Hook = NoColHook>
 __device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, cplx<T>* smc,
                                                     cplx<T>* v, int rhs, int j,
@@ -932,9 +946,7 @@ __device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, 
           int k1, k2;
           if (slotB<P, GP>(t, i, kp, k1, k2)) {
             const int r = i * PlanTraits<P>::MB + kp;
-            const int k = k1 + P::R1 * k2;
-            const int kk = (k <= P::L / 2) ? k : P::L - k;
-            v[r] = cmul(v[r], gs[kk * TC]);
+            v[r] = cmul(v[r], gs[spectrum_row<P>(k1, k2, kp) * TC]);
           }
         }
       }
@@ -948,9 +960,8 @@ __device__ __forceinline__ bool col_transform_store(const ColArgs<T>& a, int t, 
           int k1, k2;
           if (slotB<P, GP>(t, i, kp, k1, k2)) {
             const int r = i * PlanTraits<P>::MB + kp;
-            const int k = k1 + P::R1 * k2;
-            const int kk = (k <= P::L / 2) ? k : P::L - k;  // same rows as the staged tile
-            v[r] = cmul(v[r], FWI_LDG(g + (long long)kk * a.ncols));
+            // the same rows as the staged tile
+            v[r] = cmul(v[r], FWI_LDG(g + (long long)spectrum_row<P>(k1, k2, kp) * a.ncols));
           }
         }
       }
@@ -1194,6 +1205,12 @@ col_tma_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
   }
 }
 
+}  // namespace fwi
+
+#include "col_pair.cuh"
+
+namespace fwi {
+
 // --------------------------------------------------------------------------
 // Plans per transform length: L = R1 * R2 with TL threads per line.
 template <int L> struct PlanFor;
@@ -1402,6 +1419,19 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
       using SM = ColTmaSmem<L, tc>;
       if constexpr (L / 2 + 1 <= 256) {
         if (col_spectrum_map<L, tc>(a, rows_in, &gmap)) {
+          if constexpr (pair_plan<P>() && tc % 2 == 0) {
+            // two columns per thread: 16-byte stores of column pairs
+            if (a.pairs && ((uintptr_t)a.out & 15) == 0 && a.out_rhs_stride % 2 == 0 &&
+                a.line_stride % 2 == 0 && (a.nplanes == 1 || a.out_plane_stride % 2 == 0)) {
+              auto k = col_pair_kernel<P, tc>;
+              const size_t smem = ColPairSmem<L, tc>::bytes(rows_in);
+              GridCache& gc = gcache<L, T, 6, VAR>();
+              cudaError_t e = grid_for(k, tc / 2 * P::TL, smem, gc);
+              if (e != cudaSuccess) return e;
+              k<<<gc.blocks.load(), tc / 2 * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
+              return cudaGetLastError();
+            }
+          }
           auto k = col_tma_kernel<P, tc, true>;
           const size_t smem = SM::bytes(rows_in, true);
           GridCache& gc = gcache<L, T, 5, VAR>();

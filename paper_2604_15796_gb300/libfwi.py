@@ -70,7 +70,7 @@ class fwi_tuning(Structure):
                 ("jac_tensor_cores", c_int), ("overlap_halves", c_int),
                 ("debug_stall_once", c_int), ("col_tma", c_int),
                 ("col_spectrum_stage", c_int), ("jac_tma", c_int), ("row_l2_prefetch", c_int),
-                ("row_stage", c_int)]
+                ("row_stage", c_int), ("col_pairs", c_int)]
 
 
 class fwi_admm_params(Structure):
@@ -528,7 +528,7 @@ class Context:
                 "jac_tensor_cores": t.jac_tensor_cores, "overlap_halves": t.overlap_halves,
                 "col_tma": t.col_tma, "col_spectrum_stage": t.col_spectrum_stage,
                 "jac_tma": t.jac_tma, "row_l2_prefetch": t.row_l2_prefetch,
-                "row_stage": t.row_stage}
+                "row_stage": t.row_stage, "col_pairs": t.col_pairs}
 
     def set_tuning(self, row_fwd=None, row_inv=None, col=None, col_y=None,
                    jac_tensor_cores=None, overlap_halves=None):
@@ -601,6 +601,15 @@ class Context:
         t = fwi_tuning()
         self._check(fwi_get_tuning(self.handle, byref(t)))
         t.row_stage = int(bool(on))
+        self._check(fwi_set_tuning(self.handle, byref(t)))
+
+    def set_col_pairs(self, on):
+        """The FP32 convolution pass computes two columns per thread with
+        packed arithmetic (True) or one (False), where its transform length
+        allows; results agree to FP32 rounding."""
+        t = fwi_tuning()
+        self._check(fwi_get_tuning(self.handle, byref(t)))
+        t.col_pairs = int(bool(on))
         self._check(fwi_set_tuning(self.handle, byref(t)))
 
     def debug_stall_once(self):

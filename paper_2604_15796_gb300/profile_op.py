@@ -47,6 +47,8 @@ def main():
                     help="row passes without the L2 prefetch of their next work item")
     ap.add_argument("--no-jac-tma", action="store_true",
                     help="tensor-core contractions load their operand tiles with cp.async")
+    ap.add_argument("--no-col-pairs", action="store_true",
+                    help="the convolution computes one column per thread instead of two")
     ap.add_argument("--no-row-stage", action="store_true",
                     help="the forward row pass loads its rows from global memory instead "
                          "of staging them in shared memory")
@@ -68,6 +70,8 @@ def main():
             ctx.set_row_l2_prefetch(False)
         if args.no_row_stage:
             ctx.set_row_stage(False)
+        if args.no_col_pairs:
+            ctx.set_col_pairs(False)
         m = ctx.contrast_from_sos(torch.from_numpy(np.ascontiguousarray(w.sos)).cuda())
         if args.jac:
             if args.cuda_core_jacobian:

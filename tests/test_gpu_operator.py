@@ -151,3 +151,39 @@ def test_staged_row_passes_match_plain_loads(lib, shape):
     assert rel_l2(out[True][0][2], inverse.apply_AH(vin, m, prob, 0)) < 1e-5
     ref_f = operator.solve_forward(m, prob, "bicgstab", tol=1e-10)
     assert rel_l2(out[True][1], ref_f) < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (128, 32), (8, 8, 16), (128, 16, 16), (128, 8, 16)])
+def test_two_column_convolution_matches_one_column(lib, shape):
+    """The FP32 convolution pass gives the same result, to FP32 rounding,
+    with two columns per thread (packed f32x2 arithmetic on column pairs;
+    transform lengths 16, 64 and 256 along the convolution axis) as with
+    one, for single applications of K, A and A^H and for a whole forward
+    solve; both match the oracle."""
+    import torch
+    w = small_workload(shape, n_elem=3, freqs=(2.0e6,))
+    ctx = lib.Context(w.shape, w.h, w.c0, w.elem, w.freqs, tol=1e-6)
+    m = contrast(w)
+    m_gpu = to_gpu(m, torch.complex128)
+    v = phantoms.complex_normal((3,) + tuple(shape), 29)
+    v_gpu = to_gpu(v, torch.complex64)
+    out = {}
+    for pairs in (True, False):
+        ctx.set_col_pairs(pairs)
+        assert ctx.tuning()["col_pairs"] == int(pairs)
+        ops = [to_np(ctx.apply(k, v_gpu, 0, None if k == "K" else m_gpu))
+               for k in ("K", "A", "AH")]
+        f = ctx.empty_fields()
+        ctx.forward(m_gpu, fields=f)
+        out[pairs] = (ops, to_np(f))
+    ctx.close()
+    for a, b in zip(out[True][0], out[False][0]):
+        assert rel_l2(a, b) < 3e-7, rel_l2(a, b)
+    assert rel_l2(out[True][1], out[False][1]) < 1e-5
+    prob = oracle_problem(w)
+    vin = v.astype(np.complex64).astype(np.complex128)
+    assert rel_l2(out[True][0][0], operator.apply_K(vin, prob, 0)) < 1e-5
+    assert rel_l2(out[True][0][1], operator.apply_A(vin, m, prob, 0)) < 1e-5
+    assert rel_l2(out[True][0][2], inverse.apply_AH(vin, m, prob, 0)) < 1e-5
+    ref_f = operator.solve_forward(m, prob, "bicgstab", tol=1e-10)
+    assert rel_l2(out[True][1], ref_f) < 1e-4
