@@ -1,5 +1,5 @@
-// Convolution pass with two columns per thread (FP32, unsplit plans whose
-// line is one thread per n2 and per k1: R1 = R2 = TL, a power of two).
+// Convolution pass with two columns per thread (FP32; plans listed at
+// pair_plan: power-of-two DFTs, whole first DFTs per thread).
 //
 // The transforms are the four-step FFT of fft_core.cuh (forward FFT along
 // the column with the zero-padded half pruned, product with the kernel
@@ -16,9 +16,10 @@
 // sum, so results agree with the one-column kernel to FP32 rounding.
 //
 // The rest follows col_tma_kernel: persistent CTAs over the slot-fast item
-// order, the next item's input tile and kernel-spectrum tile staged by TMA
-// into shared memory while the current item transforms, bounded mbarrier
-// waits with the same error codes.
+// order, the next item's input tile (and, where it fits, its kernel-spectrum
+// tile) staged by TMA into shared memory while the current item transforms,
+// bounded mbarrier waits with the same error codes.  Split plans share their
+// second DFTs over a lane pair, exchanging column pairs by warp shuffles.
 #pragma once
 
 namespace fwi {
@@ -213,46 +214,114 @@ template <int R, bool INV> struct PDftHalfOut {
   }
 };
 
+// Exchange of a pair with the partner lane of a split DFT (16 lanes away).
+__device__ __forceinline__ PC shfl_pc(PC a) {
+  float x0, x1, y0, y1;
+  upk(a.re, x0, x1);
+  upk(a.im, y0, y1);
+  x0 = __shfl_xor_sync(0xffffffffu, x0, 16);
+  x1 = __shfl_xor_sync(0xffffffffu, x1, 16);
+  y0 = __shfl_xor_sync(0xffffffffu, y0, 16);
+  y1 = __shfl_xor_sync(0xffffffffu, y1, 16);
+  return {pk(x0, x1), pk(y0, y1)};
+}
+// z * (h w + (1 - h)) with w = w_R^J (conjugated for INV): lane h = 0 keeps
+// z, lane 1 gets z w (hf = h, hc = 1 - h are exactly 0 or 1)
+template <int J, int R, bool INV>
+__device__ __forceinline__ PC plane_twiddle(PC z, float hf, float hc) {
+  constexpr int q = tw_quarter(J, R);
+  if constexpr (q == 0) {
+    return z;
+  } else {
+    constexpr double wr = q == 2 ? -1.0 : (q == 1 || q == 3) ? 0.0 : tw_re(J, R);
+    constexpr double wf = q == 1 ? -1.0 : q == 3 ? 1.0 : q == 2 ? 0.0 : tw_im(J, R);
+    constexpr double wi = INV ? -wf : wf;
+    const float av = hf * (float)wr + hc;
+    const float bv = hf * (float)wi;
+    return ptw_tab(z, pk(av, av), pk(bv, bv));
+  }
+}
+// R = 2Q point DFT over a lane pair (lanes 16 apart).  split: lane h holds
+// x[2m + h] (m < Q) and ends with X[k + Q h] (k < Q).  isplit: lane h holds
+// X[k + Q h] and ends with x[2m + h] (unnormalised).
+template <int Q, bool INV> __device__ __forceinline__ void psplit_dft(PC* u, int h) {
+  PDft<Q, INV>::run(u);
+  const float hf = (float)h, hc = (float)(1 - h), sg = (float)(1 - 2 * h);
+  const u64 sgp = pk(sg, sg);
+  SFor<Q>::run([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const PC v = plane_twiddle<k, 2 * Q, INV>(u[k], hf, hc);
+    const PC o = shfl_pc(v);
+    u[k] = {f2fma(sgp, v.re, o.re), f2fma(sgp, v.im, o.im)};
+  });
+}
+template <int Q, bool INV> __device__ __forceinline__ void psplit_idft(PC* u, int h) {
+  const float hf = (float)h, hc = (float)(1 - h), sg = (float)(1 - 2 * h);
+  const u64 sgp = pk(sg, sg);
+  SFor<Q>::run([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    const PC own = u[k];
+    const PC o = shfl_pc(own);
+    const PC z = {f2fma(sgp, own.re, o.re), f2fma(sgp, own.im, o.im)};
+    u[k] = plane_twiddle<k, 2 * Q, INV>(z, hf, hc);
+  });
+  PDft<Q, INV>::run(u);
+}
+
 }  // namespace pair
 
-// Plans the two-column kernel covers: one thread per n2 and per k1.
+constexpr bool pow2_at_least(int r, int m) { return r >= m && (r & (r - 1)) == 0; }
+
+// Plans the two-column kernel covers: unsplit plans with one thread per n2
+// and per k1 (R1 = R2 = TL), and split plans whose first DFTs are whole
+// (S1 = 1) and whose second DFTs are shared by a lane pair (S2 = 2); all
+// DFT sizes powers of two.
 template <class P> constexpr bool pair_plan() {
   if constexpr (PlanTraits<P>::split) {
-    return false;
+    return P::S1 == 1 && P::S2 == 2 && pow2_at_least(P::R1, 4) && pow2_at_least(P::Q2, 2);
   } else {
-    return P::R1 == P::TL && P::R2 == P::TL && (P::R1 & (P::R1 - 1)) == 0 && P::R1 >= 4;
+    return P::R1 == P::TL && P::R2 == P::TL && pow2_at_least(P::R1, 4);
   }
 }
 
 // Shared memory (bytes from the 128-byte aligned base): exchange L x TC/2
 // pairs (16 bytes each) | input staging rows_in x TC | spectrum staging
-// (L/2 + 1) x TC | pair twiddle table L x (c, c, s, s) | two mbarriers and
-// the abort flag.
+// (L/2 + 1) x TC (GS only) | pair twiddle table L x (c, c, s, s) | two
+// mbarriers and the abort flag.
 template <int L, int TC> struct ColPairSmem {
   static constexpr int G_ROWS = L / 2 + 1;
-  static constexpr size_t bytes(int rows_in) {
-    return ((size_t)L * TC + (size_t)rows_in * TC + (size_t)G_ROWS * TC) * sizeof(float2) +
+  static constexpr size_t bytes(int rows_in, bool gs) {
+    return ((size_t)L * TC + (size_t)rows_in * TC + (gs ? (size_t)G_ROWS * TC : 0)) *
+               sizeof(float2) +
            (size_t)L * sizeof(float4) + 32 + 128;
   }
 };
 
-// Registers: 170 keeps three 128-thread CTAs per SM (the shared memory
-// holds three as well).
-template <class P, int TC>
-__global__ void __launch_bounds__(TC / 2 * P::TL, blocks_for_regs(TC / 2 * P::TL, 168))
+// GS: the kernel spectrum tile of each item is staged by TMA (rows 0..L/2);
+// otherwise each thread reads its spectrum pairs from global memory (L2).
+// Registers: 168 keeps three 128-thread CTAs per SM (the shared memory of
+// the 256-point convolution holds three as well); 256-thread CTAs get 128
+// (two per SM).
+constexpr int pair_regs(int threads) { return threads > 128 ? 128 : 168; }
+template <class P, int TC, bool GS>
+__global__ void __launch_bounds__(TC / 2 * P::TL,
+                                  blocks_for_regs(TC / 2 * P::TL, pair_regs(TC / 2 * P::TL)))
 col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
                 const __grid_constant__ CUtensorMap gmap, int rows_in, int nbox) {
   using namespace pair;
   static_assert(pair_plan<P>(), "two-column plan");
+  constexpr bool SPLIT = PlanTraits<P>::split;
   constexpr int NP = TC / 2;  // column pairs per tile
+  constexpr int GP = 32 / NP;  // consecutive line threads per warp
   constexpr int R1 = P::R1, R2 = P::R2, H1 = P::H1;
+  constexpr int NB = PlanTraits<P>::MB;  // phase-B values per thread (R2, or Q2 split)
   constexpr int G_ROWS = ColPairSmem<P::L, TC>::G_ROWS;
   extern __shared__ __align__(16) unsigned char smraw[];
   const uint32_t base_pad = (128u - (tc::smem_addr(smraw) & 127u)) & 127u;
   float4* ex = reinterpret_cast<float4*>(smraw + base_pad);        // exchange, L x NP
   float2* stg = reinterpret_cast<float2*>(ex + P::L * NP);         // input staging
   float2* gst = stg + rows_in * TC;                                // spectrum staging
-  float4* twp = reinterpret_cast<float4*>(gst + G_ROWS * TC);      // pair twiddles
+  float4* twp = reinterpret_cast<float4*>(gst + (GS ? G_ROWS * TC : 0));  // pair twiddles
   uint64_t* bar = reinterpret_cast<uint64_t*>(twp + P::L);         // [0] input, [1] spectrum
   volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 2);
   const uint32_t bar_in = tc::smem_addr(bar), bar_g = tc::smem_addr(bar + 1);
@@ -260,7 +329,11 @@ col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
   const float4* stg4 = reinterpret_cast<const float4*>(stg);
   const float4* gst4 = reinterpret_cast<const float4*>(gst);
   const int cp = threadIdx.x % NP;  // column pair 2cp, 2cp + 1 of the tile
-  const int t = threadIdx.x / NP;   // thread of the line
+  const int t = threadIdx.x / NP;   // thread of the line (owns n2 = t in phases A, D)
+  // phases B, C: this thread's k1 and, split, its half h of the lane pair
+  int kb, h = 0;
+  if constexpr (SPLIT) decode<2, GP>(t, kb, h);
+  else kb = t;
   const unsigned ntile = (unsigned)(a.ncols / TC);
   const unsigned per_rhs = (unsigned)a.nplanes * ntile;
   const int nact = a.active ? *a.n_active : a.nb;
@@ -301,7 +374,7 @@ col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
   __syncthreads();
   if (threadIdx.x == 0 && blockIdx.x < items) {
     issue_input(blockIdx.x);
-    issue_spectrum(blockIdx.x);
+    if (GS) issue_spectrum(blockIdx.x);
   }
   uint32_t par_in = 0, par_g = 0;
   bool failed = false, bad = false;
@@ -309,7 +382,7 @@ col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
     const ColItem it = col_item(item, (unsigned)nact, per_rhs, ntile, a.nplanes, true);
     const int j = it.tile * TC + 2 * cp;
     const bool ok = tc::mbar_wait(bar_in, par_in, abort_flag, err, kColErrWait);
-    PC v[R1];
+    PC v[P::E];
     const u64 zero = pk(0.f, 0.f);
     // phase-A samples x[R2 n1 + t] (n1 < R1/2; the rest is the zero padding)
 #pragma unroll
@@ -341,32 +414,53 @@ col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
     }
     // one thread waits for the staged spectrum; the barrier hands its
     // completion (and the copied data) to the others
-    if (threadIdx.x == 0 && !tc::mbar_wait(bar_g, par_g, abort_flag, err, kColErrWait)) bad = true;
+    if (GS && threadIdx.x == 0 && !tc::mbar_wait(bar_g, par_g, abort_flag, err, kColErrWait))
+      bad = true;
     __syncthreads();
-    // phase B: R2-point DFTs over n2; v[k2] = X[t + R1 k2]
+    // phase B: R2-point DFTs over n2 (split: over the lane pair, n2 = 2m + h);
+    // v[kp] = X[kb + R1 k2] with k2 = kp (split: kp + Q2 h)
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) v[n2] = lds_pc(ex + (n2 * R1 + t) * NP + cp);
-    PDft<R2, false>::run(v);
-    // product with the kernel spectrum (rows folded onto 0..L/2)
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) {
-      const float4 g = gst4[spectrum_row<P>(t, k2, k2) * NP + cp];
-      v[k2] = pmul(v[k2], pk(g.x, g.z), pk(g.y, g.w));
+    for (int m = 0; m < NB; ++m) {
+      const int n2 = SPLIT ? 2 * m + h : m;
+      v[m] = lds_pc(ex + (n2 * R1 + kb) * NP + cp);
     }
-    __syncthreads();
-    // every thread is done with the staged spectrum: stage the next one
-    par_g ^= 1u;
-    if (threadIdx.x == 0 && next < items && !*abort_flag) issue_spectrum(next);
-    // phase C: inverse R2-point DFTs, twiddle w_L^{-n2 t}, y[n2][t]
-    PDft<R2, true>::run(v);
+    if constexpr (SPLIT) psplit_dft<NB, false>(v, h);
+    else PDft<R2, false>::run(v);
+    // product with the kernel spectrum (rows folded onto 0..L/2): the
+    // staged tile, or the columns (j, j + 1) of this item's frequency
+    const float4* __restrict__ gg = nullptr;
+    if constexpr (!GS) {
+      const int l = a.freq_fixed >= 0 ? a.freq_fixed : (a.rhs0 + rhs_of(it)) / a.n_elem;
+      gg = reinterpret_cast<const float4*>(a.ghat + (long long)l * a.ghat_freq_stride + j);
+    }
 #pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) {
-      PC z = v[n2];
-      if (n2 > 0 && t > 0) {
-        const float4 w = twp[n2 * t];
+    for (int kp = 0; kp < NB; ++kp) {
+      const int row = spectrum_row<P>(kb, SPLIT ? kp + NB * h : kp, kp);
+      float4 g;
+      if constexpr (GS) g = gst4[row * NP + cp];
+      else g = __ldg(gg + (long long)row * (a.ncols / 2));
+      v[kp] = pmul(v[kp], pk(g.x, g.z), pk(g.y, g.w));
+    }
+    if constexpr (GS) {
+      __syncthreads();
+      // every thread is done with the staged spectrum: stage the next one
+      par_g ^= 1u;
+      if (threadIdx.x == 0 && next < items && !*abort_flag) issue_spectrum(next);
+    } else {
+      __syncthreads();  // every thread has read its phase-B values
+    }
+    // phase C: inverse DFTs over k2, twiddle w_L^{-n2 kb}, y[n2][kb]
+    if constexpr (SPLIT) psplit_idft<NB, true>(v, h);
+    else PDft<R2, true>::run(v);
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+      const int n2 = SPLIT ? 2 * m + h : m;
+      PC z = v[m];
+      if (n2 > 0 && kb > 0) {
+        const float4 w = twp[n2 * kb];
         z = ptw_tab_conj(z, pk(w.x, w.y), pk(w.z, w.w));
       }
-      sts_pc(ex + (n2 * R1 + t) * NP + cp, z);
+      sts_pc(ex + (n2 * R1 + kb) * NP + cp, z);
     }
     __syncthreads();
     // phase D: inverse R1-point DFTs of which the cropped half is formed
@@ -380,7 +474,7 @@ col_pair_kernel(const ColArgs<float> a, const __grid_constant__ CUtensorMap map,
   // copies of a CTA that stopped early may still land in its shared memory
   if (failed && threadIdx.x == 0) {
     tc::mbar_wait_drain(bar_in, par_in, err, kColErrDrain);
-    tc::mbar_wait_drain(bar_g, par_g, err, kColErrDrain);
+    if (GS) tc::mbar_wait_drain(bar_g, par_g, err, kColErrDrain);
   }
 }
 

@@ -1408,6 +1408,13 @@ bool col_tensor_map(const ColArgs<float>& a, CUtensorMap* map, int* rows_in, int
   return true;
 }
 
+// The two-column convolution stores 16-byte column pairs.
+template <typename T> bool col_pair_ok(const ColArgs<T>& a) {
+  return a.mode == C_CONV && a.pairs && a.ghat && ((uintptr_t)a.out & 15) == 0 &&
+         a.out_rhs_stride % 2 == 0 && a.line_stride % 2 == 0 &&
+         (a.nplanes == 1 || a.out_plane_stride % 2 == 0);
+}
+
 template <int L, typename T, int VAR>
 cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
   using P = typename PlanFor<L>::type;
@@ -1420,11 +1427,9 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
       if constexpr (L / 2 + 1 <= 256) {
         if (col_spectrum_map<L, tc>(a, rows_in, &gmap)) {
           if constexpr (pair_plan<P>() && tc % 2 == 0) {
-            // two columns per thread: 16-byte stores of column pairs
-            if (a.pairs && ((uintptr_t)a.out & 15) == 0 && a.out_rhs_stride % 2 == 0 &&
-                a.line_stride % 2 == 0 && (a.nplanes == 1 || a.out_plane_stride % 2 == 0)) {
-              auto k = col_pair_kernel<P, tc>;
-              const size_t smem = ColPairSmem<L, tc>::bytes(rows_in);
+            if (col_pair_ok(a)) {
+              auto k = col_pair_kernel<P, tc, true>;
+              const size_t smem = ColPairSmem<L, tc>::bytes(rows_in, true);
               GridCache& gc = gcache<L, T, 6, VAR>();
               cudaError_t e = grid_for(k, tc / 2 * P::TL, smem, gc);
               if (e != cudaSuccess) return e;
@@ -1442,6 +1447,19 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
         }
       }
       std::memset(&gmap, 0, sizeof(gmap));
+      if constexpr (pair_plan<P>() && tc % 2 == 0) {
+        // the spectrum from global memory (16-byte column pairs)
+        if (col_pair_ok(a) && ((uintptr_t)a.ghat & 15) == 0 && a.ncols % 2 == 0 &&
+            a.ghat_freq_stride % 2 == 0) {
+          auto k = col_pair_kernel<P, tc, false>;
+          const size_t smem = ColPairSmem<L, tc>::bytes(rows_in, false);
+          GridCache& gc = gcache<L, T, 7, VAR>();
+          cudaError_t e = grid_for(k, tc / 2 * P::TL, smem, gc);
+          if (e != cudaSuccess) return e;
+          k<<<gc.blocks.load(), tc / 2 * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
+          return cudaGetLastError();
+        }
+      }
       auto k = col_tma_kernel<P, tc, false>;
       const size_t smem = SM::bytes(rows_in, false);
       const size_t smem_max = SM::bytes(L, false);  // inverse mode: all L rows staged

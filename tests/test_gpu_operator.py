@@ -153,11 +153,12 @@ def test_staged_row_passes_match_plain_loads(lib, shape):
     assert rel_l2(out[True][1], ref_f) < 1e-4
 
 
-@pytest.mark.parametrize("shape", [(32, 32), (128, 32), (8, 8, 16), (128, 16, 16), (128, 8, 16)])
+@pytest.mark.parametrize("shape", [(32, 32), (128, 32), (8, 8, 16), (128, 16, 16), (128, 8, 16),
+                                   (256, 16), (256, 96), (256, 8, 8)])
 def test_two_column_convolution_matches_one_column(lib, shape):
     """The FP32 convolution pass gives the same result, to FP32 rounding,
     with two columns per thread (packed f32x2 arithmetic on column pairs;
-    transform lengths 16, 64 and 256 along the convolution axis) as with
+    transform lengths 16, 64, 256 and 512 along the convolution axis) as with
     one, for single applications of K, A and A^H and for a whole forward
     solve; both match the oracle."""
     import torch
