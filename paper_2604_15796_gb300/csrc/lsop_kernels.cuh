@@ -1319,14 +1319,20 @@ template <int L, typename T, int VAR> constexpr size_t row_fwd_stage_smem(int ns
          (size_t)nsrc * row_lpc_v<L, VAR>() * (L / 2) * sizeof(cplx<T>) + 16;
 }
 
+// Staging pays while at least three CTAs fit per SM: the BiCGSTAB update
+// mode's six arrays of 768-sample rows (about 100 KB) left two and made that
+// pass 13 % slower than its plain loads, every other measured case is faster.
+constexpr size_t kRowStageMaxSmem = 80 * 1024;
+
 template <int L, typename T, int VAR>
 cudaError_t launch_row_fwd(const RowFwdArgs<T>& a, cudaStream_t s) {
   using P = typename PlanFor<L>::type;
   constexpr int lpc = row_lpc_v<L, VAR>();
   if constexpr (sizeof(T) == 4) {
-    if (a.stage && !a.full && 2 * a.nx == L && rf_stage_aligned(a)) {
+    const int nsrc = rf_stage_count(a.mode, a.use_m);
+    if (a.stage && !a.full && 2 * a.nx == L && rf_stage_aligned(a) &&
+        row_fwd_stage_smem<L, T, VAR>(nsrc) <= kRowStageMaxSmem) {
       auto k = row_fwd_kernel<P, T, lpc, true>;
-      const int nsrc = rf_stage_count(a.mode, a.use_m);
       const size_t smem = row_fwd_stage_smem<L, T, VAR>(nsrc);
       // one occupancy per staged-array count (the modes differ in smem)
       GridCache& gc = nsrc <= 1 ? gcache<L, T, 11, VAR>()
@@ -1447,6 +1453,15 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
         }
       }
       std::memset(&gmap, 0, sizeof(gmap));
+      // The plain kernel's residency: the TMA kernel below runs only where
+      // its staging buffer keeps at least as many CTAs per SM (the 768-point
+      // columns' staging left two of three, and the pass ran 20 % slower).
+      auto kp = col_kernel<P, T, tc>;
+      GridCache& gcp = gcache<L, T, 2, VAR>();
+      {
+        cudaError_t e = grid_for(kp, tc * P::TL, col_smem_v<L, T, VAR>(), gcp);
+        if (e != cudaSuccess) return e;
+      }
       if constexpr (pair_plan<P>() && tc % 2 == 0) {
         // the spectrum from global memory (16-byte column pairs)
         if (col_pair_ok(a) && ((uintptr_t)a.ghat & 15) == 0 && a.ncols % 2 == 0 &&
@@ -1466,8 +1481,10 @@ cudaError_t launch_col(const ColArgs<T>& a, cudaStream_t s) {
       GridCache& gc = (a.mode == C_INV) ? gcache<L, T, 4, VAR>() : gcache<L, T, 3, VAR>();
       cudaError_t e = grid_for(k, tc * P::TL, smem, gc, smem_max);
       if (e != cudaSuccess) return e;
-      k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
-      return cudaGetLastError();
+      if (gc.blocks.load() >= gcp.blocks.load()) {
+        k<<<gc.blocks.load(), tc * P::TL, smem, s>>>(a, map, gmap, rows_in, nbox);
+        return cudaGetLastError();
+      }
     }
   }
   auto k = col_kernel<P, T, tc>;
